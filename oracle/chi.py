@@ -1,0 +1,74 @@
+"""Polarizability chi0 (Secs. II.B and II.C steps (i)-(ii)).  Oracle only.
+
+Real space, imaginary time (Eqs. chi_GG, chi_rr), spin-degenerate factor 2,
+index order chi(r,r') = -2 G_occ(r,r') G_unocc(r',r):
+
+    chi(r,r',tau) = -2 G_occ(r,r',tau) G_unocc(r',r,tau)
+
+For complex orbitals this is the complex conjugate (equivalently, the
+transpose) of the tau > 0 slice as printed in Eq. chi_rr; both are Hermitian
+and negative semidefinite after the transform below, and they coincide for
+real orbitals.
+
+Reciprocal space (Eqs. FFTX1, FFTX2 with the normalisation chosen so that the
+dielectric matrix reads eps = 1 - v chi with v = 4 pi / |G|^2):
+
+    chi(G,G',tau) = (dV^2 / Omega) sum_r sum_r' exp(-i G.r) chi(r,r') exp(+i G'.r')
+
+written here as dense phase matrices (a direct DFT, not an FFT algorithm).
+"""
+import numpy as np
+
+from . import gvec as _gv
+
+
+def chi_rr(g_occ, g_unocc):
+    """Eq. chi_rr (spec index order, spin factor 2)."""
+    return -2.0 * g_occ * g_unocc.T
+
+
+def rows_to_g(x_rr, gvecs, n):
+    """Eq. FFTX1: X(r,G') = sum_R' x(r,R') exp(+i G'.R') for the G' of the set."""
+    pm = _gv.phase_matrix(gvecs, n, -1.0)          # exp(-i G.r)
+    return x_rr @ pm.conj().T
+
+
+def cols_to_g(x_rg, gvecs, n, lattice):
+    """Eq. FFTX2 with the dV^2/Omega factor: chi(G,G') = dV^2/Omega sum_r exp(-iG.r) X(r,G')."""
+    vol = abs(np.linalg.det(lattice))
+    dv = vol / int(np.prod(n))
+    pm = _gv.phase_matrix(gvecs, n, -1.0)
+    return (dv * dv / vol) * (pm @ x_rg)
+
+
+def chi_gg(x_rr, gvecs, n, lattice):
+    """Both steps at once: (dV^2/Omega) P x P^H with P[j][r] = exp(-i G_j.r)."""
+    return cols_to_g(rows_to_g(x_rr, gvecs, n), gvecs, n, lattice)
+
+
+def pair_matrix_elements(psi, n_occ, gvecs, n, lattice):
+    """M_ai(G) = dV sum_r exp(-i G.r) psi_a^*(r) psi_i(r): the matrix elements
+    <psi_a| e^{-iG.r} |psi_i> of Eq. CHI_g_it, shape [N_unocc][N_occ][N_chi]."""
+    vol = abs(np.linalg.det(lattice))
+    dv = vol / int(np.prod(n))
+    pm = _gv.phase_matrix(gvecs, n, -1.0)           # [N_chi][N_r]
+    occ = psi[:n_occ]
+    un = psi[n_occ:]
+    prod = un.conj()[:, None, :] * occ[None, :, :]   # [Nu][No][N_r]
+    return dv * prod @ pm.T
+
+
+def chi_pair(psi, eps, n_occ, mu, tau, gvecs, n, lattice, m=None):
+    """Adler-Wiser pair form in imaginary time (Eq. CHI_g_it):
+    chi(G,G',tau) = -(2/Omega) sum_{i,a} exp(-(eps_a - eps_i) tau) M_ai(G) M_ai(G')^*."""
+    vol = abs(np.linalg.det(lattice))
+    if m is None:
+        m = pair_matrix_elements(psi, n_occ, gvecs, n, lattice)
+    w = np.exp(-(eps[n_occ:, None] - eps[None, :n_occ]) * tau)   # [Nu][No]
+    mm = m.reshape(-1, m.shape[-1])
+    return -(2.0 / vol) * (mm.T * w.reshape(-1)) @ mm.conj()
+
+
+def ct(f_tau, C):
+    """Eq. CTX: F(i omega_k) = sum_j C_kj F(i tau_j) over the leading axis."""
+    return np.tensordot(C, f_tau, axes=(1, 0))

@@ -1,0 +1,65 @@
+"""Diagonal correlation self-energy (Sec. II.D).  Oracle only.
+
+Space-time route (Eq. Sigma_rr, first term of Eq. Sigma_occ_reduce; the PAW
+one-centre terms are out of scope).  With G_occ/G_unocc as in green.py and
+W~ even in tau,
+
+    Sigma_unocc_nn(tau)  = + dV^2 sum_{r,r'} psi_n^*(r) G_unocc(r,r',tau) W~(r,r',tau) psi_n(r')
+    Sigma_occ_nn(-tau)   = - dV^2 sum_{r,r'} psi_n^*(r) G_occ(r,r',tau)   W~(r,r',tau) psi_n(r')
+
+(the paper's overline/underline Sigma = -G W~ with its overline-G = -G_unocc).
+Both quadratic forms are real (G o W~ is Hermitian); their real parts are kept.
+
+Even/odd split and transform (Eqs. cos_sin_sigma_matrix1/2, sigma_r_w,
+cos_sin_sigma1/2):
+
+    Sigma^c(tau) = (Sigma_unocc(tau) + Sigma_occ(-tau)) / 2
+    Sigma^s(tau) = (Sigma_unocc(tau) - Sigma_occ(-tau)) / 2
+    Sigma(i omega_k) = sum_j C_kj Sigma^c(tau_j) + i sum_j S_kj Sigma^s(tau_j)
+"""
+import numpy as np
+
+from . import green as _gr
+
+
+def sigma_tau(psi, eps, n_occ, mu, tau, w_rr, bands, dv):
+    """(Sigma_unocc_nn(tau), Sigma_occ_nn(-tau)) for the listed bands at one tau."""
+    gu = _gr.green_unocc(psi, eps, n_occ, mu, tau)
+    go = _gr.green_occ(psi, eps, n_occ, mu, tau)
+    hu = gu * w_rr
+    ho = go * w_rr
+    su = np.empty(len(bands))
+    so = np.empty(len(bands))
+    for b, n_ in enumerate(bands):
+        p = psi[n_]
+        su[b] = (dv * dv * (p.conj() @ hu @ p)).real
+        so[b] = -(dv * dv * (p.conj() @ ho @ p)).real
+    return su, so
+
+
+def sigma_pair_tau(psi, eps, n_occ, mu, tau, w_gg, gvecs, n, lattice, bands):
+    """Conventional route: Sigma_unocc_nn(tau) = (1/Omega) sum_{m unocc}
+    exp(-(eps_m-mu) tau) a_nm^H W~ a_nm with a_nm(G) = dV sum_r exp(-iG.r)
+    psi_m^*(r) psi_n(r); Sigma_occ_nn(-tau) likewise over occupied m with
+    exp(+(eps_m-mu) tau) and a minus sign.  Same quantity as sigma_tau."""
+    from . import gvec as _gv
+    vol = abs(np.linalg.det(lattice))
+    dv = vol / int(np.prod(n))
+    pm = _gv.phase_matrix(gvecs, n, -1.0)
+    su = np.empty(len(bands))
+    so = np.empty(len(bands))
+    for b, n_ in enumerate(bands):
+        a = dv * (psi.conj() * psi[n_][None, :]) @ pm.T      # [N_b][N_chi]
+        q = np.einsum("mg,gh,mh->m", a.conj(), w_gg, a).real / vol
+        fu = np.exp(-(eps[n_occ:] - mu) * tau)
+        fo = np.exp((eps[:n_occ] - mu) * tau)
+        su[b] = (fu * q[n_occ:]).sum()
+        so[b] = -(fo * q[:n_occ]).sum()
+    return su, so
+
+
+def sigma_iw(s_unocc, s_occ, C, S):
+    """Sigma_nn(i omega_k) from [N_n][N_tau] arrays via CT + ST."""
+    sc = 0.5 * (s_unocc + s_occ)
+    ss = 0.5 * (s_unocc - s_occ)
+    return sc @ C.T + 1j * (ss @ S.T)
