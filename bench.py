@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the space-time GW hot path on synthetic Si-like inputs.
+
+One step = the whole hot path through the C ABI on one seeded system:
+chi0(i omega) (gw_chi0_omega: G formation, chi = -2 G_occ o conj(G_unocc), row
+and column FFTs, cosine transform), screening (gw_screen_W), inverse cosine
+transform (gw_tau_to_omega), and the diagonal self-energy with its Thiele
+continuation (gw_sigma_diag).  The metric is the effective TFLOP/s of the
+method's algorithmic work (flop model below) divided by the device time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gw|reference]
+                  [--prec fp32|fp64|f16x3|bf16x3] [--workload si8|gamma_toy]
+
+N > 1 (under torchrun): independent replicas, one per GPU (the path is not
+sharded); value = the work of all ranks / the slowest rank's time.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "chi0+Sigma_nn effective TFLOP/s"
+N_REAL = 64          # real frequencies of the continued Sigma_nn(omega)
+FLUSH_BYTES = 512 << 20
+
+
+def flop_model(n_r, n_b, n_tau, n_chi, n_n):
+    """Algorithmic flops of one pass of the hot path (complex MAC = 8 flops)."""
+    lg = math.log2(n_r)
+    f = {
+        # G_occ and G_unocc, once for chi and once again for Sigma (Eqs. Green_occ/unocc)
+        "green": 2 * n_tau * 8.0 * n_r * n_r * n_b,
+        # chi rows, chi columns, W~ columns, W~ rows: 5 N log2 N per transform
+        "fft": n_tau * (2 * n_r + 2 * n_chi) * 5.0 * n_r * lg,
+        # forward and inverse cosine transform, real weight x complex data
+        "ct": 2 * n_tau * n_tau * 4.0 * n_chi * n_chi,
+        # eps~ = L L^H, L^{-1}, L^{-H} L^{-1}: N^3/2 complex MACs per frequency
+        "dyson": n_tau * 4.0 * n_chi ** 3,
+        # (G o W~) psi_n for the occupied and unoccupied parts
+        "sigma": n_tau * 2 * 8.0 * n_r * n_r * n_n,
+        # real-space products chi = -2 G_occ conj(G_unocc) and G o W~ (6 flops each)
+        "hadamard": n_tau * 3 * 6.0 * n_r * n_r,
+    }
+    f["total"] = sum(f.values())
+    return f
+
+
+def sm_peak_fp32(sm_mhz, n_sm=152):
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.p is None:
+            return out
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------- reference arm (CPU oracle)
+
+def oracle_sample(p, rows=96, n_solve=1536):
+    """Time the FP64 oracle on a bounded slice of the workload: G_occ/G_unocc rows and the
+    real-space chi product for `rows` rows at every tau, plus one screening solve of size
+    n_solve.  Returns (flops, seconds) under the same flop model."""
+    from oracle import chi as ochi  # noqa: F401  (oracle only in this leg)
+    from oracle import green as ogr
+    from oracle import screen as osc
+    rr = np.arange(rows)
+    t0 = time.perf_counter()
+    for tau in p.tau:
+        go = ogr.green_occ_rows(p.psi, p.eps, p.n_occ, p.mu, tau, rr)
+        gu = ogr.green_unocc_rows(p.psi, p.eps, p.n_occ, p.mu, tau, rr)
+        _ = -2.0 * go * gu.conj()
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((n_solve, 64)) + 1j * rng.standard_normal((n_solve, 64))
+    chi = -(a @ a.conj().T) / n_solve
+    osc.screen_one(chi, np.full(n_solve, 0.5))
+    dt = time.perf_counter() - t0
+    flops = len(p.tau) * 8.0 * rows * p.n_r * p.n_b + len(p.tau) * 6.0 * rows * p.n_r + 4.0 * n_solve ** 3
+    return flops, dt
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads") or 0) for i in threadpool_info())
+        if n:
+            return n
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(args, p, workload):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(p, rows=32, n_solve=512)
+    tot_f, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        f, t = oracle_sample(p)
+        tot_f += f
+        tot_t += t
+    val = tot_f / tot_t / 1e12
+    sample = "FP64 numpy oracle: G_occ/G_unocc rows + chi product for 96 of %d rows at all %d tau, plus one 1536^2 screening solve" % (p.n_r, len(p.tau))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload,
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "f16x3", "bf16x3"])
+    ap.add_argument("--workload", default="si8", choices=["si8", "gamma_toy"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from paper_1607_02859_gb300 import inputs
+    p = getattr(inputs, args.workload)()
+    n_tau = len(p.tau)
+    workload = {"workload": "%s: %dx%dx%d grid (N_r=%d), %d+%d %s bands, %d tau/i omega, chi0 %dx%d, Sigma_nn for %d bands"
+                % (args.workload, *p.n, p.n_r, p.n_occ, p.n_b - p.n_occ, "real" if p.real else "complex", n_tau,
+                   p.n_chi, p.n_chi, len(p.bands)),
+                "prec": args.prec, "l2": "per-step working set > 40 GB >> 129 MB L2; L2 also flushed between steps"}
+    if args.impl == "reference":
+        run_reference(args, p, workload)
+        return
+
+    import torch
+    from paper_1607_02859_gb300 import gw
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    ctx = gw.Context(local)
+    grid = gw.make_grid(p.n, p.lattice)
+    gvec, fidx = gw.g_set(grid, p.n_chi)                                      # product host setup
+    mats = gw.fit_transform(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
+    dt = gw.cdtype(args.prec)
+    psi_h = torch.from_numpy(p.psi.astype(np.complex128)).to(dt).pin_memory()
+    psi = psi_h.to("cuda", non_blocking=False)
+    chi_w = torch.empty((n_tau, p.n_chi, p.n_chi), dtype=dt, device="cuda")
+    w_tau = torch.empty_like(chi_w)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    w_real = np.linspace(-1.0, 1.0, N_REAL)
+    stream = torch.cuda.current_stream()
+
+    def step(psi_dev, events=None):
+        def mark(i):
+            if events is not None:
+                events[i].record(stream)
+        mark(0)
+        gw.chi0_omega(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.tau, mats["C"], fidx, args.prec, chi_w)
+        mark(1)
+        gw.screen_W(ctx, grid, gvec, args.prec, chi_w, chi_w, resid=False)
+        mark(2)
+        gw.tau_to_omega(ctx, gw.CT, mats["Cinv"], chi_w, w_tau, args.prec)
+        mark(3)
+        out = gw.sigma_diag(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"], mats["S"],
+                            w_tau, fidx, args.prec, w_real=w_real)
+        mark(4)
+        return out
+
+    for _ in range(args.warmup):
+        step(psi)
+    torch.cuda.synchronize()
+
+    fl = flop_model(p.n_r, p.n_b, n_tau, p.n_chi, len(p.bands))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    l0 = ctx.launches
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(psi)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    launches = (ctx.launches - l0) // max(args.steps, 1)
+    clocks = sampler.stop()
+    t_dev = float(np.sum(times))
+    if dist is not None:
+        t = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+        dist.barrier()
+    value = world * fl["total"] * args.steps / t_dev / 1e12
+
+    # per-stage breakdown and the dominant stage's roofline (same stream, CUDA events)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    flush.zero_()
+    step(psi, ev)
+    torch.cuda.synchronize()
+    stage_ms = {name: ev[i].elapsed_time(ev[i + 1]) for i, name in
+                enumerate(["chi0_omega", "screen_W", "inverse_ct", "sigma_diag"])}
+    stage_flops = {"chi0_omega": fl["green"] / 2 + fl["fft"] / 2 + fl["ct"] / 2 + fl["hadamard"] / 3,
+                   "screen_W": fl["dyson"], "inverse_ct": fl["ct"] / 2,
+                   "sigma_diag": fl["green"] / 2 + fl["fft"] / 2 + fl["sigma"] + 2 * fl["hadamard"] / 3}
+    dom = max(stage_ms, key=stage_ms.get)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if args.prec in ("f16x3", "bf16x3") and dom in ("chi0_omega", "sigma_diag"):
+        roof = {"bound": "tensor", "peak": peaks.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (3 split products issued per flop)"}
+    else:
+        pk = sm_peak_fp32(sm_max) if args.prec != "fp64" else sm_peak_fp32(sm_max) / 64
+        roof = {"bound": "alu", "peak": pk, "unit": "TFLOP/s",
+                "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x %.0f MHz" % sm_max}
+    achieved = stage_flops[dom] / (stage_ms[dom] / 1e3) / 1e12
+    roof.update({"kernel_stage": dom, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None})
+
+    # end to end through the public API: orbitals copied from pinned host memory every step,
+    # Sigma read back to the host inside the call
+    e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        psi_dev = psi_h.to("cuda", non_blocking=True)
+        step(psi_dev)
+        e1.record(stream)
+        e1.synchronize()
+        e_times.append(e0.elapsed_time(e1) / 1e3)
+    t_e2e = float(np.sum(e_times))
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * fl["total"] * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(psi_h.numel() * psi_h.element_size()),
+           "d2h_bytes_per_step": int(len(p.bands) * (3 * n_tau + N_REAL) * 16)}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+            "data": "synthetic", "config": dict(workload, parallelism="replicas x%d" % world),
+            "stage_ms": stage_ms, "flops_per_step": fl, "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        f, t = oracle_sample(p)
+        line["cpu_baseline"] = {"value": f / t / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": "FP64 numpy oracle: G rows + chi product for 96 of %d rows at all %d tau, plus one 1536^2 screening solve (%.1f s)" % (p.n_r, n_tau, t)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * gw.h -- C ABI of libgw.so, the GB300 (sm_103a) hot path of the cubic-scaling
+ * space-time GW method (Liu, Kaltak, Klimes, Kresse, arXiv:1607.02859).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Grid      n[3] = (n1,n2,n3), N_r = n1*n2*n3, r index = (i1*n2+i2)*n3+i3,
+ *            fractional position (i1/n1, i2/n2, i3/n3).  lattice[9] holds the
+ *            three lattice vectors as rows (bohr); Omega = |det|, dV = Omega/N_r.
+ *  G set     gvec[j] = integer triple g with G = sum_d g_d b_d; fft_index[j] =
+ *            ((g1 mod n1)*n2 + g2 mod n2)*n3 + g3 mod n3 (see gw_g_set).
+ *  Complex   interleaved (re, im).  Element type is given by gw_prec:
+ *            GW_FP64 -> complex double (16 B); every other precision -> complex
+ *            float (8 B).  Layouts are row-major.
+ *  Orbitals  psi [N_b][N_r], band-major, normalised to dV sum_r |psi|^2 = 1.
+ *            eps_h [N_b] ascending on the host; eps[n_occ-1] < mu < eps[n_occ].
+ *  Pointers  without _h are DEVICE pointers owned by the caller; _h are host
+ *            pointers.  The library never frees caller memory.  Scratch comes
+ *            from the context: a grow-only device arena (cudaMalloc) that lives
+ *            until gw_ctx_destroy.
+ *  Streams   `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *            stream).  Calls are asynchronous on it unless documented as
+ *            synchronous (those returning results in host memory).
+ *  Errors    every call returns gw_status; nothing aborts or exits.  The message
+ *            of the last failure is gw_last_error(ctx).  A GW_ERR_CUDA from a
+ *            kernel fault leaves the CUDA context unusable (a CUDA property).
+ *  Threads   a context may be used by one host thread at a time.
+ */
+#ifndef GW_H_
+#define GW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gw_status {
+  GW_OK = 0,
+  GW_ERR_ARG = 1,         /* bad pointer, sign, ordering or enum value        */
+  GW_ERR_SHAPE = 2,       /* unsupported or inconsistent size                 */
+  GW_ERR_OOM = 3,         /* device scratch allocation failed                 */
+  GW_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed      */
+  GW_ERR_NUMERIC = 5,     /* non-positive pivot, vanishing Thiele denominator */
+  GW_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                    */
+  GW_ERR_UNSUPPORTED = 7  /* valid request this build does not implement      */
+} gw_status;
+
+typedef enum gw_prec {
+  GW_FP64 = 0,   /* every step in double precision, CUDA cores                    */
+  GW_FP32 = 1,   /* every step in single precision, CUDA cores                    */
+  GW_F16X3 = 2,  /* G and Sigma contractions as 3 fp16 split products on tcgen05  */
+                 /* tensor cores with FP32 accumulation; everything else as FP32  */
+  GW_BF16X3 = 3  /* same with bf16 splits                                         */
+} gw_prec;
+
+typedef enum gw_transform {
+  GW_CT = 0,     /* out[k] = sum_j M[k][j] in[j]        (Eqs. CT_FFT, CTX, CT_W) */
+  GW_ST = 1      /* out[k] = i * sum_j M[k][j] in[j]    (Eq. ST_FFT)             */
+} gw_transform;
+
+typedef struct gw_grid {
+  int n[3];
+  double lattice[9];
+} gw_grid;
+
+typedef struct gw_ctx gw_ctx;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to CUDA device `device`. *out receives it. */
+gw_status gw_ctx_create(int device, gw_ctx** out);
+/* Free the scratch arena and the context (synchronises the device). */
+gw_status gw_ctx_destroy(gw_ctx* ctx);
+/* Message of the last failure on ctx ("" if none); ctx may be NULL for failures
+ * of gw_ctx_create or of the host setup calls.  Valid until the next call. */
+const char* gw_last_error(const gw_ctx* ctx);
+/* Number of kernels this library launched through ctx since creation. */
+unsigned long long gw_ctx_launches(const gw_ctx* ctx);
+/* Current size of the context's device scratch arena in bytes. */
+size_t gw_ctx_scratch_bytes(const gw_ctx* ctx);
+/* ABI version (major*100 + minor). */
+int gw_version(void);
+
+/* ---------------------------------------------------------------- host setup
+ * Negligible host work (Sec. II.A.2-3); no GPU is touched. */
+
+/* The G set of chi and W (the cutoff sphere of Eq. FFTX1): the n_chi lowest
+ * integer triples g_d in [-n_d/2, n_d/2) ordered by (g1^2+g2^2+g3^2, g1, g2, g3).
+ * gvec_h [n_chi][3], fft_index_h [n_chi] (may be NULL).  1 <= n_chi <= N_r. */
+gw_status gw_g_set(const gw_grid* grid, int n_chi, int32_t* gvec_h, int32_t* fft_index_h);
+
+/* v^{1/2}(G) = sqrt(4 pi)/|G| of the symmetric Coulomb kernel (Eq. bareV,
+ * e = 1), with the G = 0 entry set to 0 (head and wings of W~ dropped). */
+gw_status gw_coulomb_sqrt(const gw_grid* grid, const int32_t* gvec_h, int n_chi,
+                          double* vhalf_h);
+
+/* Nonuniform cosine/sine transform matrices (Eqs. CT_FFT, cos_error_function,
+ * ST_FFT, sin_error_function, INV_CT_FFT) for given grids tau_h[n], omega_h[n]:
+ *   C[k][j] = gamma_kj cos(omega_k tau_j),  S[k][j] = lambda_kj sin(omega_k tau_j),
+ *   Cinv = C^{-1} (Eq. INV_CT_FFT).
+ * gamma_k (lambda_k) minimises, per omega_k, the relative error of the fitted
+ * Lorentzian 2x/(x^2+w^2) (2w/(x^2+w^2)) at n_x log-spaced x in [x_min, x_max]
+ * plus ridge^2 * n_x * |gamma_k|^2 (Householder QR, FP64).  fit_err_h[2]
+ * receives the largest relative error of the cosine and sine fits.  Any of the
+ * outputs may be NULL.  GW_ERR_NUMERIC if C is singular. */
+gw_status gw_fit_transform(int n, const double* tau_h, const double* omega_h,
+                           double x_min, double x_max, int n_x, double ridge,
+                           double* C_h, double* S_h, double* Cinv_h, double* fit_err_h);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Imaginary-time Green's functions for the rows r0 .. r0+n_rows-1 (Eqs.
+ * Green_occ, Green_unocc with energies measured from mu, tau > 0):
+ *   g_occ  [n_rows][N_r]:  sum_{i<n_occ}  psi_i(r) psi_i^*(r') exp(+(eps_i-mu) tau)
+ *   g_unocc[n_rows][N_r]:  sum_{a>=n_occ} psi_a(r) psi_a^*(r') exp(-(eps_a-mu) tau)
+ * Either output may be NULL.  The exponentials are formed in FP64 on the host
+ * and pre-scaled by their largest value, which is restored in FP64 afterwards.
+ * prec: GW_FP64/GW_FP32 SIMT GEMM; GW_F16X3/GW_BF16X3 tcgen05 split GEMM. */
+gw_status gw_green_tau(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
+                       const void* psi, const double* eps_h, double mu, double tau,
+                       int r0, int n_rows, gw_prec prec, void* g_occ, void* g_unocc,
+                       void* stream);
+
+/* Polarizability in real space and imaginary time (Eqs. chi_GG, chi_rr), spin
+ * factor 2, index order of G_occ(r,r') G_unocc(r',r):
+ *   chi[r][r'] = -2 g_occ[r][r'] * conj(g_unocc[r][r'])     (n_rows x n_cols)
+ * chi may alias g_unocc or g_occ. */
+gw_status gw_chi0_rtau(gw_ctx* ctx, int n_rows, int n_cols, gw_prec prec,
+                       const void* g_occ, const void* g_unocc, void* chi, void* stream);
+
+/* Fused G formation + Hadamard (Eqs. Green_occ/unocc and chi_rr in one pass;
+ * G_occ and G_unocc tiles never leave the chip when prec is a tensor-core
+ * precision).  chi [n_rows][N_r] as in gw_chi0_rtau. */
+gw_status gw_chi0_rtau_fused(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
+                             const void* psi, const double* eps_h, double mu, double tau,
+                             int r0, int n_rows, gw_prec prec, void* chi, void* stream);
+
+/* Two-step spatial transform within the cell (Eqs. FFTX1, FFTX2 forward; Eq.
+ * FFTW backward), 3-D mixed-radix FFTs on the n1 x n2 x n3 grid (radices 2, 3,
+ * 5; each n_d in {4,6,8,10,12,16,18,20,24,30,32,36,40,48}):
+ *  direction=+1 stage=1  in [n_rows][N_r] x(r,R')  -> out [n_rows][n_chi]
+ *                        X(r,G') = sum_R' x(r,R') exp(+i G'.R')           (FFTX1)
+ *  direction=+1 stage=2  in [N_r][n_chi] X(r,G')   -> out [n_chi][n_chi]
+ *                        (dV^2/Omega) sum_r exp(-i G.r) X(r,G')          (FFTX2)
+ *                        `in` is overwritten (used as the work buffer).
+ *  direction=-1 stage=2  in [n_chi][n_chi] W(G,G') -> out [N_r][n_chi]
+ *                        W(r,G') = sum_G exp(+i G.r) W(G,G')             (FFTW 1)
+ *  direction=-1 stage=1  in [n_rows][n_chi] W(r,G') -> out [n_rows][N_r]
+ *                        (1/Omega) sum_G' W(r,G') exp(-i G'.R')           (FFTW 2)
+ * r0 is only checked against N_r (rows are independent).  fft_index_h as
+ * returned by gw_g_set. */
+gw_status gw_rr_to_GG_fft(gw_ctx* ctx, const gw_grid* grid, int direction, int stage,
+                          int n_chi, const int32_t* fft_index_h, gw_prec prec, int r0,
+                          int n_rows, const void* in, void* out, void* stream);
+
+/* Nonuniform time <-> frequency transform of `elems` complex elements per slice
+ * (Eqs. CTX, CT_W, ST_FFT):  out[k][e] = (i if kind==GW_ST) sum_j M_h[k][j] in[j][e]
+ * for k, j < n.  M_h is FP64 on the host; the sums are accumulated in FP64.
+ * Use C for chi(tau)->chi(i omega), Cinv for W~(i omega)->W~(i tau).  in and
+ * out must not overlap. */
+gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double* M_h, size_t elems,
+                          gw_prec prec, const void* in, void* out, void* stream);
+
+/* Screened interaction at n_omega frequencies (Eqs. W_tot, bareV, die,
+ * W_correlated):  chi~ = v^{1/2} chi v^{1/2},  eps~ = 1 - chi~,
+ *   W~ = v^{1/2} (eps~^{-1} - 1) v^{1/2}
+ * by a blocked Cholesky factorisation eps~ = L L^H, L^{-1}, and
+ * eps~^{-1} = L^{-H} L^{-1} on CUDA cores (FP64 or FP32 by prec; the tensor-core
+ * precisions run this step in FP32).  chi_w, w_w [n_omega][n_chi][n_chi];
+ * chi_w must be Hermitian (only its lower triangle is read); w_w may equal
+ * chi_w (in place).  resid_h[n_omega] (may be NULL) receives the relative
+ * residual |eps~ X - chi~| / |chi~| of X = eps~^{-1} - 1 estimated in FP64 on
+ * 4 seeded probe vectors.  Synchronous (it reads back the pivot check).
+ * GW_ERR_NUMERIC if a pivot is not positive (eps~ not positive definite). */
+gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h,
+                      int n_omega, gw_prec prec, const void* chi_w, void* w_w,
+                      double* resid_h, void* stream);
+
+/* Diagonal correlation self-energy (Eqs. Sigma_occ, Sigma_rr and the first term
+ * of Sigma_occ_reduce; even/odd split Eqs. cos_sin_sigma_matrix1/2; CT+ST Eqs.
+ * sigma_r_w, cos_sin_sigma1/2; Thiele continuation Eqs. pade1, pade2):
+ * for every tau_j, W~(r,R',tau_j) is formed from w_tau [n][n_chi][n_chi]
+ * (Eq. FFTW), G_occ/G_unocc are recomputed, and
+ *   Sigma_unocc_nn(tau) = +dV^2 sum_{r,R'} psi_n^*(r) G_unocc(r,R') W~(r,R') psi_n(R')
+ *   Sigma_occ_nn(-tau)  = -dV^2 sum_{r,R'} psi_n^*(r) G_occ(r,R')   W~(r,R') psi_n(R')
+ * (real parts), then Sigma^c = (Su+So)/2, Sigma^s = (Su-So)/2 and
+ *   Sigma_nn(i omega_k) = sum_j C_kj Sigma^c(tau_j) + i sum_j S_kj Sigma^s(tau_j).
+ * Thiele coefficients through z_k = i omega_k, evaluated at the real
+ * frequencies w_real_h (measured from mu).
+ * bands_h [n_n]; tau_h, omega_h [n]; C_h, S_h [n][n].
+ * Outputs (host, FP64): sigma_tau_h [2][n_n][n] = (Su, So) (may be NULL);
+ * sigma_iw_h [n_n][n] complex; sigma_real_h [n_n][n_real] complex (may be NULL).
+ * Synchronous.  GW_ERR_NUMERIC if a Thiele denominator vanishes (|.| < 1e-300);
+ * the other bands are still returned. */
+gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
+                        const void* psi, const double* eps_h, double mu, const int32_t* bands_h,
+                        int n_n, int n, const double* tau_h, const double* omega_h,
+                        const double* C_h, const double* S_h, const void* w_tau, int n_chi,
+                        const int32_t* fft_index_h, gw_prec prec, double* sigma_tau_h,
+                        double* sigma_iw_h, const double* w_real_h, int n_real,
+                        double* sigma_real_h, void* stream);
+
+/* The chi0 chain of Fig. 1 steps (1)-(3) in one call: for every tau_j and every
+ * r-block of r_block rows, fused G formation + Hadamard + row transform into the
+ * chi(r,G',tau_j) slab (Eqs. chi_rr, FFTX1; chi(r,R') is never stored whole, as
+ * in Sec. II.C step (i)), then the column transform (Eq. FFTX2) and the cosine
+ * transform (Eq. CTX) fused into one pass:
+ *   chi_w [n][n_chi][n_chi] = chi0(G,G',i omega_k),  k < n.
+ * C_h [n][n] as from gw_fit_transform.  r_block <= 0 picks a default. */
+gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
+                        const void* psi, const double* eps_h, double mu, int n,
+                        const double* tau_h, const double* C_h, int n_chi,
+                        const int32_t* fft_index_h, gw_prec prec, int r_block, void* chi_w,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_H_ */

@@ -1,0 +1,361 @@
+// Screened interaction W~ (Eqs. W_tot, bareV, die, W_correlated).
+//
+// With chi~ = v^{1/2} chi v^{1/2} Hermitian negative semidefinite, the matrix
+// eps~ = 1 - chi~ is Hermitian positive definite with eps~ >= 1, so
+//   W~ = v^{1/2} (eps~^{-1} - 1) v^{1/2}
+// follows from a Cholesky factorisation without pivoting:
+//   1. eps~ = L L^H          (right-looking, 64-column panels; the trailing
+//                             Hermitian update is a GEMM)
+//   2. M = L^{-1}            (forward substitution on the identity, block row
+//                             by block row; the update of the rows below is a
+//                             GEMM that skips the zero upper part)
+//   3. eps~^{-1} = M^H M     (lower triangle, one GEMM)
+// i.e. N^3/2 complex multiply-adds in all, instead of the N^3 + N^3/6 of a
+// solve against chi~ with N right-hand sides.
+#include <cmath>
+
+#include "gw_kernels.h"
+
+namespace gw {
+
+constexpr int kNB = 64;
+
+template <typename T>
+__global__ void build_eps_kernel(const typename cpx<T>::t* __restrict__ chi, const double* __restrict__ vh,
+                                 typename cpx<T>::t* __restrict__ E, int n) {
+  using C = typename cpx<T>::t;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (b > a || b >= n) return;
+  const T vv = T(vh[a] * vh[b]);
+  C x = chi[(long)a * n + b];
+  C e = mk(-vv * x.x, -vv * x.y);
+  if (a == b) e.x += T(1);
+  E[(long)a * n + b] = e;
+}
+
+// Unblocked Cholesky of the kb x kb diagonal block (lower), in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) potrf_diag_kernel(typename cpx<T>::t* A, long lda, int kb, int* flag,
+                                                         int col0) {
+  using C = typename cpx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C (*S)[kNB + 1] = reinterpret_cast<C (*)[kNB + 1]>(smem_raw);    // [kNB][kNB+1]
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, c = e % kb;
+    S[i][c] = c <= i ? A[(long)i * lda + c] : mk(T(0), T(0));
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (threadIdx.x == 0) {
+      T d = S[j][j].x;
+      if (!(d > T(0))) {
+        if (atomicCAS(flag, 0, 1) == 0) flag[1] = col0 + j;
+        d = T(1);
+      }
+      S[j][j] = mk(sqrt(d), T(0));
+    }
+    __syncthreads();
+    const T piv = S[j][j].x;
+    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) S[i][j] = cscale(S[i][j], T(1) / piv);
+    __syncthreads();
+    const int m = kb - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, c = j + 1 + e % m;
+      if (c <= i) S[i][c] = csub(S[i][c], cmulc(S[i][j], S[c][j]));
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, c = e % kb;
+    if (c <= i) A[(long)i * lda + c] = S[i][c];
+  }
+}
+
+// Rows below the diagonal block: x L11^H = a  ->  x (row of L21).  64 rows per CTA.
+template <typename T>
+__global__ void __launch_bounds__(64) trsm_panel_kernel(typename cpx<T>::t* A, long lda, int k0, int kb, int rows) {
+  using C = typename cpx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* L = reinterpret_cast<C*>(smem_raw);          // [kb][kb+1]
+  C* X = L + kNB * (kNB + 1);                       // [kb][64]  (column c of thread t at X[c*64+t])
+  const int t = threadIdx.x;
+  for (int e = t; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, c = e % kb;
+    L[i * (kNB + 1) + c] = c <= i ? A[(long)(k0 + i) * lda + k0 + c] : mk(T(0), T(0));
+  }
+  const long row = (long)k0 + kb + (long)blockIdx.x * 64 + t;
+  const bool active = blockIdx.x * 64 + t < rows;
+  if (active)
+    for (int c = 0; c < kb; ++c) X[c * 64 + t] = A[row * lda + k0 + c];
+  __syncthreads();
+  if (!active) return;
+  for (int c = 0; c < kb; ++c) {
+    C s = X[c * 64 + t];
+    for (int p = 0; p < c; ++p) s = csub(s, cmulc(X[p * 64 + t], L[c * (kNB + 1) + p]));
+    X[c * 64 + t] = cscale(s, T(1) / L[c * (kNB + 1) + c].x);
+  }
+  for (int c = 0; c < kb; ++c) A[row * lda + k0 + c] = X[c * 64 + t];
+}
+
+template <typename T>
+__global__ void identity_kernel(typename cpx<T>::t* M, int n) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)n * n) return;
+  const long a = e / n, b = e % n;
+  M[e] = mk(T(a == b ? 1 : 0), T(0));
+}
+
+// Y = L_ii^{-1} Y for the block rows k0..k0+kb-1 and columns 0..ncols-1 of Y.
+template <typename T>
+__global__ void __launch_bounds__(64) trsm_left_kernel(const typename cpx<T>::t* Lm, long ldl,
+                                                      typename cpx<T>::t* Y, long ldy, int k0, int kb, int ncols) {
+  using C = typename cpx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* L = reinterpret_cast<C*>(smem_raw);
+  C* X = L + kNB * (kNB + 1);
+  const int t = threadIdx.x;
+  for (int e = t; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, c = e % kb;
+    L[i * (kNB + 1) + c] = c <= i ? Lm[(long)(k0 + i) * ldl + k0 + c] : mk(T(0), T(0));
+  }
+  const int col = blockIdx.x * 64 + t;
+  const bool active = col < ncols;
+  if (active)
+    for (int r = 0; r < kb; ++r) X[r * 64 + t] = Y[(long)(k0 + r) * ldy + col];
+  __syncthreads();
+  if (!active) return;
+  for (int r = 0; r < kb; ++r) {
+    C s = X[r * 64 + t];
+    for (int p = 0; p < r; ++p) s = csub(s, cmul(L[r * (kNB + 1) + p], X[p * 64 + t]));
+    X[r * 64 + t] = cscale(s, T(1) / L[r * (kNB + 1) + r].x);
+  }
+  for (int r = 0; r < kb; ++r) Y[(long)(k0 + r) * ldy + col] = X[r * 64 + t];
+}
+
+// W~[a][b] = v_a (Einv[a][b] - delta_ab) v_b, both triangles from the lower one.
+template <typename T>
+__global__ void finalize_kernel(const typename cpx<T>::t* __restrict__ Einv, const double* __restrict__ vh,
+                                typename cpx<T>::t* __restrict__ W, int n) {
+  using C = typename cpx<T>::t;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (b > a || b >= n) return;
+  C x = Einv[(long)a * n + b];
+  if (a == b) x.x -= T(1);
+  const T vv = T(vh[a] * vh[b]);
+  x = cscale(x, vv);
+  W[(long)a * n + b] = x;
+  if (a != b) W[(long)b * n + a] = cconj(x);
+}
+
+// y = F z in FP64 for the Hermitian F given by its lower triangle Mlow:
+// F[a][b] = s_a s_b (Mlow or conj of the mirrored entry) - sub * delta_ab.
+template <typename T>
+__global__ void __launch_bounds__(256) hemv_probe_kernel(const typename cpx<T>::t* __restrict__ Mlow,
+                                                         const double* __restrict__ sv, double sub,
+                                                         const double2* __restrict__ z, double2* __restrict__ y,
+                                                         int n) {
+  const int a = blockIdx.x;
+  double re = 0, im = 0;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    double2 m;
+    if (b <= a) {
+      auto v = Mlow[(long)a * n + b];
+      m = make_double2(v.x, v.y);
+    } else {
+      auto v = Mlow[(long)b * n + a];
+      m = make_double2(v.x, -v.y);
+    }
+    const double s = sv ? sv[a] * sv[b] : 1.0;
+    m.x *= s;
+    m.y *= s;
+    if (a == b) m.x -= sub;
+    re += m.x * z[b].x - m.y * z[b].y;
+    im += m.x * z[b].y + m.y * z[b].x;
+  }
+  __shared__ double sr[256], si[256];
+  sr[threadIdx.x] = re;
+  si[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sr[threadIdx.x] += sr[threadIdx.x + w];
+      si[threadIdx.x] += si[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) y[a] = make_double2(sr[0], si[0]);
+}
+
+template <typename T>
+static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, const double* dvh, void* E, void* Mi,
+                            void* W, double2* probe, double* resid_h, cudaStream_t st) {
+  using C = typename cpx<T>::t;
+  gw_status rc;
+  C* e = static_cast<C*>(E);
+  C* m = static_cast<C*>(Mi);
+  const dim3 tb(128), gb((n + 127) / 128, n);
+  build_eps_kernel<T><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), dvh, e, n);
+  if ((rc = launch_check(ctx, "build_eps_kernel"))) return rc;
+  const size_t tsm = sizeof(C) * (kNB * (kNB + 1) + kNB * 64);
+  const size_t psm = sizeof(C) * kNB * (kNB + 1);
+  if (tsm > 48 * 1024) {
+    cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+    cudaFuncSetAttribute(trsm_left_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+  }
+  if (psm > 48 * 1024)
+    cudaFuncSetAttribute(potrf_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+  // 1. eps~ = L L^H
+  for (int k0 = 0; k0 < n; k0 += kNB) {
+    const int kb = std::min(kNB, n - k0);
+    potrf_diag_kernel<T><<<1, 256, psm, st>>>(e + (long)k0 * n + k0, n, kb, ctx->dflag, k0);
+    if ((rc = launch_check(ctx, "potrf_diag_kernel"))) return rc;
+    const int rows = n - k0 - kb;
+    if (rows <= 0) break;
+    trsm_panel_kernel<T><<<(rows + 63) / 64, 64, tsm, st>>>(e, n, k0, kb, rows);
+    if ((rc = launch_check(ctx, "trsm_panel_kernel"))) return rc;
+    GemmArgs g{};
+    g.M = rows;
+    g.N = rows;
+    g.K = kb;
+    g.alpha_re = -1;
+    g.beta = 1;
+    g.A = e + (long)(k0 + kb) * n + k0;
+    g.lda = n;
+    g.a_km = 0;
+    g.B = e + (long)(k0 + kb) * n + k0;
+    g.ldb = n;
+    g.b_nk = 1;
+    g.b_conj = true;
+    g.C = e + (long)(k0 + kb) * n + k0 + kb;
+    g.ldc = n;
+    g.tri = 1;
+    if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
+  }
+  // 2. M = L^{-1}
+  identity_kernel<T><<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(m, n);
+  if ((rc = launch_check(ctx, "identity_kernel"))) return rc;
+  for (int k0 = 0; k0 < n; k0 += kNB) {
+    const int kb = std::min(kNB, n - k0);
+    const int ncols = k0 + kb;
+    trsm_left_kernel<T><<<(ncols + 63) / 64, 64, tsm, st>>>(e, n, m, n, k0, kb, ncols);
+    if ((rc = launch_check(ctx, "trsm_left_kernel"))) return rc;
+    const int rows = n - k0 - kb;
+    if (rows <= 0) break;
+    GemmArgs g{};
+    g.M = rows;
+    g.N = ncols;
+    g.K = kb;
+    g.alpha_re = -1;
+    g.beta = 1;
+    g.A = e + (long)(k0 + kb) * n + k0;
+    g.lda = n;
+    g.B = m + (long)k0 * n;
+    g.ldb = n;
+    g.C = m + (long)(k0 + kb) * n;
+    g.ldc = n;
+    if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
+  }
+  // 3. eps~^{-1} = M^H M (lower) into E
+  {
+    GemmArgs g{};
+    g.M = n;
+    g.N = n;
+    g.K = n;
+    g.alpha_re = 1;
+    g.beta = 0;
+    g.A = m;
+    g.lda = n;
+    g.a_km = 1;
+    g.a_conj = true;
+    g.B = m;
+    g.ldb = n;
+    g.C = e;
+    g.ldc = n;
+    g.tri = 2;
+    if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
+  }
+  if (resid_h) {
+    // |eps~ X z - chi~ z| / |chi~ z| over 4 probes, X = eps~^{-1} - 1 (before chi may be overwritten)
+    double num = 0, den = 0;
+    std::vector<double2> hz(n), hu(n), hw(n), hc(n);
+    for (int q = 0; q < 4; ++q) {
+      uint64_t sd = 0x9E3779B97F4A7C15ull * (q + 1);
+      for (int i = 0; i < n; ++i) {
+        sd = sd * 6364136223846793005ull + 1442695040888963407ull;
+        double u1 = ((sd >> 11) & ((1ull << 53) - 1)) / 9007199254740992.0;
+        sd = sd * 6364136223846793005ull + 1442695040888963407ull;
+        double u2 = ((sd >> 11) & ((1ull << 53) - 1)) / 9007199254740992.0;
+        hz[i] = make_double2(u1 - 0.5, u2 - 0.5);
+      }
+      double2 *z = probe, *u = probe + n, *w = probe + 2 * n, *c = probe + 3 * n;
+      if ((rc = upload(ctx, z, hz.data(), sizeof(double2) * n, st))) return rc;
+      hemv_probe_kernel<T><<<n, 256, 0, st>>>(e, nullptr, 1.0, z, u, n);                       // u = X z
+      hemv_probe_kernel<T><<<n, 256, 0, st>>>(static_cast<const C*>(chi), dvh, 0.0, u, w, n);  // w = chi~ u
+      hemv_probe_kernel<T><<<n, 256, 0, st>>>(static_cast<const C*>(chi), dvh, 0.0, z, c, n);  // c = chi~ z
+      if ((rc = launch_check(ctx, "hemv_probe_kernel"))) return rc;
+      ctx->launches += 2;
+      if ((rc = cuda_check(ctx, cudaMemcpyAsync(hu.data(), u, sizeof(double2) * n, cudaMemcpyDeviceToHost, st), "probe")))
+        return rc;
+      cudaMemcpyAsync(hw.data(), w, sizeof(double2) * n, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(hc.data(), c, sizeof(double2) * n, cudaMemcpyDeviceToHost, st);
+      if ((rc = cuda_check(ctx, cudaStreamSynchronize(st), "probe sync"))) return rc;
+      for (int i = 0; i < n; ++i) {
+        const double rr = hu[i].x - hw[i].x - hc[i].x, ri = hu[i].y - hw[i].y - hc[i].y;
+        num += rr * rr + ri * ri;
+        den += hc[i].x * hc[i].x + hc[i].y * hc[i].y;
+      }
+    }
+    *resid_h = den > 0 ? std::sqrt(num / den) : 0.0;
+  }
+  finalize_kernel<T><<<gb, tb, 0, st>>>(e, dvh, static_cast<C*>(W), n);
+  return launch_check(ctx, "finalize_kernel");
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h, int n_omega,
+                                 gw_prec prec, const void* chi_w, void* w_w, double* resid_h, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  GridInfo g;
+  gw_status st = grid_info(ctx, grid, &g);
+  if (st) return st;
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  if (n_chi < 1 || n_chi > g.nr || n_chi > 65535) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_chi <= min(N_r, 65535)");
+  if (n_omega < 0) return fail(ctx, GW_ERR_SHAPE, "n_omega < 0");
+  if (!gvec_h || !chi_w || !w_w) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  cudaStream_t s = as_stream(stream);
+  std::vector<double> vh(n_chi);
+  if ((st = gw_coulomb_sqrt(grid, gvec_h, n_chi, vh.data()))) return fail(ctx, st, gw_last_error(nullptr));
+  const size_t es = csize(prec);
+  const size_t nn = (size_t)n_chi * n_chi;
+  Carver probe(nullptr);
+  probe.take<double>(n_chi);
+  probe.take<char>(nn * es);
+  probe.take<char>(nn * es);
+  probe.take<double2>(4 * (size_t)n_chi);
+  if ((st = reserve(ctx, probe.off))) return st;
+  Carver cv(ctx->arena);
+  double* dvh = cv.take<double>(n_chi);
+  void* E = cv.take<char>(nn * es);
+  void* M = cv.take<char>(nn * es);
+  double2* pr = cv.take<double2>(4 * (size_t)n_chi);
+  if ((st = upload(ctx, dvh, vh.data(), sizeof(double) * n_chi, s))) return st;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 2 * sizeof(int), s), "memset flag"))) return st;
+  for (int k = 0; k < n_omega; ++k) {
+    const char* in = static_cast<const char*>(chi_w) + k * nn * es;
+    char* out = static_cast<char*>(w_w) + k * nn * es;
+    st = is_fp64(prec) ? screen_one<double>(ctx, prec, n_chi, in, dvh, E, M, out, pr, resid_h ? resid_h + k : nullptr, s)
+                       : screen_one<float>(ctx, prec, n_chi, in, dvh, E, M, out, pr, resid_h ? resid_h + k : nullptr, s);
+    if (st) return st;
+  }
+  int flag[2] = {0, 0};
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(flag, ctx->dflag, sizeof(flag), cudaMemcpyDeviceToHost, s), "flag")))
+    return st;
+  if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
+  if (flag[0]) return fail(ctx, GW_ERR_NUMERIC, "eps~ not positive definite at column " + std::to_string(flag[1]));
+  return GW_OK;
+}

@@ -1,0 +1,437 @@
+// Spatial transforms within the cell (Eqs. FFTX1, FFTX2, FFTW), the
+// real-space product of Eq. chi_rr fused into the row transform, and the
+// nonuniform time/frequency transforms (Eqs. CTX, CT_W, ST_FFT).
+//
+// Data stay in HBM as row-major complex matrices whose row index is a grid
+// point r = (i1*n2+i2)*n3+i3 or a G-set index, and whose column index is a grid
+// point R' or a G' of the set.
+//  * row kernels: one CTA per row; the N_r-point row is staged in shared memory
+//    (odd-padded pencil stride, so every pencil pass is bank-conflict free) and
+//    transformed by three passes of fully unrolled register FFTs.
+//  * column kernels: the transform runs over the row index for a chunk of
+//    contiguous columns, so every HBM access is a coalesced row segment:
+//    a "plane" kernel does the (i2,i3) 2-D FFT through shared memory and a
+//    "line" kernel the i1 1-D FFT in registers.  The last i1 pass of the chi
+//    chain also applies the cosine transform over all tau (Eq. CTX) before
+//    anything is written, saving a full read+write of chi(G,G',tau).
+#include "gw_common.cuh"
+#include "gw_kernels.h"
+#include "gw_fft.cuh"
+
+namespace gw {
+
+bool grid_supported(int a, int b, int c) {
+#define X(x, y, z) \
+  if (a == x && b == y && c == z) return true;
+  GW_GRIDS(X)
+#undef X
+  return false;
+}
+
+// MODE 0: x = scale * a * conj(b) (Eq. chi_rr), forward (+i), gather the G' set.
+// MODE 1: x = a, forward (+i), gather.            (Eq. FFTX1)
+// MODE 2: scatter a[j] to fft positions, backward (-i), times scale.   (Eq. FFTW, 2nd step)
+template <typename T, int N1, int N2, int N3, int MODE>
+__global__ void __launch_bounds__(256) row_fft_kernel(const typename cpx<T>::t* __restrict__ a,
+                                                      const typename cpx<T>::t* __restrict__ b, long lda,
+                                                      typename cpx<T>::t* __restrict__ out, long ldo,
+                                                      const int* __restrict__ map, int n_chi, T scale) {
+  using C = typename cpx<T>::t;
+  using L = RowLayout<N1, N2, N3>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const long row = blockIdx.x;
+  if (MODE == 2) {
+    for (int e = threadIdx.x; e < L::TOT; e += blockDim.x) s[e] = mk(T(0), T(0));
+    __syncthreads();
+    const C* src = a + row * lda;
+    for (int j = threadIdx.x; j < n_chi; j += blockDim.x) s[L::pos(map[j])] = src[j];
+  } else {
+    const C* pa = a + row * lda;
+    const C* pb = b + row * lda;
+    for (int r = threadIdx.x; r < L::NR; r += blockDim.x) {
+      C v = pa[r];
+      if (MODE == 0) v = cscale(cmulc(v, pb[r]), scale);
+      s[L::pos(r)] = v;
+    }
+  }
+  __syncthreads();
+  fft3_smem<N1, N2, N3, MODE == 2 ? -1 : +1>(s);
+  C* dst = out + row * ldo;
+  if (MODE == 2) {
+    for (int r = threadIdx.x; r < L::NR; r += blockDim.x) dst[r] = cscale(s[L::pos(r)], scale);
+  } else {
+    for (int j = threadIdx.x; j < n_chi; j += blockDim.x) dst[j] = s[L::pos(map[j])];
+  }
+}
+
+constexpr int kPlaneW = 16;
+
+// In-place 2-D FFT over (i2, i3) of the rows of plane i1 = blockIdx.y, for 16
+// contiguous columns per CTA.
+template <typename T, int N2, int N3, int DIR>
+__global__ void __launch_bounds__(256) col_plane_kernel(typename cpx<T>::t* __restrict__ buf, long ld, int ncols,
+                                                        T scale) {
+  using C = typename cpx<T>::t;
+  constexpr int W = kPlaneW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const long i1 = blockIdx.y;
+  const int c0 = blockIdx.x * W;
+  C* base = buf + i1 * (N2 * N3) * ld + c0;
+  for (int e = threadIdx.x; e < N2 * N3 * W; e += blockDim.x) {
+    const int rr = e / W, w = e - rr * W;
+    s[e] = (c0 + w < ncols) ? base[rr * ld + w] : mk(T(0), T(0));
+  }
+  __syncthreads();
+  pencil_pass<N3, DIR>(s, N2 * W, W, [](int p) { return (p / W) * (N3 * W) + (p % W); });
+  __syncthreads();
+  pencil_pass<N2, DIR>(s, N3 * W, N3 * W, [](int p) { return (p / W) * W + (p % W); });
+  __syncthreads();
+  for (int e = threadIdx.x; e < N2 * N3 * W; e += blockDim.x) {
+    const int rr = e / W, w = e - rr * W;
+    if (c0 + w < ncols) base[rr * ld + w] = cscale(s[e], scale);
+  }
+}
+
+// In-place 1-D FFT over i1 for the column c and the (i2,i3) pair blockIdx.y.
+// GATHER_IN: read row inv[pos] of `in` (zero if -1) instead of buf[pos].
+// SCATTER_OUT: write row inv[pos] of `out` (skip if -1) instead of buf[pos].
+template <typename T, int N1, int DIR, bool GATHER_IN, bool SCATTER_OUT>
+__global__ void __launch_bounds__(256) col_line_kernel(const typename cpx<T>::t* __restrict__ in, long ldi,
+                                                       typename cpx<T>::t* __restrict__ out, long ldo, int ncols,
+                                                       int plane, const int* __restrict__ inv, T scale) {
+  using C = typename cpx<T>::t;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i23 = blockIdx.y;
+  if (c >= ncols) return;
+  C x[N1];
+#pragma unroll
+  for (int i1 = 0; i1 < N1; ++i1) {
+    const long pos = (long)i1 * plane + i23;
+    if (GATHER_IN) {
+      const int j = inv[pos];
+      x[i1] = j >= 0 ? in[(long)j * ldi + c] : mk(T(0), T(0));
+    } else {
+      x[i1] = in[pos * ldi + c];
+    }
+  }
+  RegFFT<N1, DIR>::run(x);
+#pragma unroll
+  for (int i1 = 0; i1 < N1; ++i1) {
+    const long pos = (long)i1 * plane + i23;
+    if (SCATTER_OUT) {
+      const int j = inv[pos];
+      if (j >= 0) out[(long)j * ldo + c] = cscale(x[i1], scale);
+    } else {
+      out[pos * ldo + c] = cscale(x[i1], scale);
+    }
+  }
+}
+
+// Last column pass of the chi chain: i1 FFT (-i) of every tau slab, then
+// out[k][inv[pos]][c] = sum_j cw[k][j] * slab_j(pos, c)  (Eq. CTX with the
+// dV^2/Omega of Eq. FFTX2 folded into cw).  32 columns x 8 warps per CTA.
+template <typename T, int N1>
+__global__ void __launch_bounds__(256) col_line_ct_kernel(const typename cpx<T>::t* __restrict__ slabs,
+                                                          long slab_stride, long ld, int ntau,
+                                                          const T* __restrict__ cw, int nw,
+                                                          typename cpx<T>::t* __restrict__ out, long out_slice,
+                                                          long ldo, const int* __restrict__ inv, int plane,
+                                                          int ncols) {
+  using C = typename cpx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);                       // [ntau][N1][32]
+  T* w = reinterpret_cast<T*>(s + (size_t)ntau * N1 * 32);      // [nw][ntau]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const int i23 = blockIdx.y;
+  for (int e = threadIdx.x; e < nw * ntau; e += blockDim.x) w[e] = cw[e];
+  for (int j = warp; j < ntau; j += 8) {
+    C x[N1];
+    const C* src = slabs + (long)j * slab_stride;
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1)
+      x[i1] = c < ncols ? src[((long)i1 * plane + i23) * ld + c] : mk(T(0), T(0));
+    RegFFT<N1, -1>::run(x);
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) s[(j * N1 + i1) * 32 + lane] = x[i1];
+  }
+  __syncthreads();
+  if (c >= ncols) return;
+  for (int q = warp; q < nw * N1; q += 8) {
+    const int k = q / N1, i1 = q - k * N1;
+    const int row = inv[(long)i1 * plane + i23];
+    if (row < 0) continue;
+    T re = 0, im = 0;
+    for (int j = 0; j < ntau; ++j) {
+      const C v = s[(j * N1 + i1) * 32 + lane];
+      const T wt = w[k * ntau + j];
+      re += wt * v.x;
+      im += wt * v.y;
+    }
+    out[(long)k * out_slice + (long)row * ldo + c] = mk(re, im);
+  }
+}
+
+// out[k][e] = (i if ST) sum_j M[k][j] in[j][e]
+template <typename T, bool ST>
+__global__ void __launch_bounds__(256) ct_kernel(const typename cpx<T>::t* __restrict__ in,
+                                                 typename cpx<T>::t* __restrict__ out, size_t elems, int n,
+                                                 const T* __restrict__ M) {
+  using C = typename cpx<T>::t;
+  __shared__ T w[32 * 32];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) w[e] = M[e];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < elems; e += (size_t)gridDim.x * blockDim.x) {
+    C x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < n) x[j] = in[(size_t)j * elems + e];
+    for (int k = 0; k < n; ++k) {
+      T re = 0, im = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < n) {
+          re += w[k * n + j] * x[j].x;
+          im += w[k * n + j] * x[j].y;
+        }
+      out[(size_t)k * elems + e] = ST ? mk(-im, re) : mk(re, im);
+    }
+  }
+}
+
+template <typename T>
+__global__ void hadamard_kernel(const typename cpx<T>::t* __restrict__ a, const typename cpx<T>::t* __restrict__ b,
+                                typename cpx<T>::t* out, size_t count, T scale) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = cscale(cmulc(a[e], b[e]), scale);
+}
+
+// ---------------------------------------------------------------------- launchers
+
+template <typename K>
+static gw_status set_smem(gw_ctx* ctx, K kernel, size_t bytes) {
+  if (bytes > 227 * 1024) return fail(ctx, GW_ERR_UNSUPPORTED, "shared-memory tile too large for this grid/precision");
+  if (bytes > 48 * 1024)
+    return cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+                      "cudaFuncSetAttribute");
+  return GW_OK;
+}
+
+template <typename T, int N1, int N2, int N3>
+struct GridOps {
+  using C = typename cpx<T>::t;
+  static gw_status row(gw_ctx* ctx, int mode, const void* a, const void* b, long lda, void* out, long ldo,
+                       const int* map, int n_chi, int n_rows, double scale, cudaStream_t st) {
+    const size_t bytes = RowLayout<N1, N2, N3>::TOT * sizeof(C);
+    auto go = [&](auto kernel) -> gw_status {
+      gw_status s = set_smem(ctx, kernel, bytes);
+      if (s) return s;
+      kernel<<<n_rows, 256, bytes, st>>>((const C*)a, (const C*)b, lda, (C*)out, ldo, map, n_chi, (T)scale);
+      return launch_check(ctx, "row_fft_kernel");
+    };
+    if (mode == 0) return go(row_fft_kernel<T, N1, N2, N3, 0>);
+    if (mode == 1) return go(row_fft_kernel<T, N1, N2, N3, 1>);
+    return go(row_fft_kernel<T, N1, N2, N3, 2>);
+  }
+  static gw_status plane(gw_ctx* ctx, int dir, void* buf, long ld, int ncols, double scale, cudaStream_t st) {
+    const size_t bytes = (size_t)N2 * N3 * kPlaneW * sizeof(C);
+    dim3 grid((ncols + kPlaneW - 1) / kPlaneW, N1);
+    auto go = [&](auto kernel) -> gw_status {
+      gw_status s = set_smem(ctx, kernel, bytes);
+      if (s) return s;
+      kernel<<<grid, 256, bytes, st>>>((C*)buf, ld, ncols, (T)scale);
+      return launch_check(ctx, "col_plane_kernel");
+    };
+    return dir > 0 ? go(col_plane_kernel<T, N2, N3, +1>) : go(col_plane_kernel<T, N2, N3, -1>);
+  }
+  static gw_status line(gw_ctx* ctx, int dir, int variant, const void* in, long ldi, void* out, long ldo, int ncols,
+                        const int* inv, double scale, cudaStream_t st) {
+    dim3 grid((ncols + 127) / 128, N2 * N3);
+    auto go = [&](auto kernel) -> gw_status {
+      kernel<<<grid, 128, 0, st>>>((const C*)in, ldi, (C*)out, ldo, ncols, N2 * N3, inv, (T)scale);
+      return launch_check(ctx, "col_line_kernel");
+    };
+    // variant 0: in place / plain; 1: gather rows of `in` through inv; 2: scatter rows of `out` through inv
+    if (variant == 0) return dir > 0 ? go(col_line_kernel<T, N1, +1, false, false>)
+                                     : go(col_line_kernel<T, N1, -1, false, false>);
+    if (variant == 1) return dir > 0 ? go(col_line_kernel<T, N1, +1, true, false>)
+                                     : go(col_line_kernel<T, N1, -1, true, false>);
+    return dir > 0 ? go(col_line_kernel<T, N1, +1, false, true>) : go(col_line_kernel<T, N1, -1, false, true>);
+  }
+  static gw_status line_ct(gw_ctx* ctx, const void* slabs, long slab_stride, long ld, int ntau, const void* cw, int nw,
+                           void* out, long out_slice, long ldo, const int* inv, int ncols, cudaStream_t st) {
+    const size_t bytes = (size_t)ntau * N1 * 32 * sizeof(C) + (size_t)nw * ntau * sizeof(T);
+    auto kernel = col_line_ct_kernel<T, N1>;
+    gw_status s = set_smem(ctx, kernel, bytes);
+    if (s) return s;
+    dim3 grid((ncols + 31) / 32, N2 * N3);
+    kernel<<<grid, 256, bytes, st>>>((const C*)slabs, slab_stride, ld, ntau, (const T*)cw, nw, (C*)out, out_slice,
+                                     ldo, inv, N2 * N3, ncols);
+    return launch_check(ctx, "col_line_ct_kernel");
+  }
+};
+
+template <typename T, typename F>
+static bool with_grid(const GridInfo& g, F&& f) {
+#define X(a, b, c)                                 \
+  if (g.n1 == a && g.n2 == b && g.n3 == c) {       \
+    f(GridOps<T, a, b, c>{});                      \
+    return true;                                   \
+  }
+  GW_GRIDS(X)
+#undef X
+  return false;
+}
+
+#define GW_DISPATCH(prec, g, BODY)                                                              \
+  gw_status rc = GW_OK;                                                                         \
+  bool found = is_fp64(prec) ? with_grid<double>(g, [&](auto ops) { using O = decltype(ops); BODY; }) \
+                             : with_grid<float>(g, [&](auto ops) { using O = decltype(ops); BODY; });  \
+  if (!found) return fail(ctx, GW_ERR_UNSUPPORTED, "no FFT kernels compiled for this grid");     \
+  return rc;
+
+gw_status launch_row_fft(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int mode, const void* a, const void* b,
+                         long lda, void* out, long ldo, const int* map, int n_chi, int n_rows, double scale,
+                         cudaStream_t st) {
+  if (n_rows <= 0) return GW_OK;
+  GW_DISPATCH(prec, g, rc = O::row(ctx, mode, a, b, lda, out, ldo, map, n_chi, n_rows, scale, st))
+}
+
+gw_status launch_col_plane(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, void* buf, long ld, int ncols,
+                           double scale, cudaStream_t st) {
+  GW_DISPATCH(prec, g, rc = O::plane(ctx, dir, buf, ld, ncols, scale, st))
+}
+
+gw_status launch_col_line(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, int variant, const void* in,
+                          long ldi, void* out, long ldo, int ncols, const int* inv, double scale, cudaStream_t st) {
+  GW_DISPATCH(prec, g, rc = O::line(ctx, dir, variant, in, ldi, out, ldo, ncols, inv, scale, st))
+}
+
+gw_status launch_col_line_ct(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* slabs, long slab_stride,
+                             long ld, int ntau, const void* cw, int nw, void* out, long out_slice, long ldo,
+                             const int* inv, int ncols, cudaStream_t st) {
+  GW_DISPATCH(prec, g,
+              rc = O::line_ct(ctx, slabs, slab_stride, ld, ntau, cw, nw, out, out_slice, ldo, inv, ncols, st))
+}
+
+gw_status launch_ct(gw_ctx* ctx, gw_prec prec, bool st_kind, int n, const void* dM, size_t elems, const void* in,
+                    void* out, cudaStream_t st) {
+  if (elems == 0) return GW_OK;
+  int blocks = (int)std::min<size_t>((elems + 255) / 256, (size_t)ctx->num_sms * 8);
+  if (is_fp64(prec)) {
+    if (st_kind) ct_kernel<double, true><<<blocks, 256, 0, st>>>((const double2*)in, (double2*)out, elems, n, (const double*)dM);
+    else ct_kernel<double, false><<<blocks, 256, 0, st>>>((const double2*)in, (double2*)out, elems, n, (const double*)dM);
+  } else {
+    if (st_kind) ct_kernel<float, true><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, elems, n, (const float*)dM);
+    else ct_kernel<float, false><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, elems, n, (const float*)dM);
+  }
+  return launch_check(ctx, "ct_kernel");
+}
+
+gw_status launch_hadamard(gw_ctx* ctx, gw_prec prec, size_t count, const void* a, const void* b, double scale,
+                          void* out, cudaStream_t st) {
+  if (count == 0) return GW_OK;
+  int blocks = (int)std::min<size_t>((count + 255) / 256, (size_t)ctx->num_sms * 16);
+  if (is_fp64(prec))
+    hadamard_kernel<double><<<blocks, 256, 0, st>>>((const double2*)a, (const double2*)b, (double2*)out, count, scale);
+  else
+    hadamard_kernel<float><<<blocks, 256, 0, st>>>((const float2*)a, (const float2*)b, (float2*)out, count, (float)scale);
+  return launch_check(ctx, "hadamard_kernel");
+}
+
+// Upload a host array into arena memory (pageable copy; the host buffer may be
+// released on return).
+gw_status upload(gw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return GW_OK;
+  return cuda_check(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload");
+}
+
+gw_status index_maps(gw_ctx* ctx, const GridInfo& g, const int32_t* fft_index_h, int n_chi, std::vector<int>& map,
+                     std::vector<int>& inv) {
+  if (!fft_index_h) return fail(ctx, GW_ERR_ARG, "fft_index_h is NULL");
+  if (n_chi < 1 || n_chi > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_chi <= N_r");
+  map.assign(fft_index_h, fft_index_h + n_chi);
+  inv.assign(g.nr, -1);
+  for (int j = 0; j < n_chi; ++j) {
+    if (map[j] < 0 || map[j] >= g.nr) return fail(ctx, GW_ERR_ARG, "fft_index out of range");
+    if (inv[map[j]] >= 0) return fail(ctx, GW_ERR_ARG, "fft_index has duplicates");
+    inv[map[j]] = j;
+  }
+  return GW_OK;
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" gw_status gw_chi0_rtau(gw_ctx* ctx, int n_rows, int n_cols, gw_prec prec, const void* g_occ,
+                                  const void* g_unocc, void* chi, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  if (n_rows < 0 || n_cols < 0) return fail(ctx, GW_ERR_SHAPE, "negative size");
+  if ((size_t)n_rows * n_cols == 0) return GW_OK;
+  if (!g_occ || !g_unocc || !chi) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  return launch_hadamard(ctx, prec, (size_t)n_rows * n_cols, g_occ, g_unocc, -2.0, chi, as_stream(stream));
+}
+
+extern "C" gw_status gw_rr_to_GG_fft(gw_ctx* ctx, const gw_grid* grid, int direction, int stage, int n_chi,
+                                     const int32_t* fft_index_h, gw_prec prec, int r0, int n_rows, const void* in,
+                                     void* out, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  GridInfo g;
+  gw_status st = grid_info(ctx, grid, &g);
+  if (st) return st;
+  if (!grid_supported(g.n1, g.n2, g.n3)) return fail(ctx, GW_ERR_UNSUPPORTED, "no FFT kernels compiled for this grid");
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  if (direction != 1 && direction != -1) return fail(ctx, GW_ERR_ARG, "direction must be +1 or -1");
+  if (stage != 1 && stage != 2) return fail(ctx, GW_ERR_ARG, "stage must be 1 or 2");
+  if (!in || !out) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  std::vector<int> map, inv;
+  if ((st = index_maps(ctx, g, fft_index_h, n_chi, map, inv))) return st;
+  if (stage == 1 && (n_rows < 0 || r0 < 0 || r0 + n_rows > g.nr)) return fail(ctx, GW_ERR_SHAPE, "rows out of range");
+  cudaStream_t s = as_stream(stream);
+  Carver probe(nullptr);
+  probe.take<int>(n_chi);
+  probe.take<int>(g.nr);
+  if ((st = reserve(ctx, probe.off))) return st;
+  Carver cv(ctx->arena);
+  int* dmap = cv.take<int>(n_chi);
+  int* dinv = cv.take<int>(g.nr);
+  if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
+  if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
+  if (stage == 1) {
+    if (direction > 0) return launch_row_fft(ctx, g, prec, 1, in, nullptr, g.nr, out, n_chi, dmap, n_chi, n_rows, 1.0, s);
+    return launch_row_fft(ctx, g, prec, 2, in, nullptr, n_chi, out, g.nr, dmap, n_chi, n_rows, 1.0 / g.volume, s);
+  }
+  if (direction > 0) {
+    // in [N_r][n_chi] is the work buffer: (i2,i3) planes in place, then the i1 pass writes the G rows of out.
+    void* work = const_cast<void*>(in);
+    if ((st = launch_col_plane(ctx, g, prec, -1, work, n_chi, n_chi, 1.0, s))) return st;
+    return launch_col_line(ctx, g, prec, -1, 2, work, n_chi, out, n_chi, n_chi, dinv, g.dv * g.dv / g.volume, s);
+  }
+  // W(G,G') -> W(r,G'): i1 pass gathering the G rows, then the (i2,i3) planes in place in out.
+  if ((st = launch_col_line(ctx, g, prec, +1, 1, in, n_chi, out, n_chi, n_chi, dinv, 1.0, s))) return st;
+  return launch_col_plane(ctx, g, prec, +1, out, n_chi, n_chi, 1.0, s);
+}
+
+extern "C" gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double* M_h, size_t elems, gw_prec prec,
+                                     const void* in, void* out, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  if (kind != GW_CT && kind != GW_ST) return fail(ctx, GW_ERR_ARG, "kind must be GW_CT or GW_ST");
+  if (n < 1 || n > 32) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
+  if (!M_h || !in || !out) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  if (in == out) return fail(ctx, GW_ERR_ARG, "in and out must not overlap");
+  cudaStream_t s = as_stream(stream);
+  gw_status st = reserve(ctx, 8 * 32 * 32);
+  if (st) return st;
+  if (is_fp64(prec)) {
+    if ((st = upload(ctx, ctx->arena, M_h, sizeof(double) * n * n, s))) return st;
+  } else {
+    std::vector<float> m(M_h, M_h + n * n);
+    if ((st = upload(ctx, ctx->arena, m.data(), sizeof(float) * n * n, s))) return st;
+  }
+  return launch_ct(ctx, prec, kind == GW_ST, n, ctx->arena, elems, in, out, s);
+}

@@ -1,0 +1,58 @@
+// Launchers shared between the libgw translation units (internal).
+#pragma once
+
+#include "gw_common.cuh"
+
+namespace gw {
+
+// gw_fft.cu
+gw_status launch_row_fft(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int mode, const void* a, const void* b,
+                         long lda, void* out, long ldo, const int* map, int n_chi, int n_rows, double scale,
+                         cudaStream_t st);
+gw_status launch_col_plane(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, void* buf, long ld, int ncols,
+                           double scale, cudaStream_t st);
+gw_status launch_col_line(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, int variant, const void* in,
+                          long ldi, void* out, long ldo, int ncols, const int* inv, double scale, cudaStream_t st);
+gw_status launch_col_line_ct(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* slabs, long slab_stride,
+                             long ld, int ntau, const void* cw, int nw, void* out, long out_slice, long ldo,
+                             const int* inv, int ncols, cudaStream_t st);
+gw_status launch_ct(gw_ctx* ctx, gw_prec prec, bool st_kind, int n, const void* dM, size_t elems, const void* in,
+                    void* out, cudaStream_t st);
+gw_status launch_hadamard(gw_ctx* ctx, gw_prec prec, size_t count, const void* a, const void* b, double scale,
+                          void* out, cudaStream_t st);
+gw_status upload(gw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st);
+gw_status index_maps(gw_ctx* ctx, const GridInfo& g, const int32_t* fft_index_h, int n_chi, std::vector<int>& map,
+                     std::vector<int>& inv);
+
+// gw_gemm.cu: C = alpha * op(A) op(B) + beta * C on CUDA cores (complex).
+//  a(m,k) = A[m*lda+k] (a_km = 0) or A[k*lda+m] (a_km = 1), conjugated if a_conj;
+//  b(k,n) = B[k*ldb+n] (b_nk = 0) or B[n*ldb+k] (b_nk = 1), conjugated if b_conj;
+//  kscale (real, length K) multiplies a(m,k) if not NULL;
+//  tri = 1 computes only the lower triangle (m >= n); tri = 2 additionally
+//  starts the k loop at the first row of each tile (for L^H L with L lower).
+struct GemmArgs {
+  int M, N, K;
+  double alpha_re, alpha_im, beta;
+  const void* A; long lda; int a_km; bool a_conj;
+  const void* B; long ldb; int b_nk; bool b_conj;
+  void* C; long ldc;
+  const void* kscale;
+  int tri;
+};
+gw_status launch_gemm(gw_ctx* ctx, gw_prec prec, const GemmArgs& a, cudaStream_t st);
+
+// gw_green.cu: pre-scaled exponentials of Eqs. Green_occ/unocc for one tau.
+struct GreenScales {
+  std::vector<double> s;   // [N_b], s_i / max over the occupied set and s_a / max over the unoccupied set
+  double amax_occ, amax_unocc;
+};
+GreenScales green_scales(const double* eps, int n_b, int n_occ, double mu, double tau);
+gw_status green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const void* dscale,
+                     const GreenScales& gs, int r0, int n_rows, gw_prec prec, void* g_occ, void* g_unocc,
+                     cudaStream_t st);
+
+}  // namespace gw
+
+namespace gw {
+gw_status upload_scales(gw_ctx* ctx, void* dst, const GreenScales& gs, gw_prec prec, cudaStream_t st);
+}  // namespace gw

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libgw.so (include/gw.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Device arrays are torch tensors (complex64 for the FP32 and
+tensor-core precisions, complex128 for FP64); host arrays are numpy.  The
+stream is torch's current CUDA stream.  There is no CPU fallback: if libgw.so
+is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgw.so")
+
+FP64, FP32, F16X3, BF16X3 = 0, 1, 2, 3
+PREC = {"fp64": FP64, "fp32": FP32, "f16x3": F16X3, "bf16x3": BF16X3}
+CT, ST = 0, 1
+STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "GW_ERR_CUDA",
+          5: "GW_ERR_NUMERIC", 6: "GW_ERR_TIMEOUT", 7: "GW_ERR_UNSUPPORTED"}
+
+# every symbol declared in include/gw.h
+EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes",
+           "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
+           "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
+           "gw_chi0_omega"]
+
+
+class GwError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+class Grid(ct.Structure):
+    _fields_ = [("n", ct.c_int * 3), ("lattice", ct.c_double * 9)]
+
+
+_P = ct.c_void_p
+_I = ct.c_int
+_D = ct.c_double
+_DP = ct.POINTER(ct.c_double)
+_IP = ct.POINTER(ct.c_int32)
+_G = ct.POINTER(Grid)
+
+_SIGS = {
+    "gw_ctx_create": (_I, [_I, ct.POINTER(_P)]),
+    "gw_ctx_destroy": (_I, [_P]),
+    "gw_last_error": (ct.c_char_p, [_P]),
+    "gw_ctx_launches": (ct.c_ulonglong, [_P]),
+    "gw_ctx_scratch_bytes": (ct.c_size_t, [_P]),
+    "gw_version": (_I, []),
+    "gw_g_set": (_I, [_G, _I, _IP, _IP]),
+    "gw_coulomb_sqrt": (_I, [_G, _IP, _I, _DP]),
+    "gw_fit_transform": (_I, [_I, _DP, _DP, _D, _D, _I, _D, _DP, _DP, _DP, _DP]),
+    "gw_green_tau": (_I, [_P, _G, _I, _I, _P, _DP, _D, _D, _I, _I, _I, _P, _P, _P]),
+    "gw_chi0_rtau": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    "gw_chi0_rtau_fused": (_I, [_P, _G, _I, _I, _P, _DP, _D, _D, _I, _I, _I, _P, _P]),
+    "gw_rr_to_GG_fft": (_I, [_P, _G, _I, _I, _I, _IP, _I, _I, _I, _P, _P, _P]),
+    "gw_tau_to_omega": (_I, [_P, _I, _I, _DP, ct.c_size_t, _I, _P, _P, _P]),
+    "gw_screen_W": (_I, [_P, _G, _I, _IP, _I, _I, _P, _P, _DP, _P]),
+    "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
+                           _DP, _DP, _DP, _I, _DP, _P]),
+    "gw_chi0_omega": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libgw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgw.so not built: run paper_1607_02859_gb300/build.py (or __graft_entry__.build())")
+        L = ct.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(_IP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _check(st, ctx=None):
+    if st != 0:
+        msg = lib().gw_last_error(ctx.handle if ctx is not None else None)
+        raise GwError(st, msg.decode() if msg else "")
+
+
+def make_grid(n, lattice) -> Grid:
+    g = Grid()
+    for d in range(3):
+        g.n[d] = int(n[d])
+    lat = np.asarray(lattice, dtype=np.float64).reshape(9)
+    for i in range(9):
+        g.lattice[i] = float(lat[i])
+    return g
+
+
+def prec_of(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def cdtype(prec):
+    import torch
+    return torch.complex128 if prec_of(prec) == FP64 else torch.complex64
+
+
+class Context:
+    """A libgw context bound to one CUDA device."""
+
+    def __init__(self, device=0):
+        h = _P()
+        _check(lib().gw_ctx_create(int(device), ct.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().gw_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return int(lib().gw_ctx_launches(self.handle))
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(lib().gw_ctx_scratch_bytes(self.handle))
+
+
+# ------------------------------------------------------------------ host setup
+
+def g_set(grid: Grid, n_chi: int):
+    gv = np.zeros((n_chi, 3), dtype=np.int32)
+    idx = np.zeros(n_chi, dtype=np.int32)
+    _check(lib().gw_g_set(ct.byref(grid), int(n_chi), _ip(gv), _ip(idx)))
+    return gv, idx
+
+
+def coulomb_sqrt(grid: Grid, gvec):
+    gv = _i32(gvec)
+    out = np.zeros(len(gv), dtype=np.float64)
+    _check(lib().gw_coulomb_sqrt(ct.byref(grid), _ip(gv), len(gv), _dp(out)))
+    return out
+
+
+def fit_transform(tau, omega, x_min, x_max, n_x=4000, ridge=1e-6):
+    tau = _f64(tau)
+    omega = _f64(omega)
+    n = len(tau)
+    C = np.zeros((n, n))
+    S = np.zeros((n, n))
+    Ci = np.zeros((n, n))
+    err = np.zeros(2)
+    _check(lib().gw_fit_transform(n, _dp(tau), _dp(omega), float(x_min), float(x_max), int(n_x), float(ridge),
+                                  _dp(C), _dp(S), _dp(Ci), _dp(err)))
+    return {"C": C, "S": S, "Cinv": Ci, "fit_err_cos": err[0], "fit_err_sin": err[1]}
+
+
+# ------------------------------------------------------------------ device calls
+
+def _stream():
+    import torch
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, name, prec=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if prec is not None and t.dtype != cdtype(prec):
+        raise ValueError("%s must be %s for this precision" % (name, cdtype(prec)))
+    return ct.c_void_p(t.data_ptr())
+
+
+def green_tau(ctx, grid, psi, eps, n_occ, mu, tau, r0, n_rows, prec, g_occ=None, g_unocc=None):
+    p = prec_of(prec)
+    eps = _f64(eps)
+    _check(lib().gw_green_tau(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p), _dp(eps),
+                              float(mu), float(tau), int(r0), int(n_rows), p, _dev(g_occ, "g_occ", p),
+                              _dev(g_unocc, "g_unocc", p), _stream()), ctx)
+
+
+def chi0_rtau(ctx, g_occ, g_unocc, chi, prec):
+    p = prec_of(prec)
+    n_rows, n_cols = g_occ.shape
+    _check(lib().gw_chi0_rtau(ctx.handle, n_rows, n_cols, p, _dev(g_occ, "g_occ", p), _dev(g_unocc, "g_unocc", p),
+                              _dev(chi, "chi", p), _stream()), ctx)
+
+
+def chi0_rtau_fused(ctx, grid, psi, eps, n_occ, mu, tau, r0, n_rows, prec, chi):
+    p = prec_of(prec)
+    eps = _f64(eps)
+    _check(lib().gw_chi0_rtau_fused(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p),
+                                    _dp(eps), float(mu), float(tau), int(r0), int(n_rows), p, _dev(chi, "chi", p),
+                                    _stream()), ctx)
+
+
+def rr_to_GG_fft(ctx, grid, direction, stage, fft_index, prec, r0, n_rows, inp, out):
+    p = prec_of(prec)
+    idx = _i32(fft_index)
+    _check(lib().gw_rr_to_GG_fft(ctx.handle, ct.byref(grid), int(direction), int(stage), len(idx), _ip(idx), p,
+                                 int(r0), int(n_rows), _dev(inp, "in", p), _dev(out, "out", p), _stream()), ctx)
+
+
+def tau_to_omega(ctx, kind, M, inp, out, prec):
+    p = prec_of(prec)
+    M = _f64(M)
+    n = M.shape[0]
+    elems = inp.numel() // n
+    _check(lib().gw_tau_to_omega(ctx.handle, int(kind), n, _dp(M), elems, p, _dev(inp, "in", p),
+                                 _dev(out, "out", p), _stream()), ctx)
+
+
+def screen_W(ctx, grid, gvec, prec, chi_w, w_w, resid=True):
+    p = prec_of(prec)
+    gv = _i32(gvec)
+    n_omega = chi_w.shape[0]
+    res = np.zeros(n_omega) if resid else None
+    _check(lib().gw_screen_W(ctx.handle, ct.byref(grid), len(gv), _ip(gv), n_omega, p, _dev(chi_w, "chi_w", p),
+                             _dev(w_w, "w_w", p), _dp(res), _stream()), ctx)
+    return res
+
+
+def sigma_diag(ctx, grid, psi, eps, n_occ, mu, bands, tau, omega, C, S, w_tau, fft_index, prec, w_real=None):
+    p = prec_of(prec)
+    eps = _f64(eps)
+    bands = _i32(bands)
+    tau = _f64(tau)
+    omega = _f64(omega)
+    C = _f64(C)
+    S = _f64(S)
+    idx = _i32(fft_index)
+    n = len(tau)
+    n_n = len(bands)
+    s_tau = np.zeros((2, n_n, n))
+    s_iw = np.zeros((n_n, n), dtype=np.complex128)
+    wr = None if w_real is None else _f64(w_real)
+    n_real = 0 if wr is None else len(wr)
+    s_re = np.zeros((n_n, max(n_real, 1)), dtype=np.complex128)
+    st = lib().gw_sigma_diag(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p), _dp(eps),
+                             float(mu), _ip(bands), n_n, n, _dp(tau), _dp(omega), _dp(C), _dp(S),
+                             _dev(w_tau, "w_tau", p), len(idx), _ip(idx), p, _dp(s_tau),
+                             s_iw.ctypes.data_as(_DP), _dp(wr), n_real,
+                             s_re.ctypes.data_as(_DP) if n_real else None, _stream())
+    _check(st, ctx)
+    out = {"sigma_unocc": s_tau[0], "sigma_occ": s_tau[1], "sigma_iw": s_iw}
+    if n_real:
+        out["sigma_real"] = s_re
+    return out
+
+
+def chi0_omega(ctx, grid, psi, eps, n_occ, mu, tau, C, fft_index, prec, chi_w, r_block=0):
+    p = prec_of(prec)
+    eps = _f64(eps)
+    tau = _f64(tau)
+    C = _f64(C)
+    idx = _i32(fft_index)
+    _check(lib().gw_chi0_omega(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p), _dp(eps),
+                               float(mu), len(tau), _dp(tau), _dp(C), len(idx), _ip(idx), p, int(r_block),
+                               _dev(chi_w, "chi_w", p), _stream()), ctx)
