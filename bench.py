@@ -181,8 +181,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "f16x3", "bf16x3"])
-    ap.add_argument("--workload", default="si8", choices=["si8", "gamma_toy"])
+    ap.add_argument("--workload", default="si8", choices=["si8", "mid", "gamma_toy"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-breakdown", action="store_true", help="skip the per-stage pass")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     args = ap.parse_args()
 
     from paper_1607_02859_gb300 import inputs
@@ -270,14 +272,18 @@ def main():
     # per-stage breakdown and the dominant stage's roofline (same stream, CUDA events)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     flush.zero_()
-    step(psi, ev)
+    if args.no_breakdown:
+        for e in ev:
+            e.record(stream)
+    else:
+        step(psi, ev)
     torch.cuda.synchronize()
     stage_ms = {name: ev[i].elapsed_time(ev[i + 1]) for i, name in
                 enumerate(["chi0_omega", "screen_W", "inverse_ct", "sigma_diag"])}
     stage_flops = {"chi0_omega": fl["green"] / 2 + fl["fft"] / 2 + fl["ct"] / 2 + fl["hadamard"] / 3,
                    "screen_W": fl["dyson"], "inverse_ct": fl["ct"] / 2,
                    "sigma_diag": fl["green"] / 2 + fl["fft"] / 2 + fl["sigma"] + 2 * fl["hadamard"] / 3}
-    dom = max(stage_ms, key=stage_ms.get)
+    dom = max(stage_ms, key=stage_ms.get) if not args.no_breakdown else "screen_W"
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     if args.prec in ("f16x3", "bf16x3") and dom in ("chi0_omega", "sigma_diag"):
@@ -287,13 +293,13 @@ def main():
         pk = sm_peak_fp32(sm_max) if args.prec != "fp64" else sm_peak_fp32(sm_max) / 64
         roof = {"bound": "alu", "peak": pk, "unit": "TFLOP/s",
                 "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x %.0f MHz" % sm_max}
-    achieved = stage_flops[dom] / (stage_ms[dom] / 1e3) / 1e12
+    achieved = stage_flops[dom] / max(stage_ms[dom] / 1e3, 1e-12) / 1e12
     roof.update({"kernel_stage": dom, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None})
 
     # end to end through the public API: orbitals copied from pinned host memory every step,
     # Sigma read back to the host inside the call
     e_times = []
-    for _ in range(args.steps):
+    for _ in range(0 if args.no_e2e else args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -302,7 +308,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1) / 1e3)
-    t_e2e = float(np.sum(e_times))
+    t_e2e = float(np.sum(e_times)) if e_times else float("nan")
     if dist is not None:
         t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

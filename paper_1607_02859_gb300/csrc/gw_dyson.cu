@@ -3,13 +3,20 @@
 // With chi~ = v^{1/2} chi v^{1/2} Hermitian negative semidefinite, the matrix
 // eps~ = 1 - chi~ is Hermitian positive definite with eps~ >= 1, so
 //   W~ = v^{1/2} (eps~^{-1} - 1) v^{1/2}
-// follows from a Cholesky factorisation without pivoting:
-//   1. eps~ = L L^H          (right-looking, 64-column panels; the trailing
-//                             Hermitian update is a GEMM)
-//   2. M = L^{-1}            (forward substitution on the identity, block row
-//                             by block row; the update of the rows below is a
-//                             GEMM that skips the zero upper part)
-//   3. eps~^{-1} = M^H M     (lower triangle, one GEMM)
+// follows from a Cholesky factorisation without pivoting.  The identity is
+// carried implicitly so that nothing is ever formed as "1 + small" and then
+// subtracted again (at large omega chi~ is tiny and such a round trip would
+// lose its low digits):
+//   B = eps~ - 1 = -chi~,  eps~ = L L^H with L = 1 + K on the diagonal,
+//   L_jj - 1 = B'_jj / (1 + sqrt(1 + B'_jj))  (B' = B after the updates),
+//   L^{-1} = 1 + P,
+//   eps~^{-1} - 1 = P + P^H + P^H P.
+// Steps (64-column panels):
+//   1. right-looking Cholesky; the trailing Hermitian update is a GEMM
+//   2. P = L^{-1} - 1 by forward substitution on the identity, block row by
+//      block row; the update of the rows below is a GEMM that skips the zero
+//      upper part
+//   3. P^H P (lower triangle, one GEMM), plus P + P^H
 // i.e. N^3/2 complex multiply-adds in all, instead of the N^3 + N^3/6 of a
 // solve against chi~ with N right-hand sides.
 #include <cmath>
@@ -29,9 +36,7 @@ __global__ void build_eps_kernel(const typename cpx<T>::t* __restrict__ chi, con
   if (b > a || b >= n) return;
   const T vv = T(vh[a] * vh[b]);
   C x = chi[(long)a * n + b];
-  C e = mk(-vv * x.x, -vv * x.y);
-  if (a == b) e.x += T(1);
-  E[(long)a * n + b] = e;
+  E[(long)a * n + b] = mk(-vv * x.x, -vv * x.y);
 }
 
 // Unblocked Cholesky of the kb x kb diagonal block (lower), in shared memory.
@@ -48,15 +53,15 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(typename cpx<T>::t* A, 
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     if (threadIdx.x == 0) {
-      T d = S[j][j].x;
-      if (!(d > T(0))) {
+      T b = S[j][j].x;                       // eps~_jj - 1 after the updates
+      if (!(T(1) + b > T(0))) {
         if (atomicCAS(flag, 0, 1) == 0) flag[1] = col0 + j;
-        d = T(1);
+        b = T(0);
       }
-      S[j][j] = mk(sqrt(d), T(0));
+      S[j][j] = mk(b / (T(1) + sqrt(T(1) + b)), T(0));   // L_jj - 1
     }
     __syncthreads();
-    const T piv = S[j][j].x;
+    const T piv = T(1) + S[j][j].x;
     for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) S[i][j] = cscale(S[i][j], T(1) / piv);
     __syncthreads();
     const int m = kb - j - 1;
@@ -93,17 +98,21 @@ __global__ void __launch_bounds__(64) trsm_panel_kernel(typename cpx<T>::t* A, l
   for (int c = 0; c < kb; ++c) {
     C s = X[c * 64 + t];
     for (int p = 0; p < c; ++p) s = csub(s, cmulc(X[p * 64 + t], L[c * (kNB + 1) + p]));
-    X[c * 64 + t] = cscale(s, T(1) / L[c * (kNB + 1) + c].x);
+    X[c * 64 + t] = cscale(s, T(1) / (T(1) + L[c * (kNB + 1) + c].x));
   }
   for (int c = 0; c < kb; ++c) A[row * lda + k0 + c] = X[c * 64 + t];
 }
 
+// P[rows below][k0 .. k0+kb) = -L[rows below][k0 .. k0+kb): the identity part of
+// (1 + P) contributes L_li * 1 to the update of the rows below block row i.
 template <typename T>
-__global__ void identity_kernel(typename cpx<T>::t* M, int n) {
-  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (e >= (long)n * n) return;
-  const long a = e / n, b = e % n;
-  M[e] = mk(T(a == b ? 1 : 0), T(0));
+__global__ void neg_copy_kernel(const typename cpx<T>::t* __restrict__ Lm, typename cpx<T>::t* __restrict__ P, long ld,
+                                int row0, int rows, int col0, int kb) {
+  const int c = threadIdx.x;
+  const long r = row0 + (long)blockIdx.x;
+  if (c >= kb || blockIdx.x >= rows) return;
+  const auto v = Lm[r * ld + col0 + c];
+  P[r * ld + col0 + c] = mk(-v.x, -v.y);
 }
 
 // Y = L_ii^{-1} Y for the block rows k0..k0+kb-1 and columns 0..ncols-1 of Y.
@@ -121,28 +130,50 @@ __global__ void __launch_bounds__(64) trsm_left_kernel(const typename cpx<T>::t*
   }
   const int col = blockIdx.x * 64 + t;
   const bool active = col < ncols;
+  const int dc = col - k0;                   // column inside the diagonal block, or < 0
   if (active)
-    for (int r = 0; r < kb; ++r) X[r * 64 + t] = Y[(long)(k0 + r) * ldy + col];
+    for (int r = 0; r < kb; ++r)
+      X[r * 64 + t] = dc >= 0 ? mk(T(r == dc ? 1 : 0), T(0)) : Y[(long)(k0 + r) * ldy + col];
   __syncthreads();
   if (!active) return;
   for (int r = 0; r < kb; ++r) {
     C s = X[r * 64 + t];
     for (int p = 0; p < r; ++p) s = csub(s, cmul(L[r * (kNB + 1) + p], X[p * 64 + t]));
-    X[r * 64 + t] = cscale(s, T(1) / L[r * (kNB + 1) + r].x);
+    X[r * 64 + t] = cscale(s, T(1) / (T(1) + L[r * (kNB + 1) + r].x));
   }
-  for (int r = 0; r < kb; ++r) Y[(long)(k0 + r) * ldy + col] = X[r * 64 + t];
+  for (int r = 0; r < kb; ++r) {
+    C y = X[r * 64 + t];
+    if (r == dc) {                           // (1 + K)^{-1} - 1 = -K / (1 + K)
+      const T k = L[r * (kNB + 1) + r].x;
+      y = mk(-k / (T(1) + k), T(0));
+    }
+    Y[(long)(k0 + r) * ldy + col] = y;
+  }
 }
 
-// W~[a][b] = v_a (Einv[a][b] - delta_ab) v_b, both triangles from the lower one.
+// X = P^H P + P + P^H (lower triangle, in place over P^H P).
 template <typename T>
-__global__ void finalize_kernel(const typename cpx<T>::t* __restrict__ Einv, const double* __restrict__ vh,
+__global__ void assemble_kernel(typename cpx<T>::t* __restrict__ X, const typename cpx<T>::t* __restrict__ P, int n) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (b > a || b >= n) return;
+  const long e = (long)a * n + b;
+  auto x = X[e];
+  const auto p = P[e];
+  x.x += a == b ? T(2) * p.x : p.x;
+  x.y += a == b ? T(0) : p.y;
+  X[e] = x;
+}
+
+// W~[a][b] = v_a X[a][b] v_b, both triangles from the lower one.
+template <typename T>
+__global__ void finalize_kernel(const typename cpx<T>::t* __restrict__ Xl, const double* __restrict__ vh,
                                 typename cpx<T>::t* __restrict__ W, int n) {
   using C = typename cpx<T>::t;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (b > a || b >= n) return;
-  C x = Einv[(long)a * n + b];
-  if (a == b) x.x -= T(1);
+  C x = Xl[(long)a * n + b];
   const T vv = T(vh[a] * vh[b]);
   x = cscale(x, vv);
   W[(long)a * n + b] = x;
@@ -233,9 +264,8 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
     g.tri = 1;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
   }
-  // 2. M = L^{-1}
-  identity_kernel<T><<<(int)(((long)n * n + 255) / 256), 256, 0, st>>>(m, n);
-  if ((rc = launch_check(ctx, "identity_kernel"))) return rc;
+  // 2. P = L^{-1} - 1
+  if ((rc = cuda_check(ctx, cudaMemsetAsync(m, 0, sizeof(C) * (size_t)n * n, st), "memset P"))) return rc;
   for (int k0 = 0; k0 < n; k0 += kNB) {
     const int kb = std::min(kNB, n - k0);
     const int ncols = k0 + kb;
@@ -243,6 +273,8 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
     if ((rc = launch_check(ctx, "trsm_left_kernel"))) return rc;
     const int rows = n - k0 - kb;
     if (rows <= 0) break;
+    neg_copy_kernel<T><<<rows, kNB, 0, st>>>(e, m, n, k0 + kb, rows, k0, kb);
+    if ((rc = launch_check(ctx, "neg_copy_kernel"))) return rc;
     GemmArgs g{};
     g.M = rows;
     g.N = ncols;
@@ -257,7 +289,7 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
     g.ldc = n;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
   }
-  // 3. eps~^{-1} = M^H M (lower) into E
+  // 3. eps~^{-1} - 1 = P^H P + P + P^H (lower) into E
   {
     GemmArgs g{};
     g.M = n;
@@ -276,6 +308,8 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
     g.tri = 2;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
   }
+  assemble_kernel<T><<<gb, tb, 0, st>>>(e, m, n);
+  if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
   if (resid_h) {
     // |eps~ X z - chi~ z| / |chi~ z| over 4 probes, X = eps~^{-1} - 1 (before chi may be overwritten)
     double num = 0, den = 0;
@@ -291,7 +325,7 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
       }
       double2 *z = probe, *u = probe + n, *w = probe + 2 * n, *c = probe + 3 * n;
       if ((rc = upload(ctx, z, hz.data(), sizeof(double2) * n, st))) return rc;
-      hemv_probe_kernel<T><<<n, 256, 0, st>>>(e, nullptr, 1.0, z, u, n);                       // u = X z
+      hemv_probe_kernel<T><<<n, 256, 0, st>>>(e, nullptr, 0.0, z, u, n);                       // u = X z
       hemv_probe_kernel<T><<<n, 256, 0, st>>>(static_cast<const C*>(chi), dvh, 0.0, u, w, n);  // w = chi~ u
       hemv_probe_kernel<T><<<n, 256, 0, st>>>(static_cast<const C*>(chi), dvh, 0.0, z, c, n);  // c = chi~ z
       if ((rc = launch_check(ctx, "hemv_probe_kernel"))) return rc;

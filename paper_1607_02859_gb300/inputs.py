@@ -164,6 +164,13 @@ def si8(seed=2):
                         seed, n_bands_sigma=8, pin_edges=True, name="si8_24^3_1024b")
 
 
+def mid(seed=4):
+    """16^3, 32+480 complex orbitals, 8 tau: the si8 recipe at a size whose
+    per-step device footprint (~3.5 GB) suits a full profiler capture."""
+    return make_problem((16, 16, 16), 10.26 * 16 / 24, 32, 480, (-0.5, 0.0), (0.04, 4.0), 0.02, 8,
+                        seed, n_bands_sigma=8, pin_edges=True, name="mid_16^3_512b")
+
+
 def si64(seed=3):
     """36^3, 128+4096 complex orbitals, chi on the lowest 8192 G, 20 tau."""
     return make_problem((36, 36, 36), 20.52, 128, 4096, (-0.5, 0.0), (0.03, 5.0), 0.015, 20,
