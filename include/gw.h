@@ -155,6 +155,26 @@ gw_status gw_rr_to_GG_fft(gw_ctx* ctx, const gw_grid* grid, int direction, int s
                           int n_chi, const int32_t* fft_index_h, gw_prec prec, int r0,
                           int n_rows, const void* in, void* out, void* stream);
 
+/* gw_rr_to_GG_fft without any device allocation and without a context.
+ * The paper has no counterpart: this exists for callers that must not call
+ * cudaMalloc at all -- for example a program whose memory pool owns the whole
+ * GPU and forbids allocations outside it, or a latency-bound loop that cannot
+ * take the device-wide synchronisation an allocation may cause.
+ * Arguments, layouts and results are exactly those of gw_rr_to_GG_fft.  The
+ * two index maps the transform needs live in one fixed array inside the
+ * library's device image (n_chi + N_r <= 27648 entries, i.e. up to the 24^3
+ * grid); larger requests return GW_ERR_SHAPE.  That array exists on every GPU
+ * that loads the library until the process exits.  It is looked up once per
+ * device on the first call made with that device current; make that first call
+ * before any stream capture.  Every call rewrites both maps in full, so nothing
+ * carries over between calls, but all calls share the array: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * it.  Calls on one stream are ordered and safe.  Errors are reported through
+ * gw_last_error(NULL). */
+gw_status gw_rr_to_GG_fft_noalloc(const gw_grid* grid, int direction, int stage, int n_chi,
+                                  const int32_t* fft_index_h, gw_prec prec, int r0, int n_rows,
+                                  const void* in, void* out, void* stream);
+
 /* Nonuniform time <-> frequency transform of `elems` complex elements per slice
  * (Eqs. CTX, CT_W, ST_FFT):  out[k][e] = (i if kind==GW_ST) sum_j M_h[k][j] in[j][e]
  * for k, j < n.  M_h is FP64 on the host; the sums are accumulated in FP64.

@@ -14,6 +14,8 @@
 //    "line" kernel the i1 1-D FFT in registers.  The last i1 pass of the chi
 //    chain also applies the cosine transform over all tau (Eq. CTX) before
 //    anything is written, saving a full read+write of chi(G,G',tau).
+#include <mutex>
+
 #include "gw_common.cuh"
 #include "gw_kernels.h"
 #include "gw_fft.cuh"
@@ -434,4 +436,93 @@ extern "C" gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double*
     if ((st = upload(ctx, ctx->arena, m.data(), sizeof(float) * n * n, s))) return st;
   }
   return launch_ct(ctx, prec, kind == GW_ST, n, ctx->arena, elems, in, out, s);
+}
+
+// ---------------------------------------------------------------------- no-allocation variant
+//
+// gw_rr_to_GG_fft needs two small index maps on the device (the G set's FFT
+// positions and their inverse).  The regular entry point keeps them in the
+// context's scratch arena, which is created with cudaMalloc.  This variant keeps
+// them instead in one fixed array in the library's own device memory, so a
+// caller that may not allocate device memory at all can still run the
+// transform: for example a program whose memory pool has taken the whole GPU
+// and forbids any other cudaMalloc, or a serving loop that cannot afford the
+// device-wide synchronisation a cudaMalloc/cudaFree may bring.
+
+namespace {
+
+constexpr int kNoAllocMaxInts = 2 * 13824;   // n_chi + N_r for the largest compiled grid (24^3)
+
+// Holds fft_index followed by its inverse map.  Every GPU that loads the
+// library keeps this array until the process exits; all calls share it.
+static __device__ __align__(256) int g_noalloc_maps[kNoAllocMaxInts];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_maps on the current device (looked up once per
+// device).  In host code the symbol itself is only a host-side stand-in.
+gw_status noalloc_maps_ptr(gw_ctx* err_ctx, int** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_check(err_ctx, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(err_ctx, GW_ERR_UNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_maps);
+    if (e != cudaSuccess) return cuda_check(err_ctx, e, "cudaGetSymbolAddress(g_noalloc_maps)");
+    g_noalloc_ptr[dev] = static_cast<int*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return GW_OK;
+}
+
+}  // namespace
+
+extern "C" gw_status gw_rr_to_GG_fft_noalloc(const gw_grid* grid, int direction, int stage, int n_chi,
+                                             const int32_t* fft_index_h, gw_prec prec, int r0, int n_rows,
+                                             const void* in, void* out, void* stream) {
+  gw_ctx local;                       // host-only bookkeeping: no device memory behind it
+  local.num_sms = 1;
+  auto done = [&](gw_status st) {
+    if (st) fail(nullptr, st, local.err);
+    return st;
+  };
+  GridInfo g;
+  gw_status st = grid_info(&local, grid, &g);
+  if (st) return done(st);
+  if (!grid_supported(g.n1, g.n2, g.n3)) return done(fail(&local, GW_ERR_UNSUPPORTED, "no FFT kernels compiled for this grid"));
+  if (!valid_prec(prec)) return done(fail(&local, GW_ERR_ARG, "bad precision"));
+  if (direction != 1 && direction != -1) return done(fail(&local, GW_ERR_ARG, "direction must be +1 or -1"));
+  if (stage != 1 && stage != 2) return done(fail(&local, GW_ERR_ARG, "stage must be 1 or 2"));
+  if (!in || !out) return done(fail(&local, GW_ERR_ARG, "NULL pointer"));
+  std::vector<int> map, inv;
+  if ((st = index_maps(&local, g, fft_index_h, n_chi, map, inv))) return done(st);
+  if ((long)n_chi + g.nr > kNoAllocMaxInts)
+    return done(fail(&local, GW_ERR_SHAPE, "n_chi + N_r exceeds the fixed index-map capacity of " +
+                                               std::to_string(kNoAllocMaxInts) + " entries"));
+  if (stage == 1 && (n_rows < 0 || r0 < 0 || r0 + n_rows > g.nr))
+    return done(fail(&local, GW_ERR_SHAPE, "rows out of range"));
+  int* maps = nullptr;
+  if ((st = noalloc_maps_ptr(&local, &maps))) return done(st);
+  int* dmap = maps;
+  int* dinv = maps + n_chi;
+  cudaStream_t s = as_stream(stream);
+  // both maps are rewritten in full on every call, so nothing carries over
+  if ((st = upload(&local, dmap, map.data(), sizeof(int) * n_chi, s))) return done(st);
+  if ((st = upload(&local, dinv, inv.data(), sizeof(int) * g.nr, s))) return done(st);
+  if (stage == 1) {
+    if (direction > 0) st = launch_row_fft(&local, g, prec, 1, in, nullptr, g.nr, out, n_chi, dmap, n_chi, n_rows, 1.0, s);
+    else st = launch_row_fft(&local, g, prec, 2, in, nullptr, n_chi, out, g.nr, dmap, n_chi, n_rows, 1.0 / g.volume, s);
+    return done(st);
+  }
+  if (direction > 0) {
+    void* work = const_cast<void*>(in);
+    if ((st = launch_col_plane(&local, g, prec, -1, work, n_chi, n_chi, 1.0, s))) return done(st);
+    return done(launch_col_line(&local, g, prec, -1, 2, work, n_chi, out, n_chi, n_chi, dinv, g.dv * g.dv / g.volume, s));
+  }
+  if ((st = launch_col_line(&local, g, prec, +1, 1, in, n_chi, out, n_chi, n_chi, dinv, 1.0, s))) return done(st);
+  return done(launch_col_plane(&local, g, prec, +1, out, n_chi, n_chi, 1.0, s));
 }

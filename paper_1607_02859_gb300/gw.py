@@ -26,7 +26,7 @@ STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "G
 EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes",
            "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
-           "gw_chi0_omega"]
+           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc"]
 
 
 class GwError(RuntimeError):
@@ -61,6 +61,7 @@ _SIGS = {
     "gw_chi0_rtau": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
     "gw_chi0_rtau_fused": (_I, [_P, _G, _I, _I, _P, _DP, _D, _D, _I, _I, _I, _P, _P]),
     "gw_rr_to_GG_fft": (_I, [_P, _G, _I, _I, _I, _IP, _I, _I, _I, _P, _P, _P]),
+    "gw_rr_to_GG_fft_noalloc": (_I, [_G, _I, _I, _I, _IP, _I, _I, _I, _P, _P, _P]),
     "gw_tau_to_omega": (_I, [_P, _I, _I, _DP, ct.c_size_t, _I, _P, _P, _P]),
     "gw_screen_W": (_I, [_P, _G, _I, _IP, _I, _I, _P, _P, _DP, _P]),
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
@@ -231,6 +232,15 @@ def rr_to_GG_fft(ctx, grid, direction, stage, fft_index, prec, r0, n_rows, inp, 
     idx = _i32(fft_index)
     _check(lib().gw_rr_to_GG_fft(ctx.handle, ct.byref(grid), int(direction), int(stage), len(idx), _ip(idx), p,
                                  int(r0), int(n_rows), _dev(inp, "in", p), _dev(out, "out", p), _stream()), ctx)
+
+
+def rr_to_GG_fft_noalloc(grid, direction, stage, fft_index, prec, r0, n_rows, inp, out):
+    """gw_rr_to_GG_fft with its index maps in the library's fixed device array:
+    for callers that may not allocate device memory (no context needed)."""
+    p = prec_of(prec)
+    idx = _i32(fft_index)
+    _check(lib().gw_rr_to_GG_fft_noalloc(ct.byref(grid), int(direction), int(stage), len(idx), _ip(idx), p, int(r0),
+                                         int(n_rows), _dev(inp, "in", p), _dev(out, "out", p), _stream()))
 
 
 def tau_to_omega(ctx, kind, M, inp, out, prec):
