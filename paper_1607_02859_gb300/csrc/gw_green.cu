@@ -100,7 +100,10 @@ extern "C" gw_status gw_green_tau(gw_ctx* ctx, const gw_grid* grid, int n_b, int
   cudaStream_t s = as_stream(stream);
   GreenScales gs = green_scales(eps_h, n_b, n_occ, mu, tau);
   if (prec == GW_F16X3 || prec == GW_BF16X3) {
-    return tc_green_rows(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, g_occ, g_unocc, s);
+    if ((st = reserve(ctx, tc_scratch_bytes(g, n_b, n_occ, n_rows, !g_occ || !g_unocc)))) return st;
+    if ((st = tc_green_rows(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, g_occ, g_unocc, ctx->arena, true, s)))
+      return st;
+    return tc_check(ctx, ctx->arena, s);
   }
   if ((st = reserve(ctx, Carver::round(sizeof(double) * n_b)))) return st;
   if ((st = upload_scales(ctx, ctx->arena, gs, prec, s))) return st;
@@ -118,7 +121,9 @@ extern "C" gw_status gw_chi0_rtau_fused(gw_ctx* ctx, const gw_grid* grid, int n_
   cudaStream_t s = as_stream(stream);
   GreenScales gs = green_scales(eps_h, n_b, n_occ, mu, tau);
   if (prec == GW_F16X3 || prec == GW_BF16X3) {
-    return tc_chi_rows(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, chi, s);
+    if ((st = reserve(ctx, tc_scratch_bytes(g, n_b, n_occ, n_rows, false)))) return st;
+    if ((st = tc_chi_rows(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, chi, ctx->arena, true, s))) return st;
+    return tc_check(ctx, ctx->arena, s);
   }
   // CUDA-core precisions: G_occ goes through scratch, G_unocc is formed in
   // place in chi and the product overwrites it.

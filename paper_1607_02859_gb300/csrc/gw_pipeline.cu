@@ -46,6 +46,7 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   probe.take<char>(slab * n * es);
   probe.take<char>((size_t)rb * g.nr * es);
   probe.take<char>((size_t)rb * g.nr * es);
+  if (tc) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
   if ((st = reserve(ctx, probe.off))) return st;
   Carver cv(ctx->arena);
   int* dmap = cv.take<int>(n_chi);
@@ -55,6 +56,8 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   char* slabs = cv.take<char>(slab * n * es);
   char* ga = cv.take<char>((size_t)rb * g.nr * es);
   char* gb = cv.take<char>((size_t)rb * g.nr * es);
+  void* tcs = tc ? cv.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false)) : nullptr;
+  bool first = true;
   if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
   if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
   const double fac = g.dv * g.dv / g.volume;   // Eq. FFTX2 normalisation
@@ -75,7 +78,8 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
     for (int r0 = 0; r0 < g.nr; r0 += rb) {
       const int rows = std::min(rb, g.nr - r0);
       if (tc) {
-        if ((st = tc_chi_rows(ctx, g, n_b, n_occ, psi, gs, r0, rows, prec, ga, s))) return st;
+        if ((st = tc_chi_rows(ctx, g, n_b, n_occ, psi, gs, r0, rows, prec, ga, tcs, first, s))) return st;
+        first = false;
         st = launch_row_fft(ctx, g, prec, 1, ga, nullptr, g.nr, slab_j + (size_t)r0 * n_chi * es, n_chi, dmap, n_chi,
                             rows, 1.0, s);
       } else {
@@ -87,6 +91,8 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
     }
     if ((st = launch_col_plane(ctx, g, prec, -1, slab_j, n_chi, n_chi, 1.0, s))) return st;
   }
-  return launch_col_line_ct(ctx, g, prec, slabs, (long)slab, n_chi, n, dcw, n, chi_w, (long)n_chi * n_chi, n_chi,
-                            dinv, n_chi, s);
+  if ((st = launch_col_line_ct(ctx, g, prec, slabs, (long)slab, n_chi, n, dcw, n, chi_w, (long)n_chi * n_chi, n_chi,
+                               dinv, n_chi, s)))
+    return st;
+  return tc ? tc_check(ctx, tcs, s) : GW_OK;
 }

@@ -251,6 +251,8 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   probe.take<char>((size_t)g.nr * n_chi * es);
   probe.take<char>((size_t)rb * g.nr * es);
   probe.take<char>((size_t)rb * g.nr * es);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  if (tc) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
   if ((st = reserve(ctx, probe.off))) return st;
   Carver cv(ctx->arena);
   int* dmap = cv.take<int>(n_chi);
@@ -268,6 +270,7 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   char* wrg = cv.take<char>((size_t)g.nr * n_chi * es);
   char* gob = cv.take<char>((size_t)rb * g.nr * es);
   char* gub = cv.take<char>((size_t)rb * g.nr * es);
+  void* tcs = tc ? cv.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false)) : nullptr;
   if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
   if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
   std::vector<int> bv(bands_h, bands_h + n_n);
@@ -285,14 +288,17 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   double* acc_u = acc;
   double* acc_o = acc + (size_t)n_n * n;
   const double coef = g.dv * g.dv / g.volume;   // dV^2 and the 1/Omega of Eq. FFTW
-  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  bool first = true;
   for (int j = 0; j < n; ++j) {
     const char* wj = static_cast<const char*>(w_tau) + (size_t)j * n_chi * n_chi * es;
     if ((st = launch_col_line(ctx, g, prec, +1, 1, wj, n_chi, wrg, n_chi, n_chi, dinv, 1.0, s))) return st;
     if ((st = launch_col_plane(ctx, g, prec, +1, wrg, n_chi, n_chi, 1.0, s))) return st;
     for (int r0 = 0; r0 < g.nr; r0 += rb) {
       const int rows = std::min(rb, g.nr - r0);
-      if (tc) st = tc_green_rows(ctx, g, n_b, n_occ, psi, scales[j], r0, rows, prec, gob, gub, s);
+      if (tc) {
+        st = tc_green_rows(ctx, g, n_b, n_occ, psi, scales[j], r0, rows, prec, gob, gub, tcs, first, s);
+        first = false;
+      }
       else st = green_rows(ctx, g, n_b, n_occ, psi, dscale + (size_t)j * n_b * 8, scales[j], r0, rows, prec, gob, gub, s);
       if (st) return st;
       if ((st = launch_sigma_rows(ctx, g, prec, wrg, n_chi, dmap, n_chi, gob, gub, g.nr, psi, dbands, n_n, r0, rows,
@@ -300,6 +306,7 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
         return st;
     }
   }
+  if (tc && (st = tc_check(ctx, tcs, s))) return st;
   sigma_finish_kernel<<<(n_n + 63) / 64, 64, 0, s>>>(acc_u, acc_o, n_n, n, dC, dS, dom, dwr, n_real, out_iw,
                                                       n_real > 0 ? out_re : nullptr, dstat);
   if ((st = launch_check(ctx, "sigma_finish_kernel"))) return st;

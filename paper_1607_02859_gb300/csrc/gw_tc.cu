@@ -1,15 +1,576 @@
-// Tensor-core split-precision contractions.
+// Tensor-core (tcgen05) formation of the imaginary-time Green's functions
+// (Eqs. Green_occ, Green_unocc) and of the real-space product of Eq. chi_rr.
+//
+// Complex products on real tensor cores.  With a(r,k) = psi_k(r) s_k and
+// b(R',k) = conj(psi_k(R')), G(r,R') = sum_k a(r,k) b(R',k) is one real GEMM
+//   D[r][2R'+c] = sum_k' A[r][k'] B[2R'+c][k']     (k' = 2k, 2k+1)
+// where A is the complex array viewed as real (re, im interleaved along k) and B
+// holds two real rows per complex column:
+//   B[2R'  ] = ( br_k, -bi_k )   ->  D[r][2R'  ] = Re G(r,R')
+//   B[2R'+1] = ( bi_k,  br_k )   ->  D[r][2R'+1] = Im G(r,R')
+// so the FP32 accumulator in tensor memory already holds (re, im) pairs.
+//
+// FP32-level accuracy from 16-bit tensor cores: every operand is split as
+// x = hi + lo (hi = fp16(x), lo = fp16(x - hi)) after a power-of-two scaling
+// that puts max|x| near 2^15, and D = A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (dropping A_lo B_lo ~ 2^-22 |A||B|), accumulated in FP32.  bf16 splits are
+// the same code with a coarser 2 x 8-bit representation.
+//
+// Tile: 128 rows r x 128 complex columns R' (MMA 128 x 256 x 16), K staged 64
+// real elements (128 B, SWIZZLE_128B) at a time through a 2-stage TMA/mbarrier
+// pipeline.  G_occ and G_unocc accumulate in two 256-column halves of tensor
+// memory; the epilogue either writes both (gw_green_tau) or their product
+// chi = -2 G_occ conj(G_unocc) (gw_chi0_rtau_fused), so for chi neither G tile
+// ever reaches HBM.  Warp roles: 0 = TMA producer, 1 = MMA issuer (and tensor
+// memory owner), 2..5 = epilogue.  Every wait is bounded; on time-out the
+// kernel records it in the status word, drains its own copies and MMAs, frees
+// its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <mutex>
+
 #include "gw_tc.h"
 
 namespace gw {
+namespace tc {
 
-gw_status tc_green_rows(gw_ctx* ctx, const GridInfo&, int, int, const void*, const GreenScales&, int, int, gw_prec,
-                        void*, void*, cudaStream_t) {
-  return fail(ctx, GW_ERR_UNSUPPORTED, "tensor-core precisions are not built yet");
+constexpr int BM = 128;                 // rows per tile
+constexpr int BNC = 128;                // complex columns per tile (MMA N = 256)
+constexpr int BK = 64;                  // real K per stage (one 128-byte swizzle row)
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;            // 16 KB
+constexpr int B_BYTES = 2 * BNC * BK * 2;       // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int THREADS = 192;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+struct Params {
+  int m_rows;             // valid output rows
+  int n_cols;             // valid complex output columns (N_r)
+  int k_occ_steps;        // BK stages of the occupied region
+  int k_un_steps;         // BK stages of the unoccupied region
+  int k_un_x;             // first real K index of the unoccupied region
+  float2* out0;           // chi, or G_occ
+  float2* out1;           // G_unocc (green mode)
+  long ldo;
+  float alpha_occ;        // A_occ (FP64 max exponential, rounded) times 2^{-2e}
+  float alpha_un;
+  const int* dexp;        // device: e of the 2^e operand scaling
+  int* status;            // device: [0] time-out flag, [1] where
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo&, int, int, const void*, const GreenScales&, int, int, gw_prec,
-                      void*, cudaStream_t) {
-  return fail(ctx, GW_ERR_UNSUPPORTED, "tensor-core precisions are not built yet");
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
 }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_test(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
+// 8-row core groups 1024 B apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((a & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 46;                        // version
+  d |= (uint64_t)2 << 61;                        // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = F16 (fmt 0) or BF16 (fmt 1),
+// both K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(2 * BNC >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// MODE 0: out0 = -2 G_occ conj(G_unocc);  MODE 1: out0 = G_occ, out1 = G_unocc.
+template <int MODE, uint32_t FMT>
+__global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_constant__ CUtensorMap mA_hi,
+                                                              const __grid_constant__ CUtensorMap mA_lo,
+                                                              const __grid_constant__ CUtensorMap mB_hi,
+                                                              const __grid_constant__ CUtensorMap mB_lo, Params p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * BNC;
+  const int total = p.k_occ_steps + p.k_un_steps;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto timed_out = [&](int where) {
+    *abort_flag = 1;
+    if (atomicCAS(p.status, 0, 1) == 0) p.status[1] = where;
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- TMA producer
+    int issued = 0;
+    for (int it = 0; it < total && !*abort_flag; ++it) {
+      const int s = it % STAGES;
+      if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
+        timed_out(1);
+        break;
+      }
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const int x = it < p.k_occ_steps ? it * BK : p.k_un_x + (it - p.k_occ_steps) * BK;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(st, &mA_hi, &full[s], x, m0);
+      tma_load_2d(st + A_BYTES, &mA_lo, &full[s], x, m0);
+      tma_load_2d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * n0);
+      tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * n0);
+      issued = it + 1;
+    }
+    if (*abort_flag) {
+      // let our own copies land before the CTA exits
+      for (int it = issued - STAGES < 0 ? 0 : issued - STAGES; it < issued; ++it)
+        mbar_wait(&full[it % STAGES], (it / STAGES) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
+    constexpr uint32_t idesc = make_idesc(FMT);
+    int it = 0;
+    for (; it < total && !*abort_flag; ++it) {
+      const int s = it % STAGES;
+      if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
+        timed_out(2);
+        break;
+      }
+      tc_fence_after();
+      const bool un = it >= p.k_occ_steps;
+      const int kin = un ? it - p.k_occ_steps : it;
+      const uint32_t d = tmem + (un ? 256u : 0u);
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_BYTES);
+      const uint64_t bh = sw128_desc(st + 2 * A_BYTES), bl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t off = (uint64_t)(kk * 32) >> 4;    // 16 elements = 32 bytes along K
+        umma(d, ah + off, bh + off, idesc, (kin > 0 || kk > 0) ? 1u : 0u);
+        umma(d, ah + off, bl + off, idesc, 1u);
+        umma(d, al + off, bh + off, idesc, 1u);
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);     // arrives once every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue
+    const bool ok = mbar_wait(done, 0);
+    if (!ok) timed_out(3);
+    tc_fence_after();
+    // tcgen05.ld is warp-collective: the whole warp takes the same branch
+    if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
+      const int q = warp & 3;                       // tensor-memory lane quarter of this warp
+      const int row = q * 32 + lane;
+      const int gm = m0 + row;
+      const float sc = ldexpf(1.0f, -2 * (*p.dexp));
+      const float ao = p.alpha_occ * sc, au = p.alpha_un * sc;
+      const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+#pragma unroll 1
+      for (int c = 0; c < 2 * BNC; c += 16) {
+        uint32_t ro[16], ru[16];
+        tmem_ld16(tmem + lane_addr + c, ro);
+        tmem_ld16(tmem + lane_addr + 256 + c, ru);
+        tmem_wait_ld();
+        if (gm < p.m_rows) {
+          const int nc0 = n0 + c / 2;
+          float2* o0 = p.out0 + (long)gm * p.ldo + nc0;
+          float2* o1 = p.out1 + (long)gm * p.ldo + nc0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (nc0 + j >= p.n_cols) break;
+            const float gor = __uint_as_float(ro[2 * j]) * ao, goi = __uint_as_float(ro[2 * j + 1]) * ao;
+            const float gur = __uint_as_float(ru[2 * j]) * au, gui = __uint_as_float(ru[2 * j + 1]) * au;
+            if (MODE == 0) {
+              // -2 * go * conj(gu)
+              o0[j] = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
+            } else {
+              o0[j] = make_float2(gor, goi);
+              o1[j] = make_float2(gur, gui);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// ---------------------------------------------------------------------- operand preparation
+
+__global__ void maxabs_kernel(const float2* __restrict__ x, size_t n, unsigned int* __restrict__ out) {
+  float m = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // non-negative floats order as uints
+}
+
+// e such that max|x| * 2^e lies in [2^14, 2^15)
+__global__ void exponent_kernel(const unsigned int* __restrict__ maxbits, int* __restrict__ e) {
+  const float m = __uint_as_float(*maxbits);
+  int ex = 0;
+  if (m > 0.f) {
+    frexpf(m, &ex);        // m = f * 2^ex, f in [0.5, 1)
+    *e = 15 - ex;
+  } else {
+    *e = 0;
+  }
+}
+
+template <uint32_t FMT>
+__device__ __forceinline__ void split(float x, uint16_t& hi, uint16_t& lo) {
+  if (FMT == 0) {
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(l);
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+  }
+}
+
+// Operand rows from psi [N_b][N_r] (band-major), transposed to K-major through a
+// 32 x 32 shared tile.  Band k goes to real column kcol(k) = 2k (occupied) or
+// k_un_x + 2(k - n_occ) (unoccupied); padding columns are written as zero.
+//  A: row r (rows r0..r0+rows-1):  (ar, ai) * s_k * 2^e
+//  B: rows 2R', 2R'+1:             (br, -bi) and (bi, br) of conj(psi) * 2^e
+template <bool IS_B, uint32_t FMT>
+__global__ void __launch_bounds__(256) prep_kernel(const float2* __restrict__ psi, int n_b, int n_occ, int nr, int r0,
+                                                   int rows, const float* __restrict__ sk,
+                                                   const int* __restrict__ dexp, int k_occ_pad, int k_un_x,
+                                                   int kpad, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+  __shared__ float2 t[32][33];
+  const int kb = blockIdx.y * 32;       // band tile (covers padded band slots)
+  const int rb = blockIdx.x * 32;       // row tile
+  const float sc = ldexpf(1.0f, *dexp);
+  // band slot -> band index (or -1 for padding)
+  const int occ_slots = k_occ_pad / 2, un_slots = (kpad - k_un_x) / 2;
+  auto band_of = [&](int slot) -> int {
+    if (slot < occ_slots) return slot < n_occ ? slot : -1;
+    const int u = slot - occ_slots;
+    return (u < un_slots && n_occ + u < n_b) ? n_occ + u : -1;
+  };
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int band = band_of(kb + i);
+    const int r = r0 + rb + threadIdx.x;
+    float2 v = make_float2(0.f, 0.f);
+    if (band >= 0 && rb + threadIdx.x < rows) {
+      v = psi[(long)band * nr + r];
+      const float s = IS_B ? sc : sc * sk[band];
+      v.x *= s;
+      v.y *= s;
+    }
+    t[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int rr = rb + i;
+    if (rr >= rows) continue;
+    const int slot = kb + threadIdx.x;
+    const int col = slot < occ_slots ? 2 * slot : k_un_x + 2 * (slot - occ_slots);
+    if (col >= kpad) continue;
+    const float2 v = t[threadIdx.x][i];
+    uint16_t h0, l0, h1, l1;
+    if (!IS_B) {
+      split<FMT>(v.x, h0, l0);
+      split<FMT>(v.y, h1, l1);
+      const long o = (long)rr * kpad + col;
+      reinterpret_cast<uint32_t*>(hi + o)[0] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+      reinterpret_cast<uint32_t*>(lo + o)[0] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    } else {
+      // b = conj(psi): br = v.x, bi = -v.y;  row 2R': (br, -bi) = (v.x, v.y); row 2R'+1: (bi, br) = (-v.y, v.x)
+      split<FMT>(v.x, h0, l0);
+      split<FMT>(v.y, h1, l1);
+      const long o0 = (long)(2 * rr) * kpad + col;
+      reinterpret_cast<uint32_t*>(hi + o0)[0] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+      reinterpret_cast<uint32_t*>(lo + o0)[0] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+      uint16_t h2, l2;
+      split<FMT>(-v.y, h2, l2);
+      const long o1 = o0 + kpad;
+      reinterpret_cast<uint32_t*>(hi + o1)[0] = (uint32_t)h2 | ((uint32_t)h0 << 16);
+      reinterpret_cast<uint32_t*>(lo + o1)[0] = (uint32_t)l2 | ((uint32_t)l0 << 16);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------- host side
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeFn encoder(gw_ctx* ctx, gw_status* st) {
+  static std::mutex mu;
+  static EncodeFn fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+      *st = fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+      return nullptr;
+    }
+    fn = reinterpret_cast<EncodeFn>(p);
+  }
+  *st = GW_OK;
+  return fn;
+}
+
+// 2-D map over a [rows][kpad] 16-bit row-major array, box = 64 x box_rows, 128-byte swizzle.
+static gw_status make_map(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, long rows, int box_rows,
+                          uint32_t fmt) {
+  gw_status st;
+  EncodeFn enc = encoder(ctx, &st);
+  if (!enc) return st;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return GW_OK;
+}
+
+struct Layout {
+  int k_occ_pad, k_un_pad, k_un_x, kpad;
+};
+static Layout layout(int n_b, int n_occ) {
+  Layout L;
+  L.k_occ_pad = (2 * n_occ + BK - 1) / BK * BK;
+  L.k_un_pad = (2 * (n_b - n_occ) + BK - 1) / BK * BK;
+  L.k_un_x = L.k_occ_pad;
+  L.kpad = L.k_occ_pad + L.k_un_pad;
+  return L;
+}
+
+static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp) {
+  const Layout L = layout(n_b, n_occ);
+  Carver probe(nullptr);
+  probe.take<unsigned int>(64);
+  probe.take<float>(n_b);
+  probe.take<uint16_t>((size_t)2 * g.nr * L.kpad);
+  probe.take<uint16_t>((size_t)2 * g.nr * L.kpad);
+  probe.take<uint16_t>((size_t)n_rows * L.kpad);
+  probe.take<uint16_t>((size_t)n_rows * L.kpad);
+  if (with_tmp) probe.take<float2>((size_t)n_rows * g.nr);
+  return Carver::round(probe.off);
+}
+
+// One G/chi formation for rows r0 .. r0+n_rows-1 using `scratch` (of at least
+// scratch_bytes()).  mode 0: chi into out0; mode 1: G_occ into out0 and G_unocc
+// into out1 (a NULL one goes to scratch).  prep_b = false reuses the B operand
+// and the operand scaling left in the same scratch by an earlier call for the
+// same psi.
+static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
+                     int r0, int n_rows, gw_prec prec, int mode, void* out0, void* out1, void* scratch, bool prep_b,
+                     cudaStream_t st) {
+  const uint32_t fmt = prec == GW_BF16X3 ? 1u : 0u;
+  const Layout L = layout(n_b, n_occ);
+  gw_status rc;
+  const bool need_tmp = mode == 1 && (!out0 || !out1);
+  Carver cv(scratch);
+  unsigned int* dmax = cv.take<unsigned int>(64);
+  int* dexp = reinterpret_cast<int*>(dmax + 1);
+  int* status = reinterpret_cast<int*>(dmax + 2);
+  float* dsk = cv.take<float>(n_b);
+  uint16_t* bhi = cv.take<uint16_t>((size_t)2 * g.nr * L.kpad);
+  uint16_t* blo = cv.take<uint16_t>((size_t)2 * g.nr * L.kpad);
+  uint16_t* ahi = cv.take<uint16_t>((size_t)n_rows * L.kpad);
+  uint16_t* alo = cv.take<uint16_t>((size_t)n_rows * L.kpad);
+  float2* tmp = need_tmp ? cv.take<float2>((size_t)n_rows * g.nr) : nullptr;
+  if (mode == 1) {
+    if (!out0) out0 = tmp;
+    if (!out1) out1 = tmp;
+  }
+  std::vector<float> skf(gs.s.begin(), gs.s.end());
+  if ((rc = upload(ctx, dsk, skf.data(), sizeof(float) * n_b, st))) return rc;
+  const dim3 tb(32, 8);
+  const int slots = L.kpad / 2;
+  if (prep_b) {
+    if ((rc = cuda_check(ctx, cudaMemsetAsync(dmax, 0, 64 * sizeof(unsigned int), st), "memset"))) return rc;
+    const size_t nel = (size_t)n_b * g.nr;
+    maxabs_kernel<<<std::min<size_t>((nel + 255) / 256, (size_t)ctx->num_sms * 8), 256, 0, st>>>(
+        static_cast<const float2*>(psi), nel, dmax);
+    if ((rc = launch_check(ctx, "maxabs_kernel"))) return rc;
+    exponent_kernel<<<1, 1, 0, st>>>(dmax, dexp);
+    if ((rc = launch_check(ctx, "exponent_kernel"))) return rc;
+    const dim3 gbB((g.nr + 31) / 32, (slots + 31) / 32);
+    if (fmt == 0)
+      prep_kernel<true, 0><<<gbB, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, 0, g.nr, dsk, dexp,
+                                                L.k_occ_pad, L.k_un_x, L.kpad, bhi, blo);
+    else
+      prep_kernel<true, 1><<<gbB, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, 0, g.nr, dsk, dexp,
+                                                L.k_occ_pad, L.k_un_x, L.kpad, bhi, blo);
+    if ((rc = launch_check(ctx, "prep_kernel(B)"))) return rc;
+  } else {
+    if ((rc = cuda_check(ctx, cudaMemsetAsync(status, 0, 2 * sizeof(int), st), "memset"))) return rc;
+  }
+  const dim3 gbA((n_rows + 31) / 32, (slots + 31) / 32);
+  if (fmt == 0)
+    prep_kernel<false, 0><<<gbA, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, r0, n_rows, dsk, dexp,
+                                               L.k_occ_pad, L.k_un_x, L.kpad, ahi, alo);
+  else
+    prep_kernel<false, 1><<<gbA, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, r0, n_rows, dsk, dexp,
+                                               L.k_occ_pad, L.k_un_x, L.kpad, ahi, alo);
+  if ((rc = launch_check(ctx, "prep_kernel(A)"))) return rc;
+  CUtensorMap mah, mal, mbh, mbl;
+  if ((rc = make_map(ctx, &mah, ahi, L.kpad, n_rows, BM, fmt))) return rc;
+  if ((rc = make_map(ctx, &mal, alo, L.kpad, n_rows, BM, fmt))) return rc;
+  if ((rc = make_map(ctx, &mbh, bhi, L.kpad, 2L * g.nr, 2 * BNC, fmt))) return rc;
+  if ((rc = make_map(ctx, &mbl, blo, L.kpad, 2L * g.nr, 2 * BNC, fmt))) return rc;
+  Params P;
+  P.m_rows = n_rows;
+  P.n_cols = g.nr;
+  P.k_occ_steps = L.k_occ_pad / BK;
+  P.k_un_steps = L.k_un_pad / BK;
+  P.k_un_x = L.k_un_x;
+  P.out0 = static_cast<float2*>(out0);
+  P.out1 = static_cast<float2*>(mode == 1 ? out1 : out0);
+  P.ldo = g.nr;
+  P.alpha_occ = (float)gs.amax_occ;
+  P.alpha_un = (float)gs.amax_unocc;
+  P.dexp = dexp;
+  P.status = status;
+  const dim3 grid((g.nr + BNC - 1) / BNC, (n_rows + BM - 1) / BM);
+  auto go = [&](auto kernel) -> gw_status {
+    gw_status r = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
+                             "cudaFuncSetAttribute");
+    if (r) return r;
+    kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mah, mal, mbh, mbl, P);
+    return launch_check(ctx, "green_tc_kernel");
+  };
+  if (mode == 0) rc = fmt == 0 ? go(green_tc_kernel<0, 0>) : go(green_tc_kernel<0, 1>);
+  else rc = fmt == 0 ? go(green_tc_kernel<1, 0>) : go(green_tc_kernel<1, 1>);
+  return rc;
+}
+
+// Reads the status word the kernels' bounded waits write (synchronises the stream).
+static gw_status check_status(gw_ctx* ctx, void* scratch, cudaStream_t st) {
+  int hs[2] = {0, 0};
+  const int* status = reinterpret_cast<const int*>(static_cast<const unsigned int*>(scratch) + 2);
+  gw_status rc;
+  if ((rc = cuda_check(ctx, cudaMemcpyAsync(hs, status, sizeof(hs), cudaMemcpyDeviceToHost, st), "status"))) return rc;
+  if ((rc = cuda_check(ctx, cudaStreamSynchronize(st), "tensor-core GEMM"))) return rc;
+  if (hs[0]) return fail(ctx, GW_ERR_TIMEOUT, "tensor-core pipeline wait timed out (role " + std::to_string(hs[1]) + ")");
+  return GW_OK;
+}
+
+}  // namespace tc
+
+size_t tc_scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp) {
+  return tc::scratch_bytes(g, n_b, n_occ, n_rows, with_tmp);
+}
+
+gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
+                        int r0, int n_rows, gw_prec prec, void* g_occ, void* g_unocc, void* scratch, bool prep_b,
+                        cudaStream_t st) {
+  return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 1, g_occ, g_unocc, scratch, prep_b, st);
+}
+
+gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
+                      int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st) {
+  return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 0, chi, nullptr, scratch, prep_b, st);
+}
+
+gw_status tc_check(gw_ctx* ctx, void* scratch, cudaStream_t st) { return tc::check_status(ctx, scratch, st); }
 
 }  // namespace gw

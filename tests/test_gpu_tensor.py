@@ -1,0 +1,116 @@
+"""GPU parity of the tcgen05 split-precision contractions (GW_F16X3, GW_BF16X3)
+against the FP64 oracle: Green's-function rows, the fused chi product, the chi0
+chain, and the self-energy whose G tiles come from the tensor cores.
+
+The gate for the split precisions is Sigma_nn within 1 meV of the oracle.
+fp16 x 3 represents each operand to ~2^-22 (FP32: 2^-24), so its chi0(i omega)
+error is ~4x that of the FP32 path: 5e-6 relative Frobenius is its derived
+bar (the FP32 path keeps the 1e-6 target).  bf16 x 3 represents operands to
+~2^-16 and gets 2e-5."""
+import numpy as np
+import pytest
+
+from oracle import chi as ochi
+from oracle import green as ogr
+from oracle import pipeline as opipe
+from oracle import sigma as osg
+from paper_1607_02859_gb300 import gw, inputs
+
+pytestmark = pytest.mark.gpu
+MEV = 3.674932e-5
+torch = pytest.importorskip("torch")
+TOL = {"f16x3": 5e-6, "bf16x3": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import os
+    if not os.path.exists(gw.LIB_PATH):
+        from paper_1607_02859_gb300 import build
+        build.build()
+    c = gw.Context(0)
+    yield c
+    c.close()
+
+
+def relf(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=torch.complex64)
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+PROBLEMS = {
+    "tiny_c": lambda: inputs.tiny(seed=41),
+    "ragged": lambda: inputs.tiny(seed=43, n=(8, 6, 10), a=(7.0, 6.0, 8.0), n_occ=6, n_unocc=42, n_tau=8),
+    "k_multi": lambda: inputs.tiny(seed=44, n=(12, 12, 12), a=(9.0, 9.0, 9.0), n_occ=40, n_unocc=180, n_tau=6,
+                                   n_chi=400),
+}
+
+
+@pytest.fixture(scope="module", params=list(PROBLEMS))
+def case(request):
+    p = PROBLEMS[request.param]()
+    return request.param, p, opipe.setup(p)
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_green_rows(ctx, case, prec):
+    name, p, s = case
+    grid = gw.make_grid(p.n, p.lattice)
+    psi = dev(p.psi)
+    r0, rows = 5, p.n_r - 9                       # ragged rows: partial last tile
+    for tau in (p.tau[0], p.tau[-1]):
+        go = torch.zeros((rows, p.n_r), dtype=torch.complex64, device="cuda")
+        gu = torch.zeros_like(go)
+        gw.green_tau(ctx, grid, psi, p.eps, p.n_occ, p.mu, tau, r0, rows, prec, go, gu)
+        rr = np.arange(r0, r0 + rows)
+        assert relf(host(go), ogr.green_occ_rows(p.psi, p.eps, p.n_occ, p.mu, tau, rr)) < 4 * TOL[prec]
+        assert relf(host(gu), ogr.green_unocc_rows(p.psi, p.eps, p.n_occ, p.mu, tau, rr)) < 4 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_chi_rows(ctx, case, prec):
+    name, p, s = case
+    grid = gw.make_grid(p.n, p.lattice)
+    tau = p.tau[2]
+    chi = torch.zeros((p.n_r - 3, p.n_r), dtype=torch.complex64, device="cuda")
+    gw.chi0_rtau_fused(ctx, grid, dev(p.psi), p.eps, p.n_occ, p.mu, tau, 3, p.n_r - 3, prec, chi)
+    ref = ochi.chi_rr(ogr.green_occ(p.psi, p.eps, p.n_occ, p.mu, tau), ogr.green_unocc(p.psi, p.eps, p.n_occ, p.mu, tau))
+    assert relf(host(chi), ref[3:]) < 4 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_chi0_omega(ctx, case, prec):
+    name, p, s = case
+    grid = gw.make_grid(p.n, p.lattice)
+    chi_ref, _ = opipe.chi0_omega(p, s)
+    nchi = len(s["fft_index"])
+    for rb in (0, 100):
+        out = torch.zeros((len(p.tau), nchi, nchi), dtype=torch.complex64, device="cuda")
+        gw.chi0_omega(ctx, grid, dev(p.psi), p.eps, p.n_occ, p.mu, p.tau, s["C"], s["fft_index"], prec, out,
+                      r_block=rb)
+        assert relf(host(out), chi_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_sigma(ctx, case, prec):
+    name, p, s = case
+    grid = gw.make_grid(p.n, p.lattice)
+    chi_ref, _ = opipe.chi0_omega(p, s)
+    wt, _ = opipe.w_tau(p, s, chi_ref)
+    su, so = opipe.sigma_from_w(p, s, wt)
+    sig_ref = osg.sigma_iw(su, so, s["C"], s["S"])
+    out = gw.sigma_diag(ctx, grid, dev(p.psi), p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, s["C"], s["S"],
+                        dev(wt), s["fft_index"], prec)
+    err = np.max(np.abs(out["sigma_iw"] - sig_ref))
+    assert err < MEV
+    if prec == "f16x3":
+        assert err < 1e-4 * np.max(np.abs(sig_ref))
