@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "gw_kernels.h"
+#include "gw_tc.h"
 
 namespace gw {
 
@@ -106,13 +107,14 @@ __global__ void __launch_bounds__(64) trsm_panel_kernel(typename cpx<T>::t* A, l
 // P[rows below][k0 .. k0+kb) = -L[rows below][k0 .. k0+kb): the identity part of
 // (1 + P) contributes L_li * 1 to the update of the rows below block row i.
 template <typename T>
-__global__ void neg_copy_kernel(const typename cpx<T>::t* __restrict__ Lm, typename cpx<T>::t* __restrict__ P, long ld,
-                                int row0, int rows, int col0, int kb) {
-  const int c = threadIdx.x;
+__global__ void neg_copy_kernel(const typename cpx<T>::t* __restrict__ Lm, typename cpx<T>::t* __restrict__ P, long ldl,
+                                long ldp, int row0, int rows, int col0, int kb) {
   const long r = row0 + (long)blockIdx.x;
-  if (c >= kb || blockIdx.x >= rows) return;
-  const auto v = Lm[r * ld + col0 + c];
-  P[r * ld + col0 + c] = mk(-v.x, -v.y);
+  if (blockIdx.x >= rows) return;
+  for (int c = threadIdx.x; c < kb; c += blockDim.x) {
+    const auto v = Lm[r * ldl + col0 + c];
+    P[r * ldp + col0 + c] = mk(-v.x, -v.y);
+  }
 }
 
 // Y = L_ii^{-1} Y for the block rows k0..k0+kb-1 and columns 0..ncols-1 of Y.
@@ -219,16 +221,13 @@ __global__ void __launch_bounds__(256) hemv_probe_kernel(const typename cpx<T>::
   if (threadIdx.x == 0) y[a] = make_double2(sr[0], si[0]);
 }
 
+// Cholesky (lower, K form on the diagonal) of the n x n block at a (leading
+// dimension lda) on CUDA cores, 64-column panels.  col0 labels pivots.
 template <typename T>
-static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, const double* dvh, void* E, void* Mi,
-                            void* W, double2* probe, double* resid_h, cudaStream_t st) {
+static gw_status chol_simt(gw_ctx* ctx, gw_prec prec, typename cpx<T>::t* a, long lda, int n, int col0,
+                           cudaStream_t st) {
   using C = typename cpx<T>::t;
   gw_status rc;
-  C* e = static_cast<C*>(E);
-  C* m = static_cast<C*>(Mi);
-  const dim3 tb(128), gb((n + 127) / 128, n);
-  build_eps_kernel<T><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), dvh, e, n);
-  if ((rc = launch_check(ctx, "build_eps_kernel"))) return rc;
   const size_t tsm = sizeof(C) * (kNB * (kNB + 1) + kNB * 64);
   const size_t psm = sizeof(C) * kNB * (kNB + 1);
   if (tsm > 48 * 1024) {
@@ -237,14 +236,13 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
   }
   if (psm > 48 * 1024)
     cudaFuncSetAttribute(potrf_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
-  // 1. eps~ = L L^H
   for (int k0 = 0; k0 < n; k0 += kNB) {
     const int kb = std::min(kNB, n - k0);
-    potrf_diag_kernel<T><<<1, 256, psm, st>>>(e + (long)k0 * n + k0, n, kb, ctx->dflag, k0);
+    potrf_diag_kernel<T><<<1, 256, psm, st>>>(a + (long)k0 * lda + k0, lda, kb, ctx->dflag, col0 + k0);
     if ((rc = launch_check(ctx, "potrf_diag_kernel"))) return rc;
     const int rows = n - k0 - kb;
     if (rows <= 0) break;
-    trsm_panel_kernel<T><<<(rows + 63) / 64, 64, tsm, st>>>(e, n, k0, kb, rows);
+    trsm_panel_kernel<T><<<(rows + 63) / 64, 64, tsm, st>>>(a, lda, k0, kb, rows);
     if ((rc = launch_check(ctx, "trsm_panel_kernel"))) return rc;
     GemmArgs g{};
     g.M = rows;
@@ -252,28 +250,38 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
     g.K = kb;
     g.alpha_re = -1;
     g.beta = 1;
-    g.A = e + (long)(k0 + kb) * n + k0;
-    g.lda = n;
+    g.A = a + (long)(k0 + kb) * lda + k0;
+    g.lda = lda;
     g.a_km = 0;
-    g.B = e + (long)(k0 + kb) * n + k0;
-    g.ldb = n;
+    g.B = a + (long)(k0 + kb) * lda + k0;
+    g.ldb = lda;
     g.b_nk = 1;
     g.b_conj = true;
-    g.C = e + (long)(k0 + kb) * n + k0 + kb;
-    g.ldc = n;
+    g.C = a + (long)(k0 + kb) * lda + k0 + kb;
+    g.ldc = lda;
     g.tri = 1;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
   }
-  // 2. P = L^{-1} - 1
-  if ((rc = cuda_check(ctx, cudaMemsetAsync(m, 0, sizeof(C) * (size_t)n * n, st), "memset P"))) return rc;
+  return GW_OK;
+}
+
+// P = L^{-1} - 1 for the n x n lower factor L (K form diagonal) at Lm, written
+// to the n x n block at p (both with their leading dimensions), CUDA cores.
+template <typename T>
+static gw_status inv_simt(gw_ctx* ctx, gw_prec prec, const typename cpx<T>::t* Lm, long ldl, typename cpx<T>::t* p,
+                          long ldp, int n, cudaStream_t st) {
+  using C = typename cpx<T>::t;
+  gw_status rc;
+  const size_t tsm = sizeof(C) * (kNB * (kNB + 1) + kNB * 64);
+  if ((rc = cuda_check(ctx, cudaMemset2DAsync(p, ldp * sizeof(C), 0, n * sizeof(C), n, st), "memset P"))) return rc;
   for (int k0 = 0; k0 < n; k0 += kNB) {
     const int kb = std::min(kNB, n - k0);
     const int ncols = k0 + kb;
-    trsm_left_kernel<T><<<(ncols + 63) / 64, 64, tsm, st>>>(e, n, m, n, k0, kb, ncols);
+    trsm_left_kernel<T><<<(ncols + 63) / 64, 64, tsm, st>>>(Lm, ldl, p, ldp, k0, kb, ncols);
     if ((rc = launch_check(ctx, "trsm_left_kernel"))) return rc;
     const int rows = n - k0 - kb;
     if (rows <= 0) break;
-    neg_copy_kernel<T><<<rows, kNB, 0, st>>>(e, m, n, k0 + kb, rows, k0, kb);
+    neg_copy_kernel<T><<<rows, kNB, 0, st>>>(Lm, p, ldl, ldp, k0 + kb, rows, k0, kb);
     if ((rc = launch_check(ctx, "neg_copy_kernel"))) return rc;
     GemmArgs g{};
     g.M = rows;
@@ -281,36 +289,25 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
     g.K = kb;
     g.alpha_re = -1;
     g.beta = 1;
-    g.A = e + (long)(k0 + kb) * n + k0;
-    g.lda = n;
-    g.B = m + (long)k0 * n;
-    g.ldb = n;
-    g.C = m + (long)(k0 + kb) * n;
-    g.ldc = n;
+    g.A = Lm + (long)(k0 + kb) * ldl + k0;
+    g.lda = ldl;
+    g.B = p + (long)k0 * ldp;
+    g.ldb = ldp;
+    g.C = p + (long)(k0 + kb) * ldp;
+    g.ldc = ldp;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
   }
-  // 3. eps~^{-1} - 1 = P^H P + P + P^H (lower) into E
+  return GW_OK;
+}
+
+// |eps~ X z - chi~ z| / |chi~ z| over 4 seeded probes z, in FP64, with X the
+// assembled lower triangle of eps~^{-1} - 1 and chi still intact.
+template <typename T>
+static gw_status residual_probe(gw_ctx* ctx, int n, const void* chi, const double* dvh,
+                                const typename cpx<T>::t* e, double2* probe, double* resid_h, cudaStream_t st) {
+  using C = typename cpx<T>::t;
+  gw_status rc;
   {
-    GemmArgs g{};
-    g.M = n;
-    g.N = n;
-    g.K = n;
-    g.alpha_re = 1;
-    g.beta = 0;
-    g.A = m;
-    g.lda = n;
-    g.a_km = 1;
-    g.a_conj = true;
-    g.B = m;
-    g.ldb = n;
-    g.C = e;
-    g.ldc = n;
-    g.tri = 2;
-    if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
-  }
-  assemble_kernel<T><<<gb, tb, 0, st>>>(e, m, n);
-  if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
-  if (resid_h) {
     // |eps~ X z - chi~ z| / |chi~ z| over 4 probes, X = eps~^{-1} - 1 (before chi may be overwritten)
     double num = 0, den = 0;
     std::vector<double2> hz(n), hu(n), hw(n), hc(n);
@@ -343,7 +340,129 @@ static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, c
     }
     *resid_h = den > 0 ? std::sqrt(num / den) : 0.0;
   }
+  return GW_OK;
+}
+
+template <typename T>
+static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, const double* dvh, void* E, void* Mi,
+                            void* W, double2* probe, double* resid_h, cudaStream_t st) {
+  using C = typename cpx<T>::t;
+  gw_status rc;
+  C* e = static_cast<C*>(E);
+  C* m = static_cast<C*>(Mi);
+  const dim3 tb(128), gb((n + 127) / 128, n);
+  build_eps_kernel<T><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), dvh, e, n);
+  if ((rc = launch_check(ctx, "build_eps_kernel"))) return rc;
+  // 1. eps~ = L L^H
+  if ((rc = chol_simt<T>(ctx, prec, e, n, n, 0, st))) return rc;
+  // 2. P = L^{-1} - 1
+  if ((rc = inv_simt<T>(ctx, prec, e, n, m, n, n, st))) return rc;
+  // 3. eps~^{-1} - 1 = P^H P + P + P^H (lower) into E
+  {
+    GemmArgs g{};
+    g.M = n;
+    g.N = n;
+    g.K = n;
+    g.alpha_re = 1;
+    g.beta = 0;
+    g.A = m;
+    g.lda = n;
+    g.a_km = 1;
+    g.a_conj = true;
+    g.B = m;
+    g.ldb = n;
+    g.C = e;
+    g.ldc = n;
+    g.tri = 2;
+    if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
+  }
+  assemble_kernel<T><<<gb, tb, 0, st>>>(e, m, n);
+  if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
+  if (resid_h && (rc = residual_probe<T>(ctx, n, chi, dvh, e, probe, resid_h, st))) return rc;
   finalize_kernel<T><<<gb, tb, 0, st>>>(e, dvh, static_cast<C*>(W), n);
+  return launch_check(ctx, "finalize_kernel");
+}
+
+// Tensor-core precisions: the same factorisation with 256-column panels.  The
+// 256 x 256 diagonal blocks are factored and inverted on CUDA cores (the
+// functions above); everything with a 256-wide inner dimension is a tcgen05
+// GEMM with split 16-bit products:
+//   L21 = A21 (1 + P11)^H       (panel solve through the inverted block)
+//   A22 -= L21 L21^H             (trailing update, lower tiles)
+//   P_i[:, <k0] += P_ii P_i[:, <k0],  rows below -= L_li (1 + P_i)
+//   X = P^H P                    (lower, k loop from the tile's first row)
+constexpr int kTB = 256;
+
+static size_t tc_screen_scratch(int n) { return tc_gemm_scratch(n, n, n); }
+
+static gw_status screen_one_tc(gw_ctx* ctx, gw_prec prec, int n, const void* chi, const double* dvh, void* E, void* Mi,
+                               void* W, double2* probe, double* resid_h, void* tcs, cudaStream_t st) {
+  using C = float2;
+  gw_status rc;
+  C* e = static_cast<C*>(E);
+  C* p = static_cast<C*>(Mi);
+  int* tstat = ctx->dflag + 4;
+  const dim3 tb(128), gb((n + 127) / 128, n);
+  build_eps_kernel<float><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), dvh, e, n);
+  if ((rc = launch_check(ctx, "build_eps_kernel"))) return rc;
+  if ((rc = cuda_check(ctx, cudaMemsetAsync(p, 0, sizeof(C) * (size_t)n * n, st), "memset P"))) return rc;
+  auto gemm = [&](int M, int N, int K, const C* A, bool at, bool ac, const C* B, bool bt, bool bc, C* Cm, float alpha,
+                  bool acc, int tri) {
+    TcGemm g;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = A;
+    g.lda = n;
+    g.a_trans = at;
+    g.a_conj = ac;
+    g.B = B;
+    g.ldb = n;
+    g.b_trans = bt;
+    g.b_conj = bc;
+    g.C = Cm;
+    g.ldc = n;
+    g.alpha = alpha;
+    g.accumulate = acc;
+    g.tri = tri;
+    g.status = tstat;
+    return tc_gemm(ctx, prec, g, tcs, st);
+  };
+  // 1. Cholesky, and the inverted diagonal blocks P_kk
+  for (int k0 = 0; k0 < n; k0 += kTB) {
+    const int kb = std::min(kTB, n - k0);
+    C* akk = e + (long)k0 * n + k0;
+    C* pkk = p + (long)k0 * n + k0;
+    if ((rc = chol_simt<float>(ctx, GW_FP32, akk, n, kb, k0, st))) return rc;
+    if ((rc = inv_simt<float>(ctx, GW_FP32, akk, n, pkk, n, kb, st))) return rc;
+    const int rows = n - k0 - kb;
+    if (rows <= 0) break;
+    C* a21 = e + (long)(k0 + kb) * n + k0;
+    // L21 = A21 + A21 P_kk^H   (opB(k, j) = conj(P_kk[j][k]))
+    if ((rc = gemm(rows, kb, kb, a21, false, false, pkk, true, true, a21, 1.0f, true, 0))) return rc;
+    // A22 -= L21 L21^H
+    if ((rc = gemm(rows, rows, kb, a21, false, false, a21, true, true, a21 + kb, -1.0f, true, 1))) return rc;
+  }
+  // 2. off-diagonal blocks of P = L^{-1} - 1, block row by block row
+  for (int k0 = 0; k0 < n; k0 += kTB) {
+    const int kb = std::min(kTB, n - k0);
+    C* pi = p + (long)k0 * n;                    // block row i, columns from 0
+    C* pkk = pi + k0;
+    if (k0 > 0 && (rc = gemm(kb, k0, kb, pkk, false, false, pi, false, false, pi, 1.0f, true, 0))) return rc;
+    const int rows = n - k0 - kb;
+    if (rows <= 0) break;
+    neg_copy_kernel<float><<<rows, 256, 0, st>>>(e, p, n, n, k0 + kb, rows, k0, kb);
+    if ((rc = launch_check(ctx, "neg_copy_kernel"))) return rc;
+    if ((rc = gemm(rows, k0 + kb, kb, e + (long)(k0 + kb) * n + k0, false, false, pi, false, false,
+                   p + (long)(k0 + kb) * n, -1.0f, true, 0)))
+      return rc;
+  }
+  // 3. P^H P (lower) into E, then + P + P^H
+  if ((rc = gemm(n, n, n, p, true, true, p, false, false, e, 1.0f, false, 2))) return rc;
+  assemble_kernel<float><<<gb, tb, 0, st>>>(e, p, n);
+  if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
+  if (resid_h && (rc = residual_probe<float>(ctx, n, chi, dvh, e, probe, resid_h, st))) return rc;
+  finalize_kernel<float><<<gb, tb, 0, st>>>(e, dvh, static_cast<C*>(W), n);
   return launch_check(ctx, "finalize_kernel");
 }
 
@@ -371,25 +490,31 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
   probe.take<char>(nn * es);
   probe.take<char>(nn * es);
   probe.take<double2>(4 * (size_t)n_chi);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  if (tc) probe.take<char>(tc_screen_scratch(n_chi));
   if ((st = reserve(ctx, probe.off))) return st;
   Carver cv(ctx->arena);
   double* dvh = cv.take<double>(n_chi);
   void* E = cv.take<char>(nn * es);
   void* M = cv.take<char>(nn * es);
   double2* pr = cv.take<double2>(4 * (size_t)n_chi);
+  void* tcs = tc ? cv.take<char>(tc_screen_scratch(n_chi)) : nullptr;
   if ((st = upload(ctx, dvh, vh.data(), sizeof(double) * n_chi, s))) return st;
-  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 2 * sizeof(int), s), "memset flag"))) return st;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 8 * sizeof(int), s), "memset flag"))) return st;
   for (int k = 0; k < n_omega; ++k) {
     const char* in = static_cast<const char*>(chi_w) + k * nn * es;
     char* out = static_cast<char*>(w_w) + k * nn * es;
-    st = is_fp64(prec) ? screen_one<double>(ctx, prec, n_chi, in, dvh, E, M, out, pr, resid_h ? resid_h + k : nullptr, s)
-                       : screen_one<float>(ctx, prec, n_chi, in, dvh, E, M, out, pr, resid_h ? resid_h + k : nullptr, s);
+    double* rk = resid_h ? resid_h + k : nullptr;
+    if (tc) st = screen_one_tc(ctx, prec, n_chi, in, dvh, E, M, out, pr, rk, tcs, s);
+    else if (is_fp64(prec)) st = screen_one<double>(ctx, prec, n_chi, in, dvh, E, M, out, pr, rk, s);
+    else st = screen_one<float>(ctx, prec, n_chi, in, dvh, E, M, out, pr, rk, s);
     if (st) return st;
   }
-  int flag[2] = {0, 0};
+  int flag[8] = {0};
   if ((st = cuda_check(ctx, cudaMemcpyAsync(flag, ctx->dflag, sizeof(flag), cudaMemcpyDeviceToHost, s), "flag")))
     return st;
   if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
+  if (flag[4]) return fail(ctx, GW_ERR_TIMEOUT, "tensor-core GEMM wait timed out (role " + std::to_string(flag[5]) + ")");
   if (flag[0]) return fail(ctx, GW_ERR_NUMERIC, "eps~ not positive definite at column " + std::to_string(flag[1]));
   return GW_OK;
 }

@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05) split-precision contractions (internal).
 #pragma once
 
+#include <cuda.h>
+
 #include "gw_kernels.h"
 
 namespace gw {
@@ -20,5 +22,33 @@ gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const 
 // Synchronises and reports a time-out of the tensor-core pipeline waits
 // (GW_ERR_TIMEOUT) recorded in `scratch` since its last prep_b call.
 gw_status tc_check(gw_ctx* ctx, void* scratch, cudaStream_t st);
+
+// 2-D TMA map over a [rows][kpad] row-major 16-bit array (fmt 0: fp16, 1: bf16),
+// box 64 x box_rows, 128-byte swizzle.
+gw_status tc_make_map(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, long rows, int box_rows,
+                      uint32_t fmt);
+
+// C = alpha * opA(A) opB(B) (+ C if accumulate) on tcgen05 tensor cores with
+// split 16-bit products; opA(m,k) = A[m][k] or A[k][m] (a_trans), conjugated if
+// a_conj; opB(k,n) = B[k][n] or B[n][k] (b_trans), conjugated if b_conj.
+// tri = 1: only m >= n; tri = 2: also start each tile's k loop at its first row.
+// The operands are converted to split copies first, so C may alias A or B.
+struct TcGemm {
+  int M, N, K;
+  const float2* A;
+  long lda;
+  bool a_trans, a_conj;
+  const float2* B;
+  long ldb;
+  bool b_trans, b_conj;
+  float2* C;
+  long ldc;
+  float alpha;
+  bool accumulate;
+  int tri;
+  int* status;          // device: 2 ints, set on a pipeline time-out
+};
+size_t tc_gemm_scratch(int M, int N, int K);
+gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cudaStream_t st);
 
 }  // namespace gw

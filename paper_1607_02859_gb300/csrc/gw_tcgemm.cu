@@ -1,0 +1,321 @@
+// General complex GEMM on tcgen05 tensor cores with split 16-bit products,
+// used by the screening step (Eqs. die, W_correlated) for the tensor-core
+// precisions:
+//   C[m][n] = alpha * sum_k opA(m,k) opB(k,n)   (+ C[m][n] if accumulate)
+// opA(m,k) = A[m][k] or A[k][m] (a_trans), conjugated if a_conj; opB likewise.
+// The complex-to-real mapping, the hi/lo split and the TMA/mbarrier/TMEM
+// pipeline are those of the Green's-function kernel (gw_tc.cu): A becomes a
+// real [M][2K] operand with (re, im) interleaved along K, B two real rows per
+// complex column, (br, -bi) and (bi, br), so the FP32 accumulator holds
+// (re, im) pairs.  tri = 1 writes only m >= n (and skips tiles above the
+// diagonal); tri = 2 also starts each tile's k loop at its first row, for
+// products X^H X with X lower triangular.
+#include <algorithm>
+
+#include "gw_tc.h"
+#include "gw_tcgen05.cuh"
+
+namespace gw {
+namespace tg {
+
+using namespace tcx;
+
+constexpr int BM = 128, BNC = 128, BK = 64, STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = 2 * BNC * BK * 2;
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int THREADS = 192;
+
+struct KParams {
+  int M, N;               // complex output size
+  int k_steps;            // BK stages over the padded real K
+  float2* C;
+  long ldc;
+  float alpha;
+  int accumulate;
+  const unsigned int* maxbits;   // [0] A, [1] B: max |component| (float bits)
+  int* status;
+};
+
+__device__ __forceinline__ int scale_exp(unsigned int bits) {
+  const float m = __uint_as_float(bits);
+  int ex = 0;
+  if (!(m > 0.f)) return 0;
+  frexpf(m, &ex);
+  return 15 - ex;
+}
+
+template <uint32_t FMT, int TRI>
+__global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_constant__ CUtensorMap mA_hi,
+                                                              const __grid_constant__ CUtensorMap mA_lo,
+                                                              const __grid_constant__ CUtensorMap mB_hi,
+                                                              const __grid_constant__ CUtensorMap mB_lo, KParams p) {
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * BNC;
+  if (TRI && n0 > m0 + BM - 1) return;          // tile entirely above the diagonal
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int first = TRI == 2 ? min(2 * m0 / BK, p.k_steps) : 0;
+  const int total = p.k_steps - first;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto timed_out = [&](int where) {
+    *abort_flag = 1;
+    if (atomicCAS(p.status, 0, 1) == 0) p.status[1] = where;
+  };
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int it = 0; it < total && !*abort_flag; ++it) {
+      const int s = it % STAGES;
+      if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
+        timed_out(11);
+        break;
+      }
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const int x = (first + it) * BK;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(st, &mA_hi, &full[s], x, m0);
+      tma_load_2d(st + A_BYTES, &mA_lo, &full[s], x, m0);
+      tma_load_2d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * n0);
+      tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * n0);
+      issued = it + 1;
+    }
+    if (*abort_flag)
+      for (int it = issued - STAGES < 0 ? 0 : issued - STAGES; it < issued; ++it)
+        mbar_wait(&full[it % STAGES], (it / STAGES) & 1);
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = make_idesc(FMT, 2 * BNC, BM);
+    for (int it = 0; it < total && !*abort_flag; ++it) {
+      const int s = it % STAGES;
+      if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
+        timed_out(12);
+        break;
+      }
+      tc_fence_after();
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_BYTES);
+      const uint64_t bh = sw128_desc(st + 2 * A_BYTES), bl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t off = (uint64_t)(kk * 32) >> 4;
+        umma(tmem, ah + off, bh + off, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        umma(tmem, ah + off, bl + off, idesc, 1u);
+        umma(tmem, al + off, bh + off, idesc, 1u);
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);
+  } else if (warp >= 2) {
+    const bool ok = mbar_wait(done, 0);
+    if (!ok) timed_out(13);
+    tc_fence_after();
+    if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
+      const int q = warp & 3;
+      const int row = q * 32 + lane;
+      const int gm = m0 + row;
+      const float sc = p.alpha * ldexpf(1.0f, -(scale_exp(p.maxbits[0]) + scale_exp(p.maxbits[1])));
+      const bool have = total > 0;
+      const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+#pragma unroll 1
+      for (int c = 0; c < 2 * BNC; c += 16) {
+        uint32_t r[16];
+        if (have) {
+          tmem_ld16(tmem + lane_addr + c, r);
+          tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) r[j] = 0u;
+        }
+        if (gm < p.M) {
+          const int nc0 = n0 + c / 2;
+          float2* o = p.C + (long)gm * p.ldc + nc0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int gn = nc0 + j;
+            if (gn >= p.N) break;
+            if (TRI && gn > gm) break;
+            float2 v = make_float2(__uint_as_float(r[2 * j]) * sc, __uint_as_float(r[2 * j + 1]) * sc);
+            if (p.accumulate) {
+              const float2 old = o[j];
+              v.x += old.x;
+              v.y += old.y;
+            }
+            o[j] = v;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  }
+}
+
+// max |component| of op(X), rows x K elements of a strided matrix.
+__global__ void maxabs2d_kernel(const float2* __restrict__ X, long ld, int outer, int inner,
+                                unsigned int* __restrict__ out) {
+  float m = 0.f;
+  const long n = (long)outer * inner;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const long i = e / inner, j = e - i * inner;
+    const float2 v = X[i * ld + j];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Split operand rows.  Element (i, k) of op(X) (i < rows, k < K; padding
+// columns up to kp/2 are zero) goes to real columns 2k, 2k+1 of row i (A form)
+// or of rows 2i and 2i+1 as (br, -bi), (bi, br) (B form).  A 32 x 32 shared
+// tile makes both the read and the write coalesced for either layout.
+template <bool IS_B, uint32_t FMT>
+__global__ void __launch_bounds__(256) prep_op_kernel(const float2* __restrict__ X, long ld, int trans, int conj,
+                                                      int rows, int K, int kp, const unsigned int* __restrict__ maxbits,
+                                                      uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
+  __shared__ float2 t[32][33];                  // t[i][k]
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const float sc = ldexpf(1.0f, scale_exp(*maxbits));
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    // trans: X[k][i] is contiguous in i -> thread x walks i; else walks k
+    const int i = trans ? i0 + threadIdx.x : i0 + y;
+    const int k = trans ? k0 + y : k0 + threadIdx.x;
+    float2 v = make_float2(0.f, 0.f);
+    if (i < rows && k < K) {
+      v = trans ? X[(long)k * ld + i] : X[(long)i * ld + k];
+      if (conj) v.y = -v.y;
+      v.x *= sc;
+      v.y *= sc;
+    }
+    if (trans) t[threadIdx.x][y] = v;
+    else t[y][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int i = i0 + y, k = k0 + threadIdx.x;
+    if (i >= rows || 2 * k >= kp) continue;
+    const float2 v = t[y][threadIdx.x];
+    uint16_t h0, l0, h1, l1;
+    split<FMT>(v.x, h0, l0);
+    split<FMT>(v.y, h1, l1);
+    if (!IS_B) {
+      const long o = (long)i * kp + 2 * k;
+      reinterpret_cast<uint32_t*>(hi + o)[0] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+      reinterpret_cast<uint32_t*>(lo + o)[0] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    } else {
+      // rows 2i: (br, -bi); 2i+1: (bi, br)
+      uint16_t h2, l2;
+      split<FMT>(-v.y, h2, l2);
+      const long o0 = (long)(2 * i) * kp + 2 * k, o1 = o0 + kp;
+      reinterpret_cast<uint32_t*>(hi + o0)[0] = (uint32_t)h0 | ((uint32_t)h2 << 16);
+      reinterpret_cast<uint32_t*>(lo + o0)[0] = (uint32_t)l0 | ((uint32_t)l2 << 16);
+      reinterpret_cast<uint32_t*>(hi + o1)[0] = (uint32_t)h1 | ((uint32_t)h0 << 16);
+      reinterpret_cast<uint32_t*>(lo + o1)[0] = (uint32_t)l1 | ((uint32_t)l0 << 16);
+    }
+  }
+}
+
+}  // namespace tg
+
+size_t tc_gemm_scratch(int M, int N, int K) {
+  const size_t kp = (size_t)(2 * K + tg::BK - 1) / tg::BK * tg::BK;
+  Carver probe(nullptr);
+  probe.take<unsigned int>(64);
+  probe.take<uint16_t>((size_t)M * kp);
+  probe.take<uint16_t>((size_t)M * kp);
+  probe.take<uint16_t>((size_t)2 * N * kp);
+  probe.take<uint16_t>((size_t)2 * N * kp);
+  return Carver::round(probe.off);
+}
+
+gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cudaStream_t st) {
+  using namespace tg;
+  if (g.M <= 0 || g.N <= 0) return GW_OK;
+  const uint32_t fmt = prec == GW_BF16X3 ? 1u : 0u;
+  const int K = std::max(g.K, 1);
+  const int kp = (2 * K + BK - 1) / BK * BK;
+  Carver cv(scratch);
+  unsigned int* words = cv.take<unsigned int>(64);     // [0] max A, [1] max B
+  uint16_t* ahi = cv.take<uint16_t>((size_t)g.M * kp);
+  uint16_t* alo = cv.take<uint16_t>((size_t)g.M * kp);
+  uint16_t* bhi = cv.take<uint16_t>((size_t)2 * g.N * kp);
+  uint16_t* blo = cv.take<uint16_t>((size_t)2 * g.N * kp);
+  gw_status rc;
+  if ((rc = cuda_check(ctx, cudaMemsetAsync(words, 0, 2 * sizeof(unsigned int), st), "memset"))) return rc;
+  const int blocks = ctx->num_sms * 4;
+  // A is [M][K] (or [K][M] if transposed); B's op is [K][N]: stored [K][N], or [N][K] if transposed
+  maxabs2d_kernel<<<blocks, 256, 0, st>>>(g.A, g.lda, g.a_trans ? g.K : g.M, g.a_trans ? g.M : g.K, words);
+  maxabs2d_kernel<<<blocks, 256, 0, st>>>(g.B, g.ldb, g.b_trans ? g.N : g.K, g.b_trans ? g.K : g.N, words + 1);
+  if ((rc = launch_check(ctx, "maxabs2d_kernel"))) return rc;
+  ctx->launches++;
+  const dim3 tb(32, 8);
+  const dim3 ga((g.M + 31) / 32, (kp / 2 + 31) / 32), gb((g.N + 31) / 32, (kp / 2 + 31) / 32);
+  // B operand rows are indexed by n with k along the row: element (n, k) = opB(k, n), i.e.
+  // B[k][n] (stored [K][N]: "transposed" access for the row-major reader) or B[n][k] (b_trans).
+  if (fmt == 0) {
+    prep_op_kernel<false, 0><<<ga, tb, 0, st>>>(g.A, g.lda, g.a_trans, g.a_conj, g.M, g.K, kp, words, ahi, alo);
+    prep_op_kernel<true, 0><<<gb, tb, 0, st>>>(g.B, g.ldb, !g.b_trans, g.b_conj, g.N, g.K, kp, words + 1, bhi, blo);
+  } else {
+    prep_op_kernel<false, 1><<<ga, tb, 0, st>>>(g.A, g.lda, g.a_trans, g.a_conj, g.M, g.K, kp, words, ahi, alo);
+    prep_op_kernel<true, 1><<<gb, tb, 0, st>>>(g.B, g.ldb, !g.b_trans, g.b_conj, g.N, g.K, kp, words + 1, bhi, blo);
+  }
+  if ((rc = launch_check(ctx, "prep_op_kernel"))) return rc;
+  ctx->launches++;
+  CUtensorMap mah, mal, mbh, mbl;
+  if ((rc = tc_make_map(ctx, &mah, ahi, kp, g.M, BM, fmt))) return rc;
+  if ((rc = tc_make_map(ctx, &mal, alo, kp, g.M, BM, fmt))) return rc;
+  if ((rc = tc_make_map(ctx, &mbh, bhi, kp, 2L * g.N, 2 * BNC, fmt))) return rc;
+  if ((rc = tc_make_map(ctx, &mbl, blo, kp, 2L * g.N, 2 * BNC, fmt))) return rc;
+  KParams P;
+  P.M = g.M;
+  P.N = g.N;
+  P.k_steps = kp / BK;
+  P.C = g.C;
+  P.ldc = g.ldc;
+  P.alpha = g.alpha;
+  P.accumulate = g.accumulate ? 1 : 0;
+  P.maxbits = words;
+  P.status = g.status;
+  const dim3 grid((g.N + BNC - 1) / BNC, (g.M + BM - 1) / BM);
+  auto go = [&](auto kernel) -> gw_status {
+    gw_status r = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
+                             "cudaFuncSetAttribute");
+    if (r) return r;
+    kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mah, mal, mbh, mbl, P);
+    return launch_check(ctx, "cgemm_tc_kernel");
+  };
+  if (fmt == 0) rc = g.tri == 0 ? go(cgemm_tc_kernel<0, 0>) : g.tri == 1 ? go(cgemm_tc_kernel<0, 1>) : go(cgemm_tc_kernel<0, 2>);
+  else rc = g.tri == 0 ? go(cgemm_tc_kernel<1, 0>) : g.tri == 1 ? go(cgemm_tc_kernel<1, 1>) : go(cgemm_tc_kernel<1, 2>);
+  return rc;
+}
+
+}  // namespace gw
