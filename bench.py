@@ -280,21 +280,41 @@ def main():
     torch.cuda.synchronize()
     stage_ms = {name: ev[i].elapsed_time(ev[i + 1]) for i, name in
                 enumerate(["chi0_omega", "screen_W", "inverse_ct", "sigma_diag"])}
-    stage_flops = {"chi0_omega": fl["green"] / 2 + fl["fft"] / 2 + fl["ct"] / 2 + fl["hadamard"] / 3,
-                   "screen_W": fl["dyson"], "inverse_ct": fl["ct"] / 2,
-                   "sigma_diag": fl["green"] / 2 + fl["fft"] / 2 + fl["sigma"] + 2 * fl["hadamard"] / 3}
-    dom = max(stage_ms, key=stage_ms.get) if not args.no_breakdown else "screen_W"
+    # per-kernel device time and algorithmic work (library events on the launch stream)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if args.prec in ("f16x3", "bf16x3") and dom in ("chi0_omega", "sigma_diag"):
-        roof = {"bound": "tensor", "peak": peaks.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (3 split products issued per flop)"}
-    else:
-        pk = sm_peak_fp32(sm_max) if args.prec != "fp64" else sm_peak_fp32(sm_max) / 64
-        roof = {"bound": "alu", "peak": pk, "unit": "TFLOP/s",
-                "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x %.0f MHz" % sm_max}
-    achieved = stage_flops[dom] / max(stage_ms[dom] / 1e3, 1e-12) / 1e12
-    roof.update({"kernel_stage": dom, "achieved": achieved, "frac": achieved / roof["peak"], "traffic": None})
+    tc_peak = peaks.get("bf16_tflops_sustained", 1716.4)      # fp16 dense = bf16 dense rate
+    hbm_peak = peaks.get("hbm_gbs", 6785.5)
+    kernels = {}
+    if not args.no_breakdown:
+        flush.zero_()
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        step(psi)
+        torch.cuda.synchronize()
+        for fam, (n_l, ms, work, is_bytes) in ctx.kernel_stats().items():
+            if n_l:
+                kernels[fam] = {"launches": n_l, "ms": ms, "work": work, "unit": "B" if is_bytes else "flop"}
+        ctx.set_timing(False)
+    roof = None
+    if kernels:
+        dom = max(kernels, key=lambda k: kernels[k]["ms"])
+        k = kernels[dom]
+        if k["unit"] == "B":
+            ach = k["work"] / (k["ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
+                    "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        elif dom in ("green_tc", "cgemm_tc"):
+            ach = k["work"] / (k["ms"] / 1e3) / 1e12
+            roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": tc_peak / 3.0,
+                    "peak_source": "measured sustained bf16 dense peak %.1f TFLOP/s (fp16 rate equal) / 3 split "
+                                   "products per algorithmic flop" % tc_peak}
+        else:
+            ach = k["work"] / (k["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "unit": "TFLOP/s", "peak": sm_peak_fp32(sm_max),
+                    "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x %.0f MHz" % sm_max}
+        roof.update({"kernel": dom, "launches": k["launches"], "achieved": ach, "frac": ach / roof["peak"],
+                     "traffic": None, "share_of_step": k["ms"] / (1e3 * t_dev / args.steps)})
 
     # end to end through the public API: orbitals copied from pinned host memory every step,
     # Sigma read back to the host inside the call
@@ -321,7 +341,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
             "data": "synthetic", "config": dict(workload, parallelism="replicas x%d" % world),
-            "stage_ms": stage_ms, "flops_per_step": fl, "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
+            "stage_ms": stage_ms, "kernels": kernels, "flops_per_step": fl, "roofline": roof, "e2e": e2e,
+            "gpu_launches": int(launches),
             "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         f, t = oracle_sample(p)

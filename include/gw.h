@@ -80,6 +80,17 @@ const char* gw_last_error(const gw_ctx* ctx);
 unsigned long long gw_ctx_launches(const gw_ctx* ctx);
 /* Current size of the context's device scratch arena in bytes. */
 size_t gw_ctx_scratch_bytes(const gw_ctx* ctx);
+/* Per-kernel timing for benchmarks.  While enabled, the library brackets every
+ * launch of its main kernels with CUDA events on the launch stream and records,
+ * per kernel family, the number of launches, their summed device time and their
+ * summed algorithmic work (flops of the method for the contractions, bytes of
+ * the minimal HBM traffic for the transforms).  Enabling or disabling clears
+ * the totals.  Families: "green_tc", "cgemm_tc", "cgemm_simt", "row_fft",
+ * "col_fft", "col_line_ct", "sigma_row".  gw_ctx_kernel_stats synchronises on
+ * the recorded events; any output pointer may be NULL. */
+gw_status gw_ctx_set_timing(gw_ctx* ctx, int enabled);
+gw_status gw_ctx_kernel_stats(gw_ctx* ctx, const char* family, unsigned long long* launches,
+                              double* ms, double* work, int* work_is_bytes);
 /* ABI version (major*100 + minor). */
 int gw_version(void);
 

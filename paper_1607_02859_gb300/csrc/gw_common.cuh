@@ -9,6 +9,16 @@
 
 #include "../../include/gw.h"
 
+// Kernel families whose launches can be timed individually (gw_ctx_set_timing).
+enum gw_kfam { KF_GREEN_TC = 0, KF_CGEMM_TC, KF_CGEMM_SIMT, KF_ROW_FFT, KF_COL_FFT, KF_COL_LINE_CT, KF_SIGMA_ROW,
+               KF_COUNT };
+
+struct gw_krec {
+  int fam;
+  cudaEvent_t a, b;
+  double work;
+};
+
 struct gw_ctx {
   int device = 0;
   std::string err;
@@ -17,6 +27,13 @@ struct gw_ctx {
   unsigned long long launches = 0;
   int* dflag = nullptr;        // device status word written by kernels
   int num_sms = 0;
+  // opt-in per-launch timing of the main kernels
+  bool timing = false;
+  std::vector<gw_krec> pending;
+  std::vector<cudaEvent_t> pool;
+  double tot_ms[KF_COUNT] = {0};
+  double tot_work[KF_COUNT] = {0};
+  unsigned long long tot_n[KF_COUNT] = {0};
 };
 
 namespace gw {
@@ -43,6 +60,31 @@ struct Carver {
 };
 
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// Brackets one kernel launch with CUDA events on its stream when the context's
+// timing is on; `work` is the launch's algorithmic flops (GEMMs) or bytes.
+struct KTimer {
+  gw_ctx* ctx;
+  int fam;
+  double work;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  KTimer(gw_ctx* c, int f, double w, cudaStream_t s);
+  ~KTimer();
+};
+
+// Algorithmic flops of a complex GEMM (8 per complex multiply-add), counting
+// only the computed lower triangle for tri = 1 and, for tri = 2 (X^H X with X
+// lower, K = N), only the nonzero terms.
+inline double gemm_flops(int M, int N, int K, int tri) {
+  if (tri == 0) return 8.0 * M * (double)N * K;
+  double s = 0;
+  for (int m = 0; m < M; ++m) {
+    const double cols = m + 1 < N ? m + 1 : N;
+    s += tri == 1 ? cols * K : cols * (double)(K - m > 0 ? K - m : 0);
+  }
+  return 8.0 * s;
+}
 inline bool is_fp64(gw_prec p) { return p == GW_FP64; }
 inline size_t csize(gw_prec p) { return is_fp64(p) ? 16 : 8; }
 inline bool valid_prec(int p) { return p >= GW_FP64 && p <= GW_BF16X3; }

@@ -11,42 +11,50 @@
 //   L_jj - 1 = B'_jj / (1 + sqrt(1 + B'_jj))  (B' = B after the updates),
 //   L^{-1} = 1 + P,
 //   eps~^{-1} - 1 = P + P^H + P^H P.
-// Steps (64-column panels):
-//   1. right-looking Cholesky; the trailing Hermitian update is a GEMM
-//   2. P = L^{-1} - 1 by forward substitution on the identity, block row by
-//      block row; the update of the rows below is a GEMM that skips the zero
-//      upper part
-//   3. P^H P (lower triangle, one GEMM), plus P + P^H
-// i.e. N^3/2 complex multiply-adds in all, instead of the N^3 + N^3/6 of a
-// solve against chi~ with N right-hand sides.
+// N^3/2 complex multiply-adds in all (Cholesky, L^{-1}, P^H P: N^3/6 each),
+// instead of the N^3 + N^3/6 of a solve against chi~ with N right-hand sides.
+//
+// The frequencies are independent, so every launch works on a batch of them
+// (grid z): the chain of small sequential launches on the diagonal blocks is
+// paid once per batch instead of once per frequency, and the GEMMs grow.
+//  * CUDA-core precisions: 64-column panels; the trailing updates are CUDA-core
+//    complex GEMMs.
+//  * tensor-core precisions: 256-column panels whose 256 x 256 diagonal blocks
+//    are factored and inverted on CUDA cores; everything with a 256-wide inner
+//    dimension is a tcgen05 GEMM with split 16-bit products:
+//      L21 = A21 (1 + P11)^H,  A22 -= L21 L21^H,
+//      P_i[:, <k0] += P_ii P_i[:, <k0],  rows below -= L_li (1 + P_i),
+//      X = P^H P (one frequency per launch: the largest GEMM of the step).
 #include <cmath>
+#include <type_traits>
 
 #include "gw_kernels.h"
 #include "gw_tc.h"
 
 namespace gw {
 
-constexpr int kNB = 64;
+constexpr int kNB = 64;     // CUDA-core panel width
+constexpr int kTB = 256;    // tensor-core panel width
 
 template <typename T>
-__global__ void build_eps_kernel(const typename cpx<T>::t* __restrict__ chi, const double* __restrict__ vh,
-                                 typename cpx<T>::t* __restrict__ E, int n) {
-  using C = typename cpx<T>::t;
+__global__ void build_eps_kernel(const typename cpx<T>::t* __restrict__ chi, long s_chi,
+                                 const double* __restrict__ vh, typename cpx<T>::t* __restrict__ E, long s_e, int n) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (b > a || b >= n) return;
   const T vv = T(vh[a] * vh[b]);
-  C x = chi[(long)a * n + b];
-  E[(long)a * n + b] = mk(-vv * x.x, -vv * x.y);
+  const auto x = chi[blockIdx.z * s_chi + (long)a * n + b];
+  E[blockIdx.z * s_e + (long)a * n + b] = mk(-vv * x.x, -vv * x.y);
 }
 
-// Unblocked Cholesky of the kb x kb diagonal block (lower), in shared memory.
+// Unblocked Cholesky (K form) of the kb x kb diagonal block, in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) potrf_diag_kernel(typename cpx<T>::t* A, long lda, int kb, int* flag,
+__global__ void __launch_bounds__(256) potrf_diag_kernel(typename cpx<T>::t* A, long lda, long s_a, int kb, int* flag,
                                                          int col0) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C (*S)[kNB + 1] = reinterpret_cast<C (*)[kNB + 1]>(smem_raw);    // [kNB][kNB+1]
+  A += blockIdx.z * s_a;
   for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, c = e % kb;
     S[i][c] = c <= i ? A[(long)i * lda + c] : mk(T(0), T(0));
@@ -56,7 +64,10 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(typename cpx<T>::t* A, 
     if (threadIdx.x == 0) {
       T b = S[j][j].x;                       // eps~_jj - 1 after the updates
       if (!(T(1) + b > T(0))) {
-        if (atomicCAS(flag, 0, 1) == 0) flag[1] = col0 + j;
+        if (atomicCAS(flag, 0, 1) == 0) {
+          flag[1] = col0 + j;
+          flag[2] = blockIdx.z;
+        }
         b = T(0);
       }
       S[j][j] = mk(b / (T(1) + sqrt(T(1) + b)), T(0));   // L_jj - 1
@@ -80,11 +91,13 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(typename cpx<T>::t* A, 
 
 // Rows below the diagonal block: x L11^H = a  ->  x (row of L21).  64 rows per CTA.
 template <typename T>
-__global__ void __launch_bounds__(64) trsm_panel_kernel(typename cpx<T>::t* A, long lda, int k0, int kb, int rows) {
+__global__ void __launch_bounds__(64) trsm_panel_kernel(typename cpx<T>::t* A, long lda, long s_a, int k0, int kb,
+                                                        int rows) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);          // [kb][kb+1]
   C* X = L + kNB * (kNB + 1);                       // [kb][64]  (column c of thread t at X[c*64+t])
+  A += blockIdx.z * s_a;
   const int t = threadIdx.x;
   for (int e = t; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, c = e % kb;
@@ -104,27 +117,35 @@ __global__ void __launch_bounds__(64) trsm_panel_kernel(typename cpx<T>::t* A, l
   for (int c = 0; c < kb; ++c) A[row * lda + k0 + c] = X[c * 64 + t];
 }
 
-// P[rows below][k0 .. k0+kb) = -L[rows below][k0 .. k0+kb): the identity part of
-// (1 + P) contributes L_li * 1 to the update of the rows below block row i.
+// P[rows below][col0 .. col0+kb) = -L[rows below][col0 .. col0+kb): the identity
+// part of (1 + P) contributes L_li * 1 to the update of the rows below block row i.
 template <typename T>
-__global__ void neg_copy_kernel(const typename cpx<T>::t* __restrict__ Lm, typename cpx<T>::t* __restrict__ P, long ldl,
-                                long ldp, int row0, int rows, int col0, int kb) {
+__global__ void neg_copy_kernel(const typename cpx<T>::t* __restrict__ Lm, long ldl, long s_l,
+                                typename cpx<T>::t* __restrict__ P, long ldp, long s_p, int row0, int rows, int col0,
+                                int kb) {
   const long r = row0 + (long)blockIdx.x;
-  if (blockIdx.x >= rows) return;
+  if ((int)blockIdx.x >= rows) return;
+  Lm += blockIdx.z * s_l;
+  P += blockIdx.z * s_p;
   for (int c = threadIdx.x; c < kb; c += blockDim.x) {
     const auto v = Lm[r * ldl + col0 + c];
     P[r * ldp + col0 + c] = mk(-v.x, -v.y);
   }
 }
 
-// Y = L_ii^{-1} Y for the block rows k0..k0+kb-1 and columns 0..ncols-1 of Y.
+// Y = L_ii^{-1} Y for the block rows k0..k0+kb-1 and columns 0..ncols-1 of Y,
+// with the identity as right-hand side in the diagonal-block columns (their
+// stored values are ignored) and P = L^{-1} - 1 stored on the diagonal.
 template <typename T>
-__global__ void __launch_bounds__(64) trsm_left_kernel(const typename cpx<T>::t* Lm, long ldl,
-                                                      typename cpx<T>::t* Y, long ldy, int k0, int kb, int ncols) {
+__global__ void __launch_bounds__(64) trsm_left_kernel(const typename cpx<T>::t* Lm, long ldl, long s_l,
+                                                      typename cpx<T>::t* Y, long ldy, long s_y, int k0, int kb,
+                                                      int ncols) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);
   C* X = L + kNB * (kNB + 1);
+  Lm += blockIdx.z * s_l;
+  Y += blockIdx.z * s_y;
   const int t = threadIdx.x;
   for (int e = t; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, c = e % kb;
@@ -153,31 +174,40 @@ __global__ void __launch_bounds__(64) trsm_left_kernel(const typename cpx<T>::t*
   }
 }
 
+// Zero `cols` columns of `rows` rows (leading dimension ld) per batch entry.
+template <typename T>
+__global__ void zero_block_kernel(typename cpx<T>::t* __restrict__ P, long ld, long s_p, int cols) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cols) return;
+  P[blockIdx.z * s_p + (long)blockIdx.y * ld + b] = mk(T(0), T(0));
+}
+
 // X = P^H P + P + P^H (lower triangle, in place over P^H P).
 template <typename T>
-__global__ void assemble_kernel(typename cpx<T>::t* __restrict__ X, const typename cpx<T>::t* __restrict__ P, int n) {
+__global__ void assemble_kernel(typename cpx<T>::t* __restrict__ X, long s_x, const typename cpx<T>::t* __restrict__ P,
+                                long s_p, int n) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (b > a || b >= n) return;
   const long e = (long)a * n + b;
-  auto x = X[e];
-  const auto p = P[e];
+  auto x = X[blockIdx.z * s_x + e];
+  const auto p = P[blockIdx.z * s_p + e];
   x.x += a == b ? T(2) * p.x : p.x;
   x.y += a == b ? T(0) : p.y;
-  X[e] = x;
+  X[blockIdx.z * s_x + e] = x;
 }
 
 // W~[a][b] = v_a X[a][b] v_b, both triangles from the lower one.
 template <typename T>
-__global__ void finalize_kernel(const typename cpx<T>::t* __restrict__ Xl, const double* __restrict__ vh,
-                                typename cpx<T>::t* __restrict__ W, int n) {
-  using C = typename cpx<T>::t;
+__global__ void finalize_kernel(const typename cpx<T>::t* __restrict__ Xl, long s_x, const double* __restrict__ vh,
+                                typename cpx<T>::t* __restrict__ W, long s_w, int n) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (b > a || b >= n) return;
-  C x = Xl[(long)a * n + b];
+  auto x = Xl[blockIdx.z * s_x + (long)a * n + b];
   const T vv = T(vh[a] * vh[b]);
   x = cscale(x, vv);
+  W += blockIdx.z * s_w;
   W[(long)a * n + b] = x;
   if (a != b) W[(long)b * n + a] = cconj(x);
 }
@@ -221,28 +251,48 @@ __global__ void __launch_bounds__(256) hemv_probe_kernel(const typename cpx<T>::
   if (threadIdx.x == 0) y[a] = make_double2(sr[0], si[0]);
 }
 
-// Cholesky (lower, K form on the diagonal) of the n x n block at a (leading
-// dimension lda) on CUDA cores, 64-column panels.  col0 labels pivots.
+// A batch of B frequencies whose matrices are `ms` elements apart.
+struct Batch {
+  int B;
+  long ms;
+};
+
 template <typename T>
-static gw_status chol_simt(gw_ctx* ctx, gw_prec prec, typename cpx<T>::t* a, long lda, int n, int col0,
+static gw_status set_attrs(gw_ctx* ctx) {
+  using C = typename cpx<T>::t;
+  const size_t tsm = sizeof(C) * (kNB * (kNB + 1) + kNB * 64);
+  const size_t psm = sizeof(C) * kNB * (kNB + 1);
+  gw_status rc = GW_OK;
+  if (tsm > 48 * 1024) {
+    rc = cuda_check(ctx, cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm),
+                    "cudaFuncSetAttribute");
+    if (!rc)
+      rc = cuda_check(ctx, cudaFuncSetAttribute(trsm_left_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm),
+                      "cudaFuncSetAttribute");
+  }
+  if (!rc && psm > 48 * 1024)
+    rc = cuda_check(ctx, cudaFuncSetAttribute(potrf_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm),
+                    "cudaFuncSetAttribute");
+  return rc;
+}
+
+// Cholesky (lower, K form on the diagonal) of the n x n block at a (leading
+// dimension lda) of every batch entry, on CUDA cores, 64-column panels.
+template <typename T>
+static gw_status chol_simt(gw_ctx* ctx, gw_prec prec, typename cpx<T>::t* a, long lda, int n, int col0, Batch bt,
                            cudaStream_t st) {
   using C = typename cpx<T>::t;
   gw_status rc;
   const size_t tsm = sizeof(C) * (kNB * (kNB + 1) + kNB * 64);
   const size_t psm = sizeof(C) * kNB * (kNB + 1);
-  if (tsm > 48 * 1024) {
-    cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
-    cudaFuncSetAttribute(trsm_left_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
-  }
-  if (psm > 48 * 1024)
-    cudaFuncSetAttribute(potrf_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
   for (int k0 = 0; k0 < n; k0 += kNB) {
     const int kb = std::min(kNB, n - k0);
-    potrf_diag_kernel<T><<<1, 256, psm, st>>>(a + (long)k0 * lda + k0, lda, kb, ctx->dflag, col0 + k0);
+    potrf_diag_kernel<T><<<dim3(1, 1, bt.B), 256, psm, st>>>(a + (long)k0 * lda + k0, lda, bt.ms, kb, ctx->dflag,
+                                                             col0 + k0);
     if ((rc = launch_check(ctx, "potrf_diag_kernel"))) return rc;
     const int rows = n - k0 - kb;
     if (rows <= 0) break;
-    trsm_panel_kernel<T><<<(rows + 63) / 64, 64, tsm, st>>>(a, lda, k0, kb, rows);
+    trsm_panel_kernel<T><<<dim3((rows + 63) / 64, 1, bt.B), 64, tsm, st>>>(a, lda, bt.ms, k0, kb, rows);
     if ((rc = launch_check(ctx, "trsm_panel_kernel"))) return rc;
     GemmArgs g{};
     g.M = rows;
@@ -260,28 +310,32 @@ static gw_status chol_simt(gw_ctx* ctx, gw_prec prec, typename cpx<T>::t* a, lon
     g.C = a + (long)(k0 + kb) * lda + k0 + kb;
     g.ldc = lda;
     g.tri = 1;
+    g.batch = bt.B;
+    g.sA = g.sB = g.sC = bt.ms;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
   }
   return GW_OK;
 }
 
 // P = L^{-1} - 1 for the n x n lower factor L (K form diagonal) at Lm, written
-// to the n x n block at p (both with their leading dimensions), CUDA cores.
+// to the n x n block at p, for every batch entry (CUDA cores).
 template <typename T>
-static gw_status inv_simt(gw_ctx* ctx, gw_prec prec, const typename cpx<T>::t* Lm, long ldl, typename cpx<T>::t* p,
-                          long ldp, int n, cudaStream_t st) {
+static gw_status inv_simt(gw_ctx* ctx, gw_prec prec, const typename cpx<T>::t* Lm, long ldl,
+                          typename cpx<T>::t* p, long ldp, int n, Batch bt, cudaStream_t st) {
   using C = typename cpx<T>::t;
   gw_status rc;
   const size_t tsm = sizeof(C) * (kNB * (kNB + 1) + kNB * 64);
-  if ((rc = cuda_check(ctx, cudaMemset2DAsync(p, ldp * sizeof(C), 0, n * sizeof(C), n, st), "memset P"))) return rc;
+  zero_block_kernel<T><<<dim3((n + 127) / 128, n, bt.B), 128, 0, st>>>(p, ldp, bt.ms, n);
+  if ((rc = launch_check(ctx, "zero_block_kernel"))) return rc;
   for (int k0 = 0; k0 < n; k0 += kNB) {
     const int kb = std::min(kNB, n - k0);
     const int ncols = k0 + kb;
-    trsm_left_kernel<T><<<(ncols + 63) / 64, 64, tsm, st>>>(Lm, ldl, p, ldp, k0, kb, ncols);
+    trsm_left_kernel<T><<<dim3((ncols + 63) / 64, 1, bt.B), 64, tsm, st>>>(Lm, ldl, bt.ms, p, ldp, bt.ms, k0, kb,
+                                                                          ncols);
     if ((rc = launch_check(ctx, "trsm_left_kernel"))) return rc;
     const int rows = n - k0 - kb;
     if (rows <= 0) break;
-    neg_copy_kernel<T><<<rows, kNB, 0, st>>>(Lm, p, ldl, ldp, k0 + kb, rows, k0, kb);
+    neg_copy_kernel<T><<<dim3(rows, 1, bt.B), kNB, 0, st>>>(Lm, ldl, bt.ms, p, ldp, bt.ms, k0 + kb, rows, k0, kb);
     if ((rc = launch_check(ctx, "neg_copy_kernel"))) return rc;
     GemmArgs g{};
     g.M = rows;
@@ -295,174 +349,162 @@ static gw_status inv_simt(gw_ctx* ctx, gw_prec prec, const typename cpx<T>::t* L
     g.ldb = ldp;
     g.C = p + (long)(k0 + kb) * ldp;
     g.ldc = ldp;
+    g.batch = bt.B;
+    g.sA = g.sB = g.sC = bt.ms;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
   }
   return GW_OK;
 }
 
 // |eps~ X z - chi~ z| / |chi~ z| over 4 seeded probes z, in FP64, with X the
-// assembled lower triangle of eps~^{-1} - 1 and chi still intact.
+// assembled lower triangle of eps~^{-1} - 1 (one frequency) and chi intact.
 template <typename T>
-static gw_status residual_probe(gw_ctx* ctx, int n, const void* chi, const double* dvh,
+static gw_status residual_probe(gw_ctx* ctx, int n, const typename cpx<T>::t* chi, const double* dvh,
                                 const typename cpx<T>::t* e, double2* probe, double* resid_h, cudaStream_t st) {
-  using C = typename cpx<T>::t;
   gw_status rc;
-  {
-    // |eps~ X z - chi~ z| / |chi~ z| over 4 probes, X = eps~^{-1} - 1 (before chi may be overwritten)
-    double num = 0, den = 0;
-    std::vector<double2> hz(n), hu(n), hw(n), hc(n);
-    for (int q = 0; q < 4; ++q) {
-      uint64_t sd = 0x9E3779B97F4A7C15ull * (q + 1);
-      for (int i = 0; i < n; ++i) {
-        sd = sd * 6364136223846793005ull + 1442695040888963407ull;
-        double u1 = ((sd >> 11) & ((1ull << 53) - 1)) / 9007199254740992.0;
-        sd = sd * 6364136223846793005ull + 1442695040888963407ull;
-        double u2 = ((sd >> 11) & ((1ull << 53) - 1)) / 9007199254740992.0;
-        hz[i] = make_double2(u1 - 0.5, u2 - 0.5);
-      }
-      double2 *z = probe, *u = probe + n, *w = probe + 2 * n, *c = probe + 3 * n;
-      if ((rc = upload(ctx, z, hz.data(), sizeof(double2) * n, st))) return rc;
-      hemv_probe_kernel<T><<<n, 256, 0, st>>>(e, nullptr, 0.0, z, u, n);                       // u = X z
-      hemv_probe_kernel<T><<<n, 256, 0, st>>>(static_cast<const C*>(chi), dvh, 0.0, u, w, n);  // w = chi~ u
-      hemv_probe_kernel<T><<<n, 256, 0, st>>>(static_cast<const C*>(chi), dvh, 0.0, z, c, n);  // c = chi~ z
-      if ((rc = launch_check(ctx, "hemv_probe_kernel"))) return rc;
-      ctx->launches += 2;
-      if ((rc = cuda_check(ctx, cudaMemcpyAsync(hu.data(), u, sizeof(double2) * n, cudaMemcpyDeviceToHost, st), "probe")))
-        return rc;
-      cudaMemcpyAsync(hw.data(), w, sizeof(double2) * n, cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(hc.data(), c, sizeof(double2) * n, cudaMemcpyDeviceToHost, st);
-      if ((rc = cuda_check(ctx, cudaStreamSynchronize(st), "probe sync"))) return rc;
-      for (int i = 0; i < n; ++i) {
-        const double rr = hu[i].x - hw[i].x - hc[i].x, ri = hu[i].y - hw[i].y - hc[i].y;
-        num += rr * rr + ri * ri;
-        den += hc[i].x * hc[i].x + hc[i].y * hc[i].y;
-      }
+  double num = 0, den = 0;
+  std::vector<double2> hz(n), hu(n), hw(n), hc(n);
+  for (int q = 0; q < 4; ++q) {
+    uint64_t sd = 0x9E3779B97F4A7C15ull * (q + 1);
+    for (int i = 0; i < n; ++i) {
+      sd = sd * 6364136223846793005ull + 1442695040888963407ull;
+      const double u1 = ((sd >> 11) & ((1ull << 53) - 1)) / 9007199254740992.0;
+      sd = sd * 6364136223846793005ull + 1442695040888963407ull;
+      const double u2 = ((sd >> 11) & ((1ull << 53) - 1)) / 9007199254740992.0;
+      hz[i] = make_double2(u1 - 0.5, u2 - 0.5);
     }
-    *resid_h = den > 0 ? std::sqrt(num / den) : 0.0;
+    double2 *z = probe, *u = probe + n, *w = probe + 2 * n, *c = probe + 3 * n;
+    if ((rc = upload(ctx, z, hz.data(), sizeof(double2) * n, st))) return rc;
+    hemv_probe_kernel<T><<<n, 256, 0, st>>>(e, nullptr, 0.0, z, u, n);       // u = X z
+    hemv_probe_kernel<T><<<n, 256, 0, st>>>(chi, dvh, 0.0, u, w, n);         // w = chi~ u
+    hemv_probe_kernel<T><<<n, 256, 0, st>>>(chi, dvh, 0.0, z, c, n);         // c = chi~ z
+    if ((rc = launch_check(ctx, "hemv_probe_kernel"))) return rc;
+    ctx->launches += 2;
+    cudaMemcpyAsync(hu.data(), u, sizeof(double2) * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hw.data(), w, sizeof(double2) * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hc.data(), c, sizeof(double2) * n, cudaMemcpyDeviceToHost, st);
+    if ((rc = cuda_check(ctx, cudaStreamSynchronize(st), "probe sync"))) return rc;
+    for (int i = 0; i < n; ++i) {
+      const double rr = hu[i].x - hw[i].x - hc[i].x, ri = hu[i].y - hw[i].y - hc[i].y;
+      num += rr * rr + ri * ri;
+      den += hc[i].x * hc[i].x + hc[i].y * hc[i].y;
+    }
   }
+  *resid_h = den > 0 ? std::sqrt(num / den) : 0.0;
   return GW_OK;
 }
 
+// One batch of frequencies: chi[B][n][n] -> W[B][n][n] (may alias chi), with
+// work buffers E and P of the same shape.  tcs: tensor-core scratch (NULL for
+// the CUDA-core precisions).
 template <typename T>
-static gw_status screen_one(gw_ctx* ctx, gw_prec prec, int n, const void* chi, const double* dvh, void* E, void* Mi,
-                            void* W, double2* probe, double* resid_h, cudaStream_t st) {
+static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const void* chi, const double* dvh, void* E,
+                              void* Pm, void* W, double2* probe, double* resid_h, void* tcs, cudaStream_t st) {
   using C = typename cpx<T>::t;
   gw_status rc;
   C* e = static_cast<C*>(E);
-  C* m = static_cast<C*>(Mi);
-  const dim3 tb(128), gb((n + 127) / 128, n);
-  build_eps_kernel<T><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), dvh, e, n);
+  C* p = static_cast<C*>(Pm);
+  const long nn = (long)n * n;
+  const Batch bt{B, nn};
+  if ((rc = set_attrs<T>(ctx))) return rc;
+  const dim3 tb(128), gb((n + 127) / 128, n, B);
+  build_eps_kernel<T><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), nn, dvh, e, nn, n);
   if ((rc = launch_check(ctx, "build_eps_kernel"))) return rc;
-  // 1. eps~ = L L^H
-  if ((rc = chol_simt<T>(ctx, prec, e, n, n, 0, st))) return rc;
-  // 2. P = L^{-1} - 1
-  if ((rc = inv_simt<T>(ctx, prec, e, n, m, n, n, st))) return rc;
-  // 3. eps~^{-1} - 1 = P^H P + P + P^H (lower) into E
-  {
+  if (!tcs) {
+    // CUDA cores, 64-column panels over the whole matrix
+    if ((rc = chol_simt<T>(ctx, prec, e, n, n, 0, bt, st))) return rc;
+    if ((rc = inv_simt<T>(ctx, prec, e, n, p, n, n, bt, st))) return rc;
     GemmArgs g{};
     g.M = n;
     g.N = n;
     g.K = n;
     g.alpha_re = 1;
     g.beta = 0;
-    g.A = m;
+    g.A = p;
     g.lda = n;
     g.a_km = 1;
     g.a_conj = true;
-    g.B = m;
+    g.B = p;
     g.ldb = n;
     g.C = e;
     g.ldc = n;
     g.tri = 2;
+    g.batch = B;
+    g.sA = g.sB = g.sC = nn;
     if ((rc = launch_gemm(ctx, prec, g, st))) return rc;
+  } else {
+    if constexpr (std::is_same<T, float>::value) {
+      int* tstat = ctx->dflag + 4;
+      auto gemm = [&](int M, int N, int K, const C* A, bool at, bool ac, const C* Bm, bool btr, bool bc, C* Cm,
+                      float alpha, bool acc, int tri, int batch) {
+        TcGemm g;
+        g.M = M;
+        g.N = N;
+        g.K = K;
+        g.A = A;
+        g.lda = n;
+        g.a_trans = at;
+        g.a_conj = ac;
+        g.B = Bm;
+        g.ldb = n;
+        g.b_trans = btr;
+        g.b_conj = bc;
+        g.C = Cm;
+        g.ldc = n;
+        g.alpha = alpha;
+        g.accumulate = acc;
+        g.tri = tri;
+        g.status = tstat;
+        g.batch = batch;
+        g.sA = g.sB = g.sC = nn;
+        return tc_gemm(ctx, prec, g, tcs, st);
+      };
+      // 1. Cholesky and the inverted diagonal blocks P_kk
+      for (int k0 = 0; k0 < n; k0 += kTB) {
+        const int kb = std::min(kTB, n - k0);
+        C* akk = e + (long)k0 * n + k0;
+        C* pkk = p + (long)k0 * n + k0;
+        if ((rc = chol_simt<float>(ctx, GW_FP32, akk, n, kb, k0, bt, st))) return rc;
+        if ((rc = inv_simt<float>(ctx, GW_FP32, akk, n, pkk, n, kb, bt, st))) return rc;
+        const int rows = n - k0 - kb;
+        if (rows <= 0) break;
+        C* a21 = e + (long)(k0 + kb) * n + k0;
+        // L21 = A21 + A21 P_kk^H   (opB(k, j) = conj(P_kk[j][k]))
+        if ((rc = gemm(rows, kb, kb, a21, false, false, pkk, true, true, a21, 1.0f, true, 0, B))) return rc;
+        // A22 -= L21 L21^H
+        if ((rc = gemm(rows, rows, kb, a21, false, false, a21, true, true, a21 + kb, -1.0f, true, 1, B))) return rc;
+      }
+      // 2. off-diagonal blocks of P = L^{-1} - 1, block row by block row, and
+      //    the zero upper part
+      for (int k0 = 0; k0 < n; k0 += kTB) {
+        const int kb = std::min(kTB, n - k0);
+        C* pi = p + (long)k0 * n;
+        C* pkk = pi + k0;
+        if (k0 > 0 && (rc = gemm(kb, k0, kb, pkk, false, false, pi, false, false, pi, 1.0f, true, 0, B))) return rc;
+        const int rows = n - k0 - kb;
+        if (rows <= 0) break;
+        zero_block_kernel<float><<<dim3((rows + 127) / 128, kb, B), 128, 0, st>>>(pi + k0 + kb, n, nn, rows);
+        if ((rc = launch_check(ctx, "zero_block_kernel"))) return rc;
+        neg_copy_kernel<float><<<dim3(rows, 1, B), 256, 0, st>>>(e, n, nn, p, n, nn, k0 + kb, rows, k0, kb);
+        if ((rc = launch_check(ctx, "neg_copy_kernel"))) return rc;
+        if ((rc = gemm(rows, k0 + kb, kb, e + (long)(k0 + kb) * n + k0, false, false, pi, false, false,
+                       p + (long)(k0 + kb) * n, -1.0f, true, 0, B)))
+          return rc;
+      }
+      // 3. P^H P (lower), one frequency per launch
+      for (int b = 0; b < B; ++b)
+        if ((rc = gemm(n, n, n, p + b * nn, true, true, p + b * nn, false, false, e + b * nn, 1.0f, false, 2, 1)))
+          return rc;
+    }
   }
-  assemble_kernel<T><<<gb, tb, 0, st>>>(e, m, n);
+  assemble_kernel<T><<<gb, tb, 0, st>>>(e, nn, p, nn, n);
   if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
-  if (resid_h && (rc = residual_probe<T>(ctx, n, chi, dvh, e, probe, resid_h, st))) return rc;
-  finalize_kernel<T><<<gb, tb, 0, st>>>(e, dvh, static_cast<C*>(W), n);
-  return launch_check(ctx, "finalize_kernel");
-}
-
-// Tensor-core precisions: the same factorisation with 256-column panels.  The
-// 256 x 256 diagonal blocks are factored and inverted on CUDA cores (the
-// functions above); everything with a 256-wide inner dimension is a tcgen05
-// GEMM with split 16-bit products:
-//   L21 = A21 (1 + P11)^H       (panel solve through the inverted block)
-//   A22 -= L21 L21^H             (trailing update, lower tiles)
-//   P_i[:, <k0] += P_ii P_i[:, <k0],  rows below -= L_li (1 + P_i)
-//   X = P^H P                    (lower, k loop from the tile's first row)
-constexpr int kTB = 256;
-
-static size_t tc_screen_scratch(int n) { return tc_gemm_scratch(n, n, n); }
-
-static gw_status screen_one_tc(gw_ctx* ctx, gw_prec prec, int n, const void* chi, const double* dvh, void* E, void* Mi,
-                               void* W, double2* probe, double* resid_h, void* tcs, cudaStream_t st) {
-  using C = float2;
-  gw_status rc;
-  C* e = static_cast<C*>(E);
-  C* p = static_cast<C*>(Mi);
-  int* tstat = ctx->dflag + 4;
-  const dim3 tb(128), gb((n + 127) / 128, n);
-  build_eps_kernel<float><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), dvh, e, n);
-  if ((rc = launch_check(ctx, "build_eps_kernel"))) return rc;
-  if ((rc = cuda_check(ctx, cudaMemsetAsync(p, 0, sizeof(C) * (size_t)n * n, st), "memset P"))) return rc;
-  auto gemm = [&](int M, int N, int K, const C* A, bool at, bool ac, const C* B, bool bt, bool bc, C* Cm, float alpha,
-                  bool acc, int tri) {
-    TcGemm g;
-    g.M = M;
-    g.N = N;
-    g.K = K;
-    g.A = A;
-    g.lda = n;
-    g.a_trans = at;
-    g.a_conj = ac;
-    g.B = B;
-    g.ldb = n;
-    g.b_trans = bt;
-    g.b_conj = bc;
-    g.C = Cm;
-    g.ldc = n;
-    g.alpha = alpha;
-    g.accumulate = acc;
-    g.tri = tri;
-    g.status = tstat;
-    return tc_gemm(ctx, prec, g, tcs, st);
-  };
-  // 1. Cholesky, and the inverted diagonal blocks P_kk
-  for (int k0 = 0; k0 < n; k0 += kTB) {
-    const int kb = std::min(kTB, n - k0);
-    C* akk = e + (long)k0 * n + k0;
-    C* pkk = p + (long)k0 * n + k0;
-    if ((rc = chol_simt<float>(ctx, GW_FP32, akk, n, kb, k0, st))) return rc;
-    if ((rc = inv_simt<float>(ctx, GW_FP32, akk, n, pkk, n, kb, st))) return rc;
-    const int rows = n - k0 - kb;
-    if (rows <= 0) break;
-    C* a21 = e + (long)(k0 + kb) * n + k0;
-    // L21 = A21 + A21 P_kk^H   (opB(k, j) = conj(P_kk[j][k]))
-    if ((rc = gemm(rows, kb, kb, a21, false, false, pkk, true, true, a21, 1.0f, true, 0))) return rc;
-    // A22 -= L21 L21^H
-    if ((rc = gemm(rows, rows, kb, a21, false, false, a21, true, true, a21 + kb, -1.0f, true, 1))) return rc;
-  }
-  // 2. off-diagonal blocks of P = L^{-1} - 1, block row by block row
-  for (int k0 = 0; k0 < n; k0 += kTB) {
-    const int kb = std::min(kTB, n - k0);
-    C* pi = p + (long)k0 * n;                    // block row i, columns from 0
-    C* pkk = pi + k0;
-    if (k0 > 0 && (rc = gemm(kb, k0, kb, pkk, false, false, pi, false, false, pi, 1.0f, true, 0))) return rc;
-    const int rows = n - k0 - kb;
-    if (rows <= 0) break;
-    neg_copy_kernel<float><<<rows, 256, 0, st>>>(e, p, n, n, k0 + kb, rows, k0, kb);
-    if ((rc = launch_check(ctx, "neg_copy_kernel"))) return rc;
-    if ((rc = gemm(rows, k0 + kb, kb, e + (long)(k0 + kb) * n + k0, false, false, pi, false, false,
-                   p + (long)(k0 + kb) * n, -1.0f, true, 0)))
-      return rc;
-  }
-  // 3. P^H P (lower) into E, then + P + P^H
-  if ((rc = gemm(n, n, n, p, true, true, p, false, false, e, 1.0f, false, 2))) return rc;
-  assemble_kernel<float><<<gb, tb, 0, st>>>(e, p, n);
-  if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
-  if (resid_h && (rc = residual_probe<float>(ctx, n, chi, dvh, e, probe, resid_h, st))) return rc;
-  finalize_kernel<float><<<gb, tb, 0, st>>>(e, dvh, static_cast<C*>(W), n);
+  if (resid_h)
+    for (int b = 0; b < B; ++b)
+      if ((rc = residual_probe<T>(ctx, n, static_cast<const C*>(chi) + b * nn, dvh, e + b * nn, probe, resid_h + b,
+                                  st)))
+        return rc;
+  finalize_kernel<T><<<gb, tb, 0, st>>>(e, nn, dvh, static_cast<C*>(W), nn, n);
   return launch_check(ctx, "finalize_kernel");
 }
 
@@ -479,42 +521,59 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
   if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
   if (n_chi < 1 || n_chi > g.nr || n_chi > 65535) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_chi <= min(N_r, 65535)");
   if (n_omega < 0) return fail(ctx, GW_ERR_SHAPE, "n_omega < 0");
+  if (n_omega == 0) return GW_OK;
   if (!gvec_h || !chi_w || !w_w) return fail(ctx, GW_ERR_ARG, "NULL pointer");
   cudaStream_t s = as_stream(stream);
   std::vector<double> vh(n_chi);
   if ((st = gw_coulomb_sqrt(grid, gvec_h, n_chi, vh.data()))) return fail(ctx, st, gw_last_error(nullptr));
   const size_t es = csize(prec);
   const size_t nn = (size_t)n_chi * n_chi;
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  // frequencies per batch: the two work matrices of a batch within 64 GB
+  const size_t budget = size_t(64) << 30;
+  const int bmax = (int)std::max<size_t>(1, std::min<size_t>(n_omega, budget / (2 * nn * es)));
+  const int nbatch = (n_omega + bmax - 1) / bmax;
+  const int bsz = (n_omega + nbatch - 1) / nbatch;
   Carver probe(nullptr);
   probe.take<double>(n_chi);
-  probe.take<char>(nn * es);
-  probe.take<char>(nn * es);
+  probe.take<char>(bsz * nn * es);
+  probe.take<char>(bsz * nn * es);
   probe.take<double2>(4 * (size_t)n_chi);
-  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
-  if (tc) probe.take<char>(tc_screen_scratch(n_chi));
+  const size_t tcs_bytes =
+      tc ? std::max(tc_gemm_scratch(n_chi, n_chi, n_chi, 1), tc_gemm_scratch(n_chi, n_chi, kTB, bsz)) : 0;
+  if (tc) probe.take<char>(tcs_bytes);
   if ((st = reserve(ctx, probe.off))) return st;
   Carver cv(ctx->arena);
   double* dvh = cv.take<double>(n_chi);
-  void* E = cv.take<char>(nn * es);
-  void* M = cv.take<char>(nn * es);
+  void* E = cv.take<char>(bsz * nn * es);
+  void* M = cv.take<char>(bsz * nn * es);
   double2* pr = cv.take<double2>(4 * (size_t)n_chi);
-  void* tcs = tc ? cv.take<char>(tc_screen_scratch(n_chi)) : nullptr;
+  void* tcs = tc ? cv.take<char>(tcs_bytes) : nullptr;
   if ((st = upload(ctx, dvh, vh.data(), sizeof(double) * n_chi, s))) return st;
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 8 * sizeof(int), s), "memset flag"))) return st;
-  for (int k = 0; k < n_omega; ++k) {
-    const char* in = static_cast<const char*>(chi_w) + k * nn * es;
-    char* out = static_cast<char*>(w_w) + k * nn * es;
-    double* rk = resid_h ? resid_h + k : nullptr;
-    if (tc) st = screen_one_tc(ctx, prec, n_chi, in, dvh, E, M, out, pr, rk, tcs, s);
-    else if (is_fp64(prec)) st = screen_one<double>(ctx, prec, n_chi, in, dvh, E, M, out, pr, rk, s);
-    else st = screen_one<float>(ctx, prec, n_chi, in, dvh, E, M, out, pr, rk, s);
+  int first_bad = -1;
+  for (int k0 = 0; k0 < n_omega; k0 += bsz) {
+    const int B = std::min(bsz, n_omega - k0);
+    const char* in = static_cast<const char*>(chi_w) + k0 * nn * es;
+    char* out = static_cast<char*>(w_w) + k0 * nn * es;
+    double* rk = resid_h ? resid_h + k0 : nullptr;
+    if (is_fp64(prec)) st = screen_batch<double>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, nullptr, s);
+    else st = screen_batch<float>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, tcs, s);
     if (st) return st;
+    if (nbatch > 1 && first_bad < 0) {
+      int f[3] = {0, 0, 0};
+      cudaMemcpyAsync(f, ctx->dflag, sizeof(f), cudaMemcpyDeviceToHost, s);
+      if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
+      if (f[0]) first_bad = k0 + f[2];
+    }
   }
   int flag[8] = {0};
   if ((st = cuda_check(ctx, cudaMemcpyAsync(flag, ctx->dflag, sizeof(flag), cudaMemcpyDeviceToHost, s), "flag")))
     return st;
   if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
   if (flag[4]) return fail(ctx, GW_ERR_TIMEOUT, "tensor-core GEMM wait timed out (role " + std::to_string(flag[5]) + ")");
-  if (flag[0]) return fail(ctx, GW_ERR_NUMERIC, "eps~ not positive definite at column " + std::to_string(flag[1]));
+  if (flag[0])
+    return fail(ctx, GW_ERR_NUMERIC, "eps~ not positive definite at column " + std::to_string(flag[1]) +
+                                         " of frequency " + std::to_string(first_bad >= 0 ? first_bad : flag[2]));
   return GW_OK;
 }

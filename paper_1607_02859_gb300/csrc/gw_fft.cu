@@ -227,9 +227,12 @@ struct GridOps {
   static gw_status row(gw_ctx* ctx, int mode, const void* a, const void* b, long lda, void* out, long ldo,
                        const int* map, int n_chi, int n_rows, double scale, cudaStream_t st) {
     const size_t bytes = RowLayout<N1, N2, N3>::TOT * sizeof(C);
+    const double rd = mode == 0 ? 2.0 * RowLayout<N1, N2, N3>::NR : (mode == 1 ? RowLayout<N1, N2, N3>::NR : n_chi);
+    const double wr = mode == 2 ? RowLayout<N1, N2, N3>::NR : n_chi;
     auto go = [&](auto kernel) -> gw_status {
       gw_status s = set_smem(ctx, kernel, bytes);
       if (s) return s;
+      KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (rd + wr) * sizeof(C), st);
       kernel<<<n_rows, 256, bytes, st>>>((const C*)a, (const C*)b, lda, (C*)out, ldo, map, n_chi, (T)scale);
       return launch_check(ctx, "row_fft_kernel");
     };
@@ -243,6 +246,7 @@ struct GridOps {
     auto go = [&](auto kernel) -> gw_status {
       gw_status s = set_smem(ctx, kernel, bytes);
       if (s) return s;
+      KTimer kt(ctx, KF_COL_FFT, 2.0 * N1 * N2 * N3 * (double)ncols * sizeof(C), st);
       kernel<<<grid, 256, bytes, st>>>((C*)buf, ld, ncols, (T)scale);
       return launch_check(ctx, "col_plane_kernel");
     };
@@ -252,6 +256,7 @@ struct GridOps {
                         const int* inv, double scale, cudaStream_t st) {
     dim3 grid((ncols + 127) / 128, N2 * N3);
     auto go = [&](auto kernel) -> gw_status {
+      KTimer kt(ctx, KF_COL_FFT, 2.0 * N1 * N2 * N3 * (double)ncols * sizeof(C), st);
       kernel<<<grid, 128, 0, st>>>((const C*)in, ldi, (C*)out, ldo, ncols, N2 * N3, inv, (T)scale);
       return launch_check(ctx, "col_line_kernel");
     };
@@ -269,6 +274,7 @@ struct GridOps {
     gw_status s = set_smem(ctx, kernel, bytes);
     if (s) return s;
     dim3 grid((ncols + 31) / 32, N2 * N3);
+    KTimer kt(ctx, KF_COL_LINE_CT, ((double)ntau * N1 * N2 * N3 + (double)nw * ncols) * ncols * sizeof(C), st);
     kernel<<<grid, 256, bytes, st>>>((const C*)slabs, slab_stride, ld, ntau, (const T*)cw, nw, (C*)out, out_slice,
                                      ldo, inv, N2 * N3, ncols);
     return launch_check(ctx, "col_line_ct_kernel");

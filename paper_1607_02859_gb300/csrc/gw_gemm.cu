@@ -20,6 +20,7 @@ struct GemmP {
   C* Cm;
   long ldc;
   const T* kscale;
+  long sA, sB, sC;
 };
 
 template <typename T, int AKM, bool AC, int BNK, bool BC, bool SCALE, int TRI>
@@ -30,6 +31,9 @@ __global__ void __launch_bounds__(256) cgemm_kernel(GemmP<T> p) {
   __shared__ C Bs[BK][BN + PAD];
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (TRI && n0 > m0 + BM - 1) return;
+  p.A += blockIdx.z * p.sA;
+  p.B += blockIdx.z * p.sB;
+  p.Cm += blockIdx.z * p.sC;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   C acc[4][4];
 #pragma unroll
@@ -109,11 +113,15 @@ static gw_status run_gemm(gw_ctx* ctx, const GemmArgs& a, cudaStream_t st) {
   p.Cm = (C*)a.C;
   p.ldc = a.ldc;
   p.kscale = (const T*)a.kscale;
-  dim3 grid((a.N + 63) / 64, (a.M + 63) / 64);
+  p.sA = a.sA;
+  p.sB = a.sB;
+  p.sC = a.sC;
+  dim3 grid((a.N + 63) / 64, (a.M + 63) / 64, a.batch > 0 ? a.batch : 1);
   if (grid.y > 65535) return fail(ctx, GW_ERR_SHAPE, "GEMM M too large");
 #define GW_GEMM_CASE(AKM, AC, BNK, BC, SC, TRI)                                                   \
   if (a.a_km == AKM && a.a_conj == AC && a.b_nk == BNK && a.b_conj == BC && (a.kscale != nullptr) == SC && \
       a.tri == TRI) {                                                                               \
+    KTimer kt(ctx, KF_CGEMM_SIMT, grid.z * gemm_flops(a.M, a.N, a.K, TRI), st);                   \
     cgemm_kernel<T, AKM, AC, BNK, BC, SC, TRI><<<grid, 256, 0, st>>>(p);                           \
     return launch_check(ctx, "cgemm_kernel");                                                       \
   }

@@ -86,9 +86,86 @@ gw_status check_energies(gw_ctx* ctx, const double* eps, int n_b, int n_occ, dou
   return GW_OK;
 }
 
+static cudaEvent_t take_event(gw_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+KTimer::KTimer(gw_ctx* c, int f, double w, cudaStream_t s) : ctx(c), fam(f), work(w), st(s) {
+  if (ctx && ctx->timing) {
+    a = take_event(ctx);
+    if (a) cudaEventRecord(a, st);
+  }
+}
+
+KTimer::~KTimer() {
+  if (!a) return;
+  cudaEvent_t b = take_event(ctx);
+  if (!b) {
+    ctx->pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, st);
+  ctx->pending.push_back({fam, a, b, work});
+}
+
+static void drain_timers(gw_ctx* ctx) {
+  for (auto& r : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ctx->tot_ms[r.fam] += ms;
+      ctx->tot_work[r.fam] += r.work;
+      ctx->tot_n[r.fam] += 1;
+    }
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->pending.clear();
+  cudaGetLastError();
+}
+
 }  // namespace gw
 
 using namespace gw;
+
+static const char* kFamNames[KF_COUNT] = {"green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft",
+                                          "col_line_ct", "sigma_row"};
+
+extern "C" gw_status gw_ctx_set_timing(gw_ctx* ctx, int enabled) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  drain_timers(ctx);
+  for (int f = 0; f < KF_COUNT; ++f) {
+    ctx->tot_ms[f] = 0;
+    ctx->tot_work[f] = 0;
+    ctx->tot_n[f] = 0;
+  }
+  ctx->timing = enabled != 0;
+  return GW_OK;
+}
+
+extern "C" gw_status gw_ctx_kernel_stats(gw_ctx* ctx, const char* family, unsigned long long* launches, double* ms,
+                                         double* work, int* work_is_bytes) {
+  if (!ctx || !family) return fail(ctx, GW_ERR_ARG, "NULL argument");
+  int f = -1;
+  for (int i = 0; i < KF_COUNT; ++i)
+    if (std::strcmp(family, kFamNames[i]) == 0) f = i;
+  if (f < 0) return fail(ctx, GW_ERR_ARG, std::string("unknown kernel family ") + family);
+  drain_timers(ctx);
+  if (launches) *launches = ctx->tot_n[f];
+  if (ms) *ms = ctx->tot_ms[f];
+  if (work) *work = ctx->tot_work[f];
+  if (work_is_bytes) *work_is_bytes = (f == KF_GREEN_TC || f == KF_CGEMM_TC || f == KF_CGEMM_SIMT) ? 0 : 1;
+  return GW_OK;
+}
 
 // ---------------------------------------------------------------------- context
 
@@ -119,6 +196,8 @@ extern "C" gw_status gw_ctx_destroy(gw_ctx* ctx) {
   if (!ctx) return GW_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  drain_timers(ctx);
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->dflag) cudaFree(ctx->dflag);
   delete ctx;

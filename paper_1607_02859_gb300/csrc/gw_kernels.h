@@ -38,6 +38,8 @@ struct GemmArgs {
   void* C; long ldc;
   const void* kscale;
   int tri;
+  int batch = 1;              // grid z: independent problems sA/sB/sC elements apart
+  long sA = 0, sB = 0, sC = 0;
 };
 gw_status launch_gemm(gw_ctx* ctx, gw_prec prec, const GemmArgs& a, cudaStream_t st);
 

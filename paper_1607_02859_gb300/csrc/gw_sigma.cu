@@ -186,6 +186,7 @@ struct SigmaOps {
                                 "cudaFuncSetAttribute");
       if (rc) return rc;
     }
+    KTimer kt(ctx, KF_SIGMA_ROW, (double)n_rows * (n_chi + 2.0 * RowLayout<N1, N2, N3>::NR) * sizeof(C), st);
     kernel<<<n_rows, 256, bytes, st>>>((const C*)wrg, ldw, map, n_chi, (const C*)go, (const C*)gu, ldg,
                                        (const C*)psi, bands, n_n, r0, coef, acc_u, acc_o, acc_stride);
     return launch_check(ctx, "sigma_row_kernel");

@@ -337,6 +337,23 @@ gw_status tc_make_map(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, l
   return GW_OK;
 }
 
+gw_status tc_make_map3(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, long rows, int batch, int box_rows,
+                       uint32_t fmt) {
+  using namespace tc;
+  gw_status st;
+  EncodeFn enc = encoder(ctx, &st);
+  if (!enc) return st;
+  cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)kpad * 2 * (cuuint64_t)rows};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, GW_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed (" + std::to_string((int)r) + ")");
+  return GW_OK;
+}
+
 namespace tc {
 
 struct Layout {
@@ -444,6 +461,7 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
     gw_status r = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                              "cudaFuncSetAttribute");
     if (r) return r;
+    KTimer kt(ctx, KF_GREEN_TC, 8.0 * n_rows * (double)g.nr * n_b, st);
     kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mah, mal, mbh, mbl, P);
     return launch_check(ctx, "green_tc_kernel");
   };

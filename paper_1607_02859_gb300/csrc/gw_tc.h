@@ -27,6 +27,9 @@ gw_status tc_check(gw_ctx* ctx, void* scratch, cudaStream_t st);
 // box 64 x box_rows, 128-byte swizzle.
 gw_status tc_make_map(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, long rows, int box_rows,
                       uint32_t fmt);
+// Same over a [batch][rows][kpad] array (3-D map, box depth 1).
+gw_status tc_make_map3(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, long rows, int batch, int box_rows,
+                       uint32_t fmt);
 
 // C = alpha * opA(A) opB(B) (+ C if accumulate) on tcgen05 tensor cores with
 // split 16-bit products; opA(m,k) = A[m][k] or A[k][m] (a_trans), conjugated if
@@ -47,8 +50,10 @@ struct TcGemm {
   bool accumulate;
   int tri;
   int* status;          // device: 2 ints, set on a pipeline time-out
+  int batch = 1;        // independent products sA/sB/sC elements apart (grid z)
+  long sA = 0, sB = 0, sC = 0;
 };
-size_t tc_gemm_scratch(int M, int N, int K);
+size_t tc_gemm_scratch(int M, int N, int K, int batch);
 gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cudaStream_t st);
 
 }  // namespace gw

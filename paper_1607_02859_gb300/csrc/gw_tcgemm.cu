@@ -34,7 +34,9 @@ struct KParams {
   long ldc;
   float alpha;
   int accumulate;
-  const unsigned int* maxbits;   // [0] A, [1] B: max |component| (float bits)
+  const unsigned int* maxbits;   // [b] A, [batch + b] B: max |component| (float bits)
+  int batch;
+  long sC;
   int* status;
 };
 
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap mB_lo, KParams p) {
   const int m0 = blockIdx.y * BM;
   const int n0 = blockIdx.x * BNC;
+  const int bz = blockIdx.z;
   if (TRI && n0 > m0 + BM - 1) return;          // tile entirely above the diagonal
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -99,10 +102,10 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
       uint8_t* st = smem + s * STAGE_BYTES;
       const int x = (first + it) * BK;
       mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(st, &mA_hi, &full[s], x, m0);
-      tma_load_2d(st + A_BYTES, &mA_lo, &full[s], x, m0);
-      tma_load_2d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * n0);
-      tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * n0);
+      tma_load_3d(st, &mA_hi, &full[s], x, m0, bz);
+      tma_load_3d(st + A_BYTES, &mA_lo, &full[s], x, m0, bz);
+      tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * n0, bz);
+      tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * n0, bz);
       issued = it + 1;
     }
     if (*abort_flag)
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
       const int q = warp & 3;
       const int row = q * 32 + lane;
       const int gm = m0 + row;
-      const float sc = p.alpha * ldexpf(1.0f, -(scale_exp(p.maxbits[0]) + scale_exp(p.maxbits[1])));
+      const float sc = p.alpha * ldexpf(1.0f, -(scale_exp(p.maxbits[bz]) + scale_exp(p.maxbits[p.batch + bz])));
       const bool have = total > 0;
       const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
 #pragma unroll 1
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
         }
         if (gm < p.M) {
           const int nc0 = n0 + c / 2;
-          float2* o = p.C + (long)gm * p.ldc + nc0;
+          float2* o = p.C + bz * p.sC + (long)gm * p.ldc + nc0;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int gn = nc0 + j;
@@ -181,8 +184,10 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
 }
 
 // max |component| of op(X), rows x K elements of a strided matrix.
-__global__ void maxabs2d_kernel(const float2* __restrict__ X, long ld, int outer, int inner,
+__global__ void maxabs2d_kernel(const float2* __restrict__ X, long ld, int outer, int inner, long sx,
                                 unsigned int* __restrict__ out) {
+  X += blockIdx.y * sx;
+  out += blockIdx.y;
   float m = 0.f;
   const long n = (long)outer * inner;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
@@ -199,12 +204,17 @@ __global__ void maxabs2d_kernel(const float2* __restrict__ X, long ld, int outer
 // or of rows 2i and 2i+1 as (br, -bi), (bi, br) (B form).  A 32 x 32 shared
 // tile makes both the read and the write coalesced for either layout.
 template <bool IS_B, uint32_t FMT>
-__global__ void __launch_bounds__(256) prep_op_kernel(const float2* __restrict__ X, long ld, int trans, int conj,
-                                                      int rows, int K, int kp, const unsigned int* __restrict__ maxbits,
+__global__ void __launch_bounds__(256) prep_op_kernel(const float2* __restrict__ X, long ld, long sx, int trans,
+                                                      int conj, int rows, int K, int kp,
+                                                      const unsigned int* __restrict__ maxbits,
                                                       uint16_t* __restrict__ hi, uint16_t* __restrict__ lo) {
   __shared__ float2 t[32][33];                  // t[i][k]
   const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  const float sc = ldexpf(1.0f, scale_exp(*maxbits));
+  X += blockIdx.z * sx;
+  const long ob = (long)blockIdx.z * (IS_B ? 2 : 1) * rows * kp;
+  hi += ob;
+  lo += ob;
+  const float sc = ldexpf(1.0f, scale_exp(maxbits[blockIdx.z]));
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     // trans: X[k][i] is contiguous in i -> thread x walks i; else walks k
     const int i = trans ? i0 + threadIdx.x : i0 + y;
@@ -246,55 +256,61 @@ __global__ void __launch_bounds__(256) prep_op_kernel(const float2* __restrict__
 
 }  // namespace tg
 
-size_t tc_gemm_scratch(int M, int N, int K) {
-  const size_t kp = (size_t)(2 * K + tg::BK - 1) / tg::BK * tg::BK;
+size_t tc_gemm_scratch(int M, int N, int K, int batch) {
+  const size_t kp = (size_t)(2 * std::max(K, 1) + tg::BK - 1) / tg::BK * tg::BK;
   Carver probe(nullptr);
-  probe.take<unsigned int>(64);
-  probe.take<uint16_t>((size_t)M * kp);
-  probe.take<uint16_t>((size_t)M * kp);
-  probe.take<uint16_t>((size_t)2 * N * kp);
-  probe.take<uint16_t>((size_t)2 * N * kp);
+  probe.take<unsigned int>(256);
+  probe.take<uint16_t>((size_t)batch * M * kp);
+  probe.take<uint16_t>((size_t)batch * M * kp);
+  probe.take<uint16_t>((size_t)batch * 2 * N * kp);
+  probe.take<uint16_t>((size_t)batch * 2 * N * kp);
   return Carver::round(probe.off);
 }
 
 gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cudaStream_t st) {
   using namespace tg;
   if (g.M <= 0 || g.N <= 0) return GW_OK;
+  const int batch = std::max(g.batch, 1);
+  if (batch > 128) return fail(ctx, GW_ERR_SHAPE, "tensor-core GEMM batch above 128");
   const uint32_t fmt = prec == GW_BF16X3 ? 1u : 0u;
   const int K = std::max(g.K, 1);
   const int kp = (2 * K + BK - 1) / BK * BK;
   Carver cv(scratch);
-  unsigned int* words = cv.take<unsigned int>(64);     // [0] max A, [1] max B
-  uint16_t* ahi = cv.take<uint16_t>((size_t)g.M * kp);
-  uint16_t* alo = cv.take<uint16_t>((size_t)g.M * kp);
-  uint16_t* bhi = cv.take<uint16_t>((size_t)2 * g.N * kp);
-  uint16_t* blo = cv.take<uint16_t>((size_t)2 * g.N * kp);
+  unsigned int* words = cv.take<unsigned int>(256);    // [b] max A, [batch + b] max B
+  uint16_t* ahi = cv.take<uint16_t>((size_t)batch * g.M * kp);
+  uint16_t* alo = cv.take<uint16_t>((size_t)batch * g.M * kp);
+  uint16_t* bhi = cv.take<uint16_t>((size_t)batch * 2 * g.N * kp);
+  uint16_t* blo = cv.take<uint16_t>((size_t)batch * 2 * g.N * kp);
   gw_status rc;
-  if ((rc = cuda_check(ctx, cudaMemsetAsync(words, 0, 2 * sizeof(unsigned int), st), "memset"))) return rc;
-  const int blocks = ctx->num_sms * 4;
+  if ((rc = cuda_check(ctx, cudaMemsetAsync(words, 0, 2 * batch * sizeof(unsigned int), st), "memset"))) return rc;
+  const int blocks = std::max(1, ctx->num_sms * 4 / batch);
   // A is [M][K] (or [K][M] if transposed); B's op is [K][N]: stored [K][N], or [N][K] if transposed
-  maxabs2d_kernel<<<blocks, 256, 0, st>>>(g.A, g.lda, g.a_trans ? g.K : g.M, g.a_trans ? g.M : g.K, words);
-  maxabs2d_kernel<<<blocks, 256, 0, st>>>(g.B, g.ldb, g.b_trans ? g.N : g.K, g.b_trans ? g.K : g.N, words + 1);
+  maxabs2d_kernel<<<dim3(blocks, batch), 256, 0, st>>>(g.A, g.lda, g.a_trans ? g.K : g.M, g.a_trans ? g.M : g.K, g.sA,
+                                                       words);
+  maxabs2d_kernel<<<dim3(blocks, batch), 256, 0, st>>>(g.B, g.ldb, g.b_trans ? g.N : g.K, g.b_trans ? g.K : g.N, g.sB,
+                                                       words + batch);
   if ((rc = launch_check(ctx, "maxabs2d_kernel"))) return rc;
   ctx->launches++;
   const dim3 tb(32, 8);
-  const dim3 ga((g.M + 31) / 32, (kp / 2 + 31) / 32), gb((g.N + 31) / 32, (kp / 2 + 31) / 32);
+  const dim3 ga((g.M + 31) / 32, (kp / 2 + 31) / 32, batch), gb((g.N + 31) / 32, (kp / 2 + 31) / 32, batch);
   // B operand rows are indexed by n with k along the row: element (n, k) = opB(k, n), i.e.
-  // B[k][n] (stored [K][N]: "transposed" access for the row-major reader) or B[n][k] (b_trans).
+  // B[k][n] (stored [K][N]: read transposed) or B[n][k] (b_trans: read as is).
   if (fmt == 0) {
-    prep_op_kernel<false, 0><<<ga, tb, 0, st>>>(g.A, g.lda, g.a_trans, g.a_conj, g.M, g.K, kp, words, ahi, alo);
-    prep_op_kernel<true, 0><<<gb, tb, 0, st>>>(g.B, g.ldb, !g.b_trans, g.b_conj, g.N, g.K, kp, words + 1, bhi, blo);
+    prep_op_kernel<false, 0><<<ga, tb, 0, st>>>(g.A, g.lda, g.sA, g.a_trans, g.a_conj, g.M, g.K, kp, words, ahi, alo);
+    prep_op_kernel<true, 0><<<gb, tb, 0, st>>>(g.B, g.ldb, g.sB, !g.b_trans, g.b_conj, g.N, g.K, kp, words + batch,
+                                                bhi, blo);
   } else {
-    prep_op_kernel<false, 1><<<ga, tb, 0, st>>>(g.A, g.lda, g.a_trans, g.a_conj, g.M, g.K, kp, words, ahi, alo);
-    prep_op_kernel<true, 1><<<gb, tb, 0, st>>>(g.B, g.ldb, !g.b_trans, g.b_conj, g.N, g.K, kp, words + 1, bhi, blo);
+    prep_op_kernel<false, 1><<<ga, tb, 0, st>>>(g.A, g.lda, g.sA, g.a_trans, g.a_conj, g.M, g.K, kp, words, ahi, alo);
+    prep_op_kernel<true, 1><<<gb, tb, 0, st>>>(g.B, g.ldb, g.sB, !g.b_trans, g.b_conj, g.N, g.K, kp, words + batch,
+                                                bhi, blo);
   }
   if ((rc = launch_check(ctx, "prep_op_kernel"))) return rc;
   ctx->launches++;
   CUtensorMap mah, mal, mbh, mbl;
-  if ((rc = tc_make_map(ctx, &mah, ahi, kp, g.M, BM, fmt))) return rc;
-  if ((rc = tc_make_map(ctx, &mal, alo, kp, g.M, BM, fmt))) return rc;
-  if ((rc = tc_make_map(ctx, &mbh, bhi, kp, 2L * g.N, 2 * BNC, fmt))) return rc;
-  if ((rc = tc_make_map(ctx, &mbl, blo, kp, 2L * g.N, 2 * BNC, fmt))) return rc;
+  if ((rc = tc_make_map3(ctx, &mah, ahi, kp, g.M, batch, BM, fmt))) return rc;
+  if ((rc = tc_make_map3(ctx, &mal, alo, kp, g.M, batch, BM, fmt))) return rc;
+  if ((rc = tc_make_map3(ctx, &mbh, bhi, kp, 2L * g.N, batch, 2 * BNC, fmt))) return rc;
+  if ((rc = tc_make_map3(ctx, &mbl, blo, kp, 2L * g.N, batch, 2 * BNC, fmt))) return rc;
   KParams P;
   P.M = g.M;
   P.N = g.N;
@@ -304,12 +320,15 @@ gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cud
   P.alpha = g.alpha;
   P.accumulate = g.accumulate ? 1 : 0;
   P.maxbits = words;
+  P.batch = batch;
+  P.sC = g.sC;
   P.status = g.status;
-  const dim3 grid((g.N + BNC - 1) / BNC, (g.M + BM - 1) / BM);
+  const dim3 grid((g.N + BNC - 1) / BNC, (g.M + BM - 1) / BM, batch);
   auto go = [&](auto kernel) -> gw_status {
     gw_status r = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                              "cudaFuncSetAttribute");
     if (r) return r;
+    KTimer kt(ctx, KF_CGEMM_TC, batch * gemm_flops(g.M, g.N, g.K, g.tri), st);
     kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mah, mal, mbh, mbl, P);
     return launch_check(ctx, "cgemm_tc_kernel");
   };

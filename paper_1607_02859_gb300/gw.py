@@ -24,7 +24,7 @@ STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "G
 
 # every symbol declared in include/gw.h
 EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes",
-           "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
+           "gw_ctx_set_timing", "gw_ctx_kernel_stats", "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
            "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc"]
 
@@ -54,6 +54,8 @@ _SIGS = {
     "gw_ctx_launches": (ct.c_ulonglong, [_P]),
     "gw_ctx_scratch_bytes": (ct.c_size_t, [_P]),
     "gw_version": (_I, []),
+    "gw_ctx_set_timing": (_I, [_P, _I]),
+    "gw_ctx_kernel_stats": (_I, [_P, ct.c_char_p, ct.POINTER(ct.c_ulonglong), _DP, _DP, ct.POINTER(ct.c_int)]),
     "gw_g_set": (_I, [_G, _I, _IP, _IP]),
     "gw_coulomb_sqrt": (_I, [_G, _IP, _I, _DP]),
     "gw_fit_transform": (_I, [_I, _DP, _DP, _D, _D, _I, _D, _DP, _DP, _DP, _DP]),
@@ -154,6 +156,24 @@ class Context:
     @property
     def scratch_bytes(self) -> int:
         return int(lib().gw_ctx_scratch_bytes(self.handle))
+
+    FAMILIES = ("green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft", "col_line_ct", "sigma_row")
+
+    def set_timing(self, enabled: bool):
+        _check(lib().gw_ctx_set_timing(self.handle, 1 if enabled else 0), self)
+
+    def kernel_stats(self):
+        """{family: (launches, ms, work, work_is_bytes)} since timing was enabled."""
+        out = {}
+        for fam in self.FAMILIES:
+            n = ct.c_ulonglong(0)
+            ms = ct.c_double(0)
+            w = ct.c_double(0)
+            b = ct.c_int(0)
+            _check(lib().gw_ctx_kernel_stats(self.handle, fam.encode(), ct.byref(n), ct.byref(ms), ct.byref(w),
+                                             ct.byref(b)), self)
+            out[fam] = (int(n.value), float(ms.value), float(w.value), bool(b.value))
+        return out
 
 
 # ------------------------------------------------------------------ host setup
