@@ -27,9 +27,10 @@ gw_status tc_check(gw_ctx* ctx, void* scratch, cudaStream_t st);
 // box 64 x box_rows, 128-byte swizzle.
 gw_status tc_make_map(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, long rows, int box_rows,
                       uint32_t fmt);
-// Same over a [batch][rows][kpad] array (3-D map, box depth 1).
+// Same over a [batch][rows][kpad] array (3-D map, box depth 1), with a box of
+// box_k elements along K and the matching swizzle (64 -> 128 B, 32 -> 64 B).
 gw_status tc_make_map3(gw_ctx* ctx, CUtensorMap* m, const void* base, int kpad, long rows, int batch, int box_rows,
-                       uint32_t fmt);
+                       uint32_t fmt, int box_k);
 
 // C = alpha * opA(A) opB(B) (+ C if accumulate) on tcgen05 tensor cores with
 // split 16-bit products; opA(m,k) = A[m][k] or A[k][m] (a_trans), conjugated if

@@ -20,9 +20,9 @@ namespace tg {
 
 using namespace tcx;
 
-constexpr int BM = 128, BNC = 128, BK = 64, STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = 2 * BNC * BK * 2;
+constexpr int BM = 128, BNC = 128, BK = 32, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;            // 8 KB
+constexpr int B_BYTES = 2 * BNC * BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
@@ -30,13 +30,13 @@ constexpr int THREADS = 192;
 struct KParams {
   int M, N;               // complex output size
   int k_steps;            // BK stages over the padded real K
+  int batch, tm, tn;      // batch entries, row tiles, column tiles
   float2* C;
   long ldc;
+  long sC;
   float alpha;
   int accumulate;
   const unsigned int* maxbits;   // [b] A, [batch + b] B: max |component| (float bits)
-  int batch;
-  long sC;
   int* status;
 };
 
@@ -48,30 +48,37 @@ __device__ __forceinline__ int scale_exp(unsigned int bits) {
   return 15 - ex;
 }
 
+// Persistent: CTA c takes tiles c, c + gridDim.x, ... (row tiles ascending, so
+// the longest tiles of a triangular product go first).  Two 256-column
+// accumulators in tensor memory let the epilogue of one tile run while the
+// MMAs of the next one issue.  Stages are 32 real K (64-byte swizzled rows),
+// four in flight.
 template <uint32_t FMT, int TRI>
 __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_constant__ CUtensorMap mA_hi,
                                                               const __grid_constant__ CUtensorMap mA_lo,
                                                               const __grid_constant__ CUtensorMap mB_hi,
                                                               const __grid_constant__ CUtensorMap mB_lo, KParams p) {
-  const int m0 = blockIdx.y * BM;
-  const int n0 = blockIdx.x * BNC;
-  const int bz = blockIdx.z;
-  if (TRI && n0 > m0 + BM - 1) return;          // tile entirely above the diagonal
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* tfull = empty + STAGES;       // [2] accumulator ready for the epilogue
+  uint64_t* tempty = tfull + 2;           // [2] accumulator drained by the epilogue
+  uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int first = TRI == 2 ? min(2 * m0 / BK, p.k_steps) : 0;
-  const int total = p.k_steps - first;
+  const long per_b = (long)p.tm * p.tn;
+  const long ntiles = per_b * p.batch;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -79,7 +86,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(256));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -90,65 +97,103 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
     *abort_flag = 1;
     if (atomicCAS(p.status, 0, 1) == 0) p.status[1] = where;
   };
+  // tile t -> (batch entry, row tile, column tile); false if above the diagonal
+  auto tile = [&](long t, int& bz, int& bm, int& bn) {
+    bz = (int)(t / per_b);
+    const long r = t - (long)bz * per_b;
+    bm = (int)(r / p.tn);
+    bn = (int)(r - (long)bm * p.tn);
+    return !TRI || bn <= bm;
+  };
+  auto first_k = [&](int bm) { return TRI == 2 ? min(2 * bm * BM / BK, p.k_steps) : 0; };
 
   if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int it = 0; it < total && !*abort_flag; ++it) {
-      const int s = it % STAGES;
-      if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) {
-        timed_out(11);
-        break;
+    // ---------------------------------------------------------- TMA producer
+    long kit = 0;
+    for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+      int bz, bm, bn;
+      if (!tile(t, bz, bm, bn)) continue;
+      for (int ks = first_k(bm); ks < p.k_steps; ++ks, ++kit) {
+        const int s = (int)(kit % STAGES);
+        if (kit >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((kit / STAGES) & 1) ^ 1))) {
+          timed_out(21);
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int x = ks * BK;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_3d(st, &mA_hi, &full[s], x, bm * BM, bz);
+        tma_load_3d(st + A_BYTES, &mA_lo, &full[s], x, bm * BM, bz);
+        tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * bn * BNC, bz);
+        tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * bn * BNC, bz);
       }
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const int x = (first + it) * BK;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &mA_hi, &full[s], x, m0, bz);
-      tma_load_3d(st + A_BYTES, &mA_lo, &full[s], x, m0, bz);
-      tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * n0, bz);
-      tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * n0, bz);
-      issued = it + 1;
     }
     if (*abort_flag)
-      for (int it = issued - STAGES < 0 ? 0 : issued - STAGES; it < issued; ++it)
-        mbar_wait(&full[it % STAGES], (it / STAGES) & 1);
+      for (long it = kit - STAGES < 0 ? 0 : kit - STAGES; it < kit; ++it)
+        mbar_wait(&full[it % STAGES], (uint32_t)((it / STAGES) & 1));
   } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = make_idesc(FMT, 2 * BNC, BM);
-    for (int it = 0; it < total && !*abort_flag; ++it) {
-      const int s = it % STAGES;
-      if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
-        timed_out(12);
+    long kit = 0;
+    int tl = 0;
+    for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+      int bz, bm, bn;
+      if (!tile(t, bz, bm, bn)) continue;
+      const int b = tl & 1;
+      if (tl >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((tl >> 1) & 1) ^ 1))) {
+        timed_out(22);
         break;
       }
       tc_fence_after();
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_BYTES);
-      const uint64_t bh = sw128_desc(st + 2 * A_BYTES), bl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
+      const uint32_t d = tmem + (uint32_t)(b * 256);
+      const int f = first_k(bm);
+      for (int ks = f; ks < p.k_steps; ++ks, ++kit) {
+        const int s = (int)(kit % STAGES);
+        if (!mbar_wait(&full[s], (uint32_t)((kit / STAGES) & 1))) {
+          timed_out(23);
+          break;
+        }
+        tc_fence_after();
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const uint64_t ah = sw64_desc(st), al = sw64_desc(st + A_BYTES);
+        const uint64_t bh = sw64_desc(st + 2 * A_BYTES), bl = sw64_desc(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t off = (uint64_t)(kk * 32) >> 4;
-        umma(tmem, ah + off, bh + off, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-        umma(tmem, ah + off, bl + off, idesc, 1u);
-        umma(tmem, al + off, bh + off, idesc, 1u);
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;    // 16 elements = 32 bytes along K
+          umma(d, ah + off, bh + off, idesc, (ks > f || kk > 0) ? 1u : 0u);
+          umma(d, ah + off, bl + off, idesc, 1u);
+          umma(d, al + off, bh + off, idesc, 1u);
+        }
+        umma_commit(&empty[s]);
       }
-      umma_commit(&empty[s]);
+      umma_commit(&tfull[b]);
+      ++tl;
     }
     umma_commit(done);
+    mbar_wait(done, 0);      // every MMA of this CTA has completed before tensor memory is freed
   } else if (warp >= 2) {
-    const bool ok = mbar_wait(done, 0);
-    if (!ok) timed_out(13);
-    tc_fence_after();
-    if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
-      const int q = warp & 3;
-      const int row = q * 32 + lane;
-      const int gm = m0 + row;
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;                         // tensor-memory lane quarter of this warp
+    const int row = q * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    int tl = 0;
+    for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int bz, bm, bn;
+      if (!tile(t, bz, bm, bn)) continue;
+      const int b = tl & 1;
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)((tl >> 1) & 1));
+      if (!ok) timed_out(24);
+      tc_fence_after();
+      if (!__all_sync(0xffffffffu, ok && !*abort_flag)) break;
+      const int gm = bm * BM + row;
+      const int n0 = bn * BNC;
       const float sc = p.alpha * ldexpf(1.0f, -(scale_exp(p.maxbits[bz]) + scale_exp(p.maxbits[p.batch + bz])));
-      const bool have = total > 0;
-      const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+      const bool have = first_k(bm) < p.k_steps;
 #pragma unroll 1
       for (int c = 0; c < 2 * BNC; c += 16) {
         uint32_t r[16];
         if (have) {
-          tmem_ld16(tmem + lane_addr + c, r);
+          tmem_ld16(tmem + lane_addr + (uint32_t)(b * 256 + c), r);
           tmem_wait_ld();
         } else {
 #pragma unroll
@@ -172,6 +217,10 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+      ++tl;
     }
   }
   tc_fence_before();
@@ -179,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
 }
 
@@ -307,23 +356,28 @@ gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cud
   if ((rc = launch_check(ctx, "prep_op_kernel"))) return rc;
   ctx->launches++;
   CUtensorMap mah, mal, mbh, mbl;
-  if ((rc = tc_make_map3(ctx, &mah, ahi, kp, g.M, batch, BM, fmt))) return rc;
-  if ((rc = tc_make_map3(ctx, &mal, alo, kp, g.M, batch, BM, fmt))) return rc;
-  if ((rc = tc_make_map3(ctx, &mbh, bhi, kp, 2L * g.N, batch, 2 * BNC, fmt))) return rc;
-  if ((rc = tc_make_map3(ctx, &mbl, blo, kp, 2L * g.N, batch, 2 * BNC, fmt))) return rc;
+  if ((rc = tc_make_map3(ctx, &mah, ahi, kp, g.M, batch, BM, fmt, BK))) return rc;
+  if ((rc = tc_make_map3(ctx, &mal, alo, kp, g.M, batch, BM, fmt, BK))) return rc;
+  if ((rc = tc_make_map3(ctx, &mbh, bhi, kp, 2L * g.N, batch, 2 * BNC, fmt, BK))) return rc;
+  if ((rc = tc_make_map3(ctx, &mbl, blo, kp, 2L * g.N, batch, 2 * BNC, fmt, BK))) return rc;
   KParams P;
   P.M = g.M;
   P.N = g.N;
   P.k_steps = kp / BK;
+  P.batch = batch;
+  P.tm = (g.M + BM - 1) / BM;
+  P.tn = (g.N + BNC - 1) / BNC;
   P.C = g.C;
   P.ldc = g.ldc;
+  P.sC = g.sC;
   P.alpha = g.alpha;
   P.accumulate = g.accumulate ? 1 : 0;
   P.maxbits = words;
-  P.batch = batch;
-  P.sC = g.sC;
   P.status = g.status;
-  const dim3 grid((g.N + BNC - 1) / BNC, (g.M + BM - 1) / BM, batch);
+  long tiles = 0;                                       // tiles with work (lower ones only for tri)
+  for (int bm = 0; bm < P.tm; ++bm) tiles += g.tri ? std::min(bm + 1, P.tn) : P.tn;
+  tiles *= batch;
+  const dim3 grid((unsigned)std::max<long>(1, std::min<long>(tiles, ctx->num_sms)));
   auto go = [&](auto kernel) -> gw_status {
     gw_status r = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                              "cudaFuncSetAttribute");

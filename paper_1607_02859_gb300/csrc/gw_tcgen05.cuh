@@ -74,6 +74,22 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* p) {
   return d;
 }
 
+// Same for 64-byte rows (SWIZZLE_64B): 8-row core groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((a & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;                        // SWIZZLE_64B
+  return d;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Instruction descriptor, kind::f16: D = F32, A/B = F16 (fmt 0) or BF16 (fmt 1),
 // both K-major, N x M = n x m.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int n, int m) {
