@@ -19,8 +19,8 @@
 // paid once per batch instead of once per frequency, and the GEMMs grow.
 //  * CUDA-core precisions: 64-column panels; the trailing updates are CUDA-core
 //    complex GEMMs.
-//  * tensor-core precisions: 256-column panels whose 256 x 256 diagonal blocks
-//    are factored and inverted on CUDA cores; everything with a 256-wide inner
+//  * tensor-core precisions: 512-column panels whose 512 x 512 diagonal blocks
+//    are factored and inverted on CUDA cores; everything with a 512-wide inner
 //    dimension is a tcgen05 GEMM with split 16-bit products:
 //      L21 = A21 (1 + P11)^H,  A22 -= L21 L21^H,
 //      P_i[:, <k0] += P_ii P_i[:, <k0],  rows below -= L_li (1 + P_i),
@@ -34,7 +34,7 @@
 namespace gw {
 
 constexpr int kNB = 64;     // CUDA-core panel width
-constexpr int kTB = 256;    // tensor-core panel width
+constexpr int kTB = 512;    // tensor-core panel width
 
 template <typename T>
 __global__ void build_eps_kernel(const typename cpx<T>::t* __restrict__ chi, long s_chi,

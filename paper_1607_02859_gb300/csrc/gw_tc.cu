@@ -16,9 +16,10 @@
 // (dropping A_lo B_lo ~ 2^-22 |A||B|), accumulated in FP32.  bf16 splits are
 // the same code with a coarser 2 x 8-bit representation.
 //
-// Tile: 128 rows r x 128 complex columns R' (MMA 128 x 256 x 16), K staged 64
-// real elements (128 B, SWIZZLE_128B) at a time through a 2-stage TMA/mbarrier
-// pipeline.  G_occ and G_unocc accumulate in two 256-column halves of tensor
+// Tile: 128 rows r x 128 complex columns R' (MMA 128 x 256 x 16), K staged 32
+// real elements (64 B, SWIZZLE_64B) at a time through a 4-stage TMA/mbarrier
+// pipeline; the epilogue stages rows in shared memory and writes 128-byte row
+// segments.  G_occ and G_unocc accumulate in two 256-column halves of tensor
 // memory; the epilogue either writes both (gw_green_tau) or their product
 // chi = -2 G_occ conj(G_unocc) (gw_chi0_rtau_fused), so for chi neither G tile
 // ever reaches HBM.  Warp roles: 0 = TMA producer, 1 = MMA issuer (and tensor
@@ -42,12 +43,14 @@ using namespace tcx;
 
 constexpr int BM = 128;                 // rows per tile
 constexpr int BNC = 128;                // complex columns per tile (MMA N = 256)
-constexpr int BK = 64;                  // real K per stage (one 128-byte swizzle row)
-constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;            // 16 KB
-constexpr int B_BYTES = 2 * BNC * BK * 2;       // 32 KB
+constexpr int BK = 32;                  // real K per stage (one 64-byte swizzle row)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;            // 8 KB
+constexpr int B_BYTES = 2 * BNC * BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int EPI_COLS = 16;                    // complex columns per epilogue round
+constexpr int EPI_BYTES = 4 * 32 * EPI_COLS * 8;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
 
 struct Params {
@@ -73,7 +76,8 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap mB_lo, Params p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  float2* epi = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);     // [4 warps][32 rows][16]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + EPI_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -120,10 +124,10 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
       uint8_t* st = smem + s * STAGE_BYTES;
       const int x = it < p.k_occ_steps ? it * BK : p.k_un_x + (it - p.k_occ_steps) * BK;
       mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(st, &mA_hi, &full[s], x, m0);
-      tma_load_2d(st + A_BYTES, &mA_lo, &full[s], x, m0);
-      tma_load_2d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * n0);
-      tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * n0);
+      tma_load_3d(st, &mA_hi, &full[s], x, m0, 0);
+      tma_load_3d(st + A_BYTES, &mA_lo, &full[s], x, m0, 0);
+      tma_load_3d(st + 2 * A_BYTES, &mB_hi, &full[s], x, 2 * n0, 0);
+      tma_load_3d(st + 2 * A_BYTES + B_BYTES, &mB_lo, &full[s], x, 2 * n0, 0);
       issued = it + 1;
     }
     if (*abort_flag) {
@@ -146,8 +150,8 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
       const int kin = un ? it - p.k_occ_steps : it;
       const uint32_t d = tmem + (un ? 256u : 0u);
       uint8_t* st = smem + s * STAGE_BYTES;
-      const uint64_t ah = sw128_desc(st), al = sw128_desc(st + A_BYTES);
-      const uint64_t bh = sw128_desc(st + 2 * A_BYTES), bl = sw128_desc(st + 2 * A_BYTES + B_BYTES);
+      const uint64_t ah = sw64_desc(st), al = sw64_desc(st + A_BYTES);
+      const uint64_t bh = sw64_desc(st + 2 * A_BYTES), bl = sw64_desc(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t off = (uint64_t)(kk * 32) >> 4;    // 16 elements = 32 bytes along K
@@ -166,34 +170,54 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
     // tcgen05.ld is warp-collective: the whole warp takes the same branch
     if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
       const int q = warp & 3;                       // tensor-memory lane quarter of this warp
-      const int row = q * 32 + lane;
-      const int gm = m0 + row;
+      const int r0 = m0 + q * 32;                   // first output row of this warp
       const float sc = ldexpf(1.0f, -2 * (*p.dexp));
       const float ao = p.alpha_occ * sc, au = p.alpha_un * sc;
       const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+      float2* stg = epi + q * 32 * EPI_COLS;
 #pragma unroll 1
-      for (int c = 0; c < 2 * BNC; c += 16) {
-        uint32_t ro[16], ru[16];
-        tmem_ld16(tmem + lane_addr + c, ro);
-        tmem_ld16(tmem + lane_addr + 256 + c, ru);
-        tmem_wait_ld();
-        if (gm < p.m_rows) {
-          const int nc0 = n0 + c / 2;
-          float2* o0 = p.out0 + (long)gm * p.ldo + nc0;
-          float2* o1 = p.out1 + (long)gm * p.ldo + nc0;
+      for (int c = 0; c < 2 * BNC; c += 2 * EPI_COLS) {
+        uint32_t ro[2][16], ru[2][16];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (nc0 + j >= p.n_cols) break;
-            const float gor = __uint_as_float(ro[2 * j]) * ao, goi = __uint_as_float(ro[2 * j + 1]) * ao;
-            const float gur = __uint_as_float(ru[2 * j]) * au, gui = __uint_as_float(ru[2 * j + 1]) * au;
-            if (MODE == 0) {
-              // -2 * go * conj(gu)
-              o0[j] = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
+        for (int u = 0; u < 2; ++u) {
+          tmem_ld16(tmem + lane_addr + c + 16 * u, ro[u]);
+          tmem_ld16(tmem + lane_addr + 256 + c + 16 * u, ru[u]);
+        }
+        tmem_wait_ld();
+        const int nc0 = n0 + c / 2;
+#pragma unroll 1
+        for (int pass = 0; pass < (MODE == 0 ? 1 : 2); ++pass) {
+          // row `lane` of the chunk to shared memory (rotated), then 128-byte row segments out
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float gor = __uint_as_float(ro[u][2 * j]) * ao, goi = __uint_as_float(ro[u][2 * j + 1]) * ao;
+              const float gur = __uint_as_float(ru[u][2 * j]) * au, gui = __uint_as_float(ru[u][2 * j + 1]) * au;
+              float2 v;
+              if (MODE == 0) v = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
+              else v = pass == 0 ? make_float2(gor, goi) : make_float2(gur, gui);
+              stg[lane * EPI_COLS + ((u * 8 + j + lane) & (EPI_COLS - 1))] = v;
+            }
+          __syncwarp();
+          float2* outp = (MODE == 0 || pass == 0) ? p.out0 : p.out1;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int idx = i * 32 + lane;
+            const int rr = idx >> 3, pc = (idx & 7) * 2;
+            const int gm = r0 + rr, gn = nc0 + pc;
+            if (gm >= p.m_rows || gn >= p.n_cols) continue;
+            const float2 v0 = stg[rr * EPI_COLS + ((pc + rr) & (EPI_COLS - 1))];
+            const float2 v1 = stg[rr * EPI_COLS + ((pc + 1 + rr) & (EPI_COLS - 1))];
+            float2* o = outp + (long)gm * p.ldo + gn;
+            if (gn + 1 < p.n_cols && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+              *reinterpret_cast<float4*>(o) = make_float4(v0.x, v0.y, v1.x, v1.y);
             } else {
-              o0[j] = make_float2(gor, goi);
-              o1[j] = make_float2(gur, gui);
+              o[0] = v0;
+              if (gn + 1 < p.n_cols) o[1] = v1;
             }
           }
+          __syncwarp();
         }
       }
     }
@@ -440,10 +464,10 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
                                                L.k_occ_pad, L.k_un_x, L.kpad, ahi, alo);
   if ((rc = launch_check(ctx, "prep_kernel(A)"))) return rc;
   CUtensorMap mah, mal, mbh, mbl;
-  if ((rc = tc_make_map(ctx, &mah, ahi, L.kpad, n_rows, BM, fmt))) return rc;
-  if ((rc = tc_make_map(ctx, &mal, alo, L.kpad, n_rows, BM, fmt))) return rc;
-  if ((rc = tc_make_map(ctx, &mbh, bhi, L.kpad, 2L * g.nr, 2 * BNC, fmt))) return rc;
-  if ((rc = tc_make_map(ctx, &mbl, blo, L.kpad, 2L * g.nr, 2 * BNC, fmt))) return rc;
+  if ((rc = tc_make_map3(ctx, &mah, ahi, L.kpad, n_rows, 1, BM, fmt, BK))) return rc;
+  if ((rc = tc_make_map3(ctx, &mal, alo, L.kpad, n_rows, 1, BM, fmt, BK))) return rc;
+  if ((rc = tc_make_map3(ctx, &mbh, bhi, L.kpad, 2L * g.nr, 1, 2 * BNC, fmt, BK))) return rc;
+  if ((rc = tc_make_map3(ctx, &mbl, blo, L.kpad, 2L * g.nr, 1, 2 * BNC, fmt, BK))) return rc;
   Params P;
   P.m_rows = n_rows;
   P.n_cols = g.nr;

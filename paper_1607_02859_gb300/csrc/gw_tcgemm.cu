@@ -24,7 +24,9 @@ constexpr int BM = 128, BNC = 128, BK = 32, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;            // 8 KB
 constexpr int B_BYTES = 2 * BNC * BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int EPI_COLS = 32;                     // complex columns per epilogue round
+constexpr int EPI_BYTES = 4 * 32 * EPI_COLS * 8; // per epilogue warp: 32 rows x 32 complex
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
 constexpr int THREADS = 192;
 
 struct KParams {
@@ -60,7 +62,8 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap mB_lo, KParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  float2* epi = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);     // [4 warps][32 rows][32]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + EPI_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;       // [2] accumulator ready for the epilogue
   uint64_t* tempty = tfull + 2;           // [2] accumulator drained by the epilogue
@@ -185,37 +188,85 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
       if (!ok) timed_out(24);
       tc_fence_after();
       if (!__all_sync(0xffffffffu, ok && !*abort_flag)) break;
-      const int gm = bm * BM + row;
       const int n0 = bn * BNC;
+      const int r0 = bm * BM + q * 32;                // first output row of this warp
       const float sc = p.alpha * ldexpf(1.0f, -(scale_exp(p.maxbits[bz]) + scale_exp(p.maxbits[p.batch + bz])));
       const bool have = first_k(bm) < p.k_steps;
+      float2* stg = epi + q * 32 * EPI_COLS;          // this warp's 32 x 32 staging tile
+      float2* cb = p.C + bz * p.sC;
 #pragma unroll 1
-      for (int c = 0; c < 2 * BNC; c += 16) {
-        uint32_t r[16];
+      for (int c = 0; c < 2 * BNC; c += 2 * EPI_COLS) {
+        // four 16-column loads from tensor memory: row `lane`, complex columns c/2 .. c/2+31
+        uint32_t r[4][16];
         if (have) {
-          tmem_ld16(tmem + lane_addr + (uint32_t)(b * 256 + c), r);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) tmem_ld16(tmem + lane_addr + (uint32_t)(b * 256 + c + 16 * u), r[u]);
           tmem_wait_ld();
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) r[j] = 0u;
-        }
-        if (gm < p.M) {
-          const int nc0 = n0 + c / 2;
-          float2* o = p.C + bz * p.sC + (long)gm * p.ldc + nc0;
+          for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int gn = nc0 + j;
-            if (gn >= p.N) break;
-            if (TRI && gn > gm) break;
-            float2 v = make_float2(__uint_as_float(r[2 * j]) * sc, __uint_as_float(r[2 * j + 1]) * sc);
-            if (p.accumulate) {
-              const float2 old = o[j];
-              v.x += old.x;
-              v.y += old.y;
-            }
-            o[j] = v;
+            for (int j = 0; j < 16; ++j) r[u][j] = 0u;
+        }
+        // row-rotated staging so that both the writes here and the row reads below are spread over banks
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            stg[lane * EPI_COLS + ((u * 8 + j + lane) & (EPI_COLS - 1))] =
+                make_float2(__uint_as_float(r[u][2 * j]) * sc, __uint_as_float(r[u][2 * j + 1]) * sc);
+        __syncwarp();
+        const int nc0 = n0 + c / 2;
+        // 16 pairs of complex values per lane: two 256-byte row segments per warp instruction
+        float4 old[16];
+        if (p.accumulate) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int idx = i * 32 + lane;
+            const int rr = idx >> 4, pc = (idx & 15) * 2;
+            const int gm = r0 + rr, gn = nc0 + pc;
+            const float2* o = cb + (long)gm * p.ldc + gn;
+            const bool full2 = gm < p.M && gn + 1 < p.N && ((reinterpret_cast<uintptr_t>(o) & 15) == 0);
+            old[i] = full2 ? *reinterpret_cast<const float4*>(o) : make_float4(0.f, 0.f, 0.f, 0.f);
           }
         }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int idx = i * 32 + lane;
+          const int rr = idx >> 4, pc = (idx & 15) * 2;
+          const int gm = r0 + rr, gn = nc0 + pc;
+          if (gm >= p.M) continue;
+          float2 v0 = stg[rr * EPI_COLS + ((pc + rr) & (EPI_COLS - 1))];
+          float2 v1 = stg[rr * EPI_COLS + ((pc + 1 + rr) & (EPI_COLS - 1))];
+          float2* o = cb + (long)gm * p.ldc + gn;
+          const bool ok0 = gn < p.N && (!TRI || gn <= gm);
+          const bool ok1 = gn + 1 < p.N && (!TRI || gn + 1 <= gm);
+          if (gn + 1 < p.N && ((reinterpret_cast<uintptr_t>(o) & 15) == 0) && ok0 && ok1) {
+            if (p.accumulate) {
+              v0.x += old[i].x;
+              v0.y += old[i].y;
+              v1.x += old[i].z;
+              v1.y += old[i].w;
+            }
+            *reinterpret_cast<float4*>(o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+          } else {
+            if (ok0) {
+              if (p.accumulate) {
+                v0.x += o[0].x;
+                v0.y += o[0].y;
+              }
+              o[0] = v0;
+            }
+            if (ok1) {
+              if (p.accumulate) {
+                v1.x += o[1].x;
+                v1.y += o[1].y;
+              }
+              o[1] = v1;
+            }
+          }
+        }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
