@@ -33,6 +33,14 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "chi0+Sigma_nn effective TFLOP/s"
+ACCURACY = {
+    "f16x3": "G, Sigma and screening contractions as 3 fp16 split products on tcgen05 (fp32 accumulate); "
+             "tested: Sigma_nn within 1 meV of the FP64 oracle, chi0(i omega) within 5e-6 relative (sampled rows at "
+             "this size)",
+    "fp32": "all steps FP32 on CUDA cores; tested: chi0(i omega) within 1e-6 relative, Sigma_nn within 1 meV",
+    "fp64": "all steps FP64 on CUDA cores",
+    "bf16x3": "3 bf16 split products on tcgen05; tested: chi0 within 2e-5 relative, Sigma_nn within 1 meV",
+}
 N_REAL = 64          # real frequencies of the continued Sigma_nn(omega)
 FLUSH_BYTES = 512 << 20
 
@@ -180,7 +188,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "f16x3", "bf16x3"])
+    ap.add_argument("--prec", default="f16x3", choices=["fp32", "fp64", "f16x3", "bf16x3"])
     ap.add_argument("--workload", default="si8", choices=["si8", "mid", "gamma_toy"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-stage pass")
@@ -193,7 +201,8 @@ def main():
     workload = {"workload": "%s: %dx%dx%d grid (N_r=%d), %d+%d %s bands, %d tau/i omega, chi0 %dx%d, Sigma_nn for %d bands"
                 % (args.workload, *p.n, p.n_r, p.n_occ, p.n_b - p.n_occ, "real" if p.real else "complex", n_tau,
                    p.n_chi, p.n_chi, len(p.bands)),
-                "prec": args.prec, "l2": "per-step working set > 40 GB >> 129 MB L2; L2 also flushed between steps"}
+                "prec": args.prec, "l2": "per-step working set > 40 GB >> 129 MB L2; L2 also flushed between steps",
+                "accuracy": ACCURACY.get(args.prec, "")}
     if args.impl == "reference":
         run_reference(args, p, workload)
         return
@@ -339,7 +348,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "f16x3": "f16x3->f32", "bf16x3": "bf16x3->f32"}[args.prec],
             "data": "synthetic", "config": dict(workload, parallelism="replicas x%d" % world),
             "stage_ms": stage_ms, "kernels": kernels, "flops_per_step": fl, "roofline": roof, "e2e": e2e,
             "gpu_launches": int(launches),

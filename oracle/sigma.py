@@ -63,3 +63,34 @@ def sigma_iw(s_unocc, s_occ, C, S):
     sc = 0.5 * (s_unocc + s_occ)
     ss = 0.5 * (s_unocc - s_occ)
     return sc @ C.T + 1j * (ss @ S.T)
+
+
+def sigma_pair_sparse(psi, eps, n_occ, mu, taus, entries, n, lattice, fft_index, bands):
+    """The conventional route of sigma_pair_tau for a W~(G,G',tau) with only a
+    few nonzero entries, given as (j, j', values) with G-set indices j, j' and
+    one value per tau:
+    Sigma_unocc_nn(tau) = (1/Omega) sum_{m unocc} exp(-(eps_m-mu) tau)
+                          sum_(j,j') conj(a_nm(G_j)) W~_jj'(tau) a_nm(G_j'),
+    Sigma_occ_nn(-tau) likewise over occupied m with exp(+(eps_m-mu) tau) and a
+    minus sign; a_nm(G) = dV sum_r exp(-iG.r) psi_m^*(r) psi_n(r).
+    Returns ([N_n][N_tau], [N_n][N_tau])."""
+    vol = abs(np.linalg.det(lattice))
+    dv = vol / int(np.prod(n))
+    taus = np.atleast_1d(np.asarray(taus, dtype=np.float64))
+    idx = sorted({e[0] for e in entries} | {e[1] for e in entries})
+    pos = {j: k for k, j in enumerate(idx)}
+    su = np.empty((len(bands), len(taus)))
+    so = np.empty((len(bands), len(taus)))
+    for b, n_ in enumerate(bands):
+        prod = psi.conj() * psi[n_][None, :]
+        f = np.fft.fftn(prod.reshape(psi.shape[0], *n), axes=(1, 2, 3)).reshape(psi.shape[0], -1)
+        a = dv * f[:, np.asarray(fft_index)[idx]]                  # [N_b][len(idx)]
+        for t, tau in enumerate(taus):
+            q = np.zeros(psi.shape[0])
+            for (j, jp, vals) in entries:
+                val = np.atleast_1d(vals)[t]
+                q += (np.conj(a[:, pos[j]]) * val * a[:, pos[jp]]).real
+            q /= vol
+            su[b, t] = (np.exp(-(eps[n_occ:] - mu) * tau) * q[n_occ:]).sum()
+            so[b, t] = -(np.exp((eps[:n_occ] - mu) * tau) * q[:n_occ]).sum()
+    return su, so

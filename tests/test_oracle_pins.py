@@ -369,3 +369,38 @@ def test_thiele_breakdown_raises():
     z = 1j * np.array([1.0, 2.0, 3.0])
     with pytest.raises(oth.ThieleBreakdown):
         oth.coefficients(z, np.array([1.0, 2.0, 1.0]))
+
+
+def test_fft_pair_elements_and_rows_match_dense_definitions(tiny_c):
+    """The FFT-based pair matrix elements and chi rows used for full-size sampled
+    checks equal the dense-phase-matrix definitions."""
+    p = tiny_c
+    gv = ogv.g_set(p.n, p.n_r)
+    idx = ogv.fft_index(gv, p.n)
+    dense = ochi.pair_matrix_elements(p.psi, p.n_occ, gv, p.n, p.lattice)      # [Nu][No][Nchi]
+    for i in range(p.n_occ):
+        m = ochi.pair_matrix_elements_fft(p.psi, i, np.arange(p.n_occ, p.n_b), p.n, p.lattice, idx)
+        assert np.allclose(m, dense[:, i, :], atol=1e-13)
+    rows = [0, 5, 77]
+    taus = [0.1, 2.0]
+    got = ochi.chi_rows_pair(p.psi, p.eps, p.n_occ, taus, rows, p.n, p.lattice, idx)
+    for j, t in enumerate(taus):
+        full = ochi.chi_pair(p.psi, p.eps, p.n_occ, p.mu, t, gv, p.n, p.lattice, m=dense)
+        assert np.allclose(got[j], full[rows], atol=1e-14)
+
+
+def test_sparse_pair_sigma_matches_dense(tiny_c):
+    p = tiny_c
+    gv = ogv.g_set(p.n, p.n_r)
+    idx = ogv.fft_index(gv, p.n)
+    taus = [0.2, 3.0]
+    entries = [(3, 3, [-0.4, -0.3]), (10, 10, [-0.2, -0.1]), (3, 10, [0.05 + 0.02j, 0.01j]),
+               (10, 3, [0.05 - 0.02j, -0.01j])]
+    a = osg.sigma_pair_sparse(p.psi, p.eps, p.n_occ, p.mu, taus, entries, p.n, p.lattice, idx, p.bands)
+    for t, tau in enumerate(taus):
+        w = np.zeros((p.n_r, p.n_r), dtype=complex)
+        for j, jp, v in entries:
+            w[j, jp] = v[t]
+        b = osg.sigma_pair_tau(p.psi, p.eps, p.n_occ, p.mu, tau, w, gv, p.n, p.lattice, p.bands)
+        assert np.allclose(a[0][:, t], b[0], atol=1e-14)
+        assert np.allclose(a[1][:, t], b[1], atol=1e-14)
