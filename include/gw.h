@@ -120,6 +120,14 @@ gw_status gw_fit_transform(int n, const double* tau_h, const double* omega_h,
                            double x_min, double x_max, int n_x, double ridge,
                            double* C_h, double* S_h, double* Cinv_h, double* fit_err_h);
 
+/* Device scratch in bytes that the context arena needs for gw_chi0_omega
+ * (r_block <= 0: the default), gw_screen_W (n frequencies) and gw_sigma_diag
+ * (n_n bands, up to 64 real frequencies) on this problem.  The arena is shared
+ * by the calls of one context, so a context needs the largest of the three.
+ * Host only; any output may be NULL.  Used for admission by memory footprint. */
+gw_status gw_workspace_size(const gw_grid* grid, int n_b, int n_occ, int n, int n_chi, int n_n, gw_prec prec,
+                            int r_block, size_t* chi0_bytes, size_t* screen_bytes, size_t* sigma_bytes);
+
 /* ---------------------------------------------------------------- hot path */
 
 /* Imaginary-time Green's functions for the rows r0 .. r0+n_rows-1 (Eqs.

@@ -508,9 +508,47 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
   return launch_check(ctx, "finalize_kernel");
 }
 
+// Frequencies per batch (the two work matrices of a batch within 64 GB) and
+// the scratch gw_screen_W needs.
+size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* nbatch_out) {
+  const size_t es = csize(prec);
+  const size_t nn = (size_t)n_chi * n_chi;
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  const size_t budget = size_t(64) << 30;
+  const int no = std::max(n_omega, 1);
+  const int bmax = (int)std::max<size_t>(1, std::min<size_t>(no, budget / (2 * nn * es)));
+  const int nbatch = (no + bmax - 1) / bmax;
+  const int bsz = (no + nbatch - 1) / nbatch;
+  Carver probe(nullptr);
+  probe.take<double>(n_chi);
+  probe.take<char>(bsz * nn * es);
+  probe.take<char>(bsz * nn * es);
+  probe.take<double2>(4 * (size_t)n_chi);
+  if (tc) probe.take<char>(std::max(tc_gemm_scratch(n_chi, n_chi, n_chi, 1), tc_gemm_scratch(n_chi, n_chi, kTB, bsz)));
+  if (bsz_out) *bsz_out = bsz;
+  if (nbatch_out) *nbatch_out = nbatch;
+  return probe.off;
+}
+
 }  // namespace gw
 
 using namespace gw;
+
+extern "C" gw_status gw_workspace_size(const gw_grid* grid, int n_b, int n_occ, int n, int n_chi, int n_n,
+                                       gw_prec prec, int r_block, size_t* chi0_bytes, size_t* screen_bytes,
+                                       size_t* sigma_bytes) {
+  GridInfo g;
+  gw_status st = grid_info(nullptr, grid, &g);
+  if (st) return st;
+  if (!valid_prec(prec)) return fail(nullptr, GW_ERR_ARG, "bad precision");
+  if (n_b < 2 || n_occ < 1 || n_occ >= n_b || n < 1 || n_chi < 1 || n_chi > g.nr || n_n < 1)
+    return fail(nullptr, GW_ERR_SHAPE, "bad sizes");
+  const int rb = r_block > 0 ? std::min(r_block, g.nr) : std::min(g.nr, 2048);
+  if (chi0_bytes) *chi0_bytes = chi0_omega_scratch(g, n_b, n_occ, n, n_chi, prec, rb);
+  if (screen_bytes) *screen_bytes = screen_scratch(n_chi, n, prec, nullptr, nullptr);
+  if (sigma_bytes) *sigma_bytes = sigma_scratch(g, n_b, n_occ, n, n_chi, n_n, 64, prec);
+  return GW_OK;
+}
 
 extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h, int n_omega,
                                  gw_prec prec, const void* chi_w, void* w_w, double* resid_h, void* stream) {
@@ -529,20 +567,11 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
   const size_t es = csize(prec);
   const size_t nn = (size_t)n_chi * n_chi;
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
-  // frequencies per batch: the two work matrices of a batch within 64 GB
-  const size_t budget = size_t(64) << 30;
-  const int bmax = (int)std::max<size_t>(1, std::min<size_t>(n_omega, budget / (2 * nn * es)));
-  const int nbatch = (n_omega + bmax - 1) / bmax;
-  const int bsz = (n_omega + nbatch - 1) / nbatch;
-  Carver probe(nullptr);
-  probe.take<double>(n_chi);
-  probe.take<char>(bsz * nn * es);
-  probe.take<char>(bsz * nn * es);
-  probe.take<double2>(4 * (size_t)n_chi);
+  int bsz = 0, nbatch = 0;
+  const size_t need = screen_scratch(n_chi, n_omega, prec, &bsz, &nbatch);
   const size_t tcs_bytes =
       tc ? std::max(tc_gemm_scratch(n_chi, n_chi, n_chi, 1), tc_gemm_scratch(n_chi, n_chi, kTB, bsz)) : 0;
-  if (tc) probe.take<char>(tcs_bytes);
-  if ((st = reserve(ctx, probe.off))) return st;
+  if ((st = reserve(ctx, need))) return st;
   Carver cv(ctx->arena);
   double* dvh = cv.take<double>(n_chi);
   void* E = cv.take<char>(bsz * nn * es);

@@ -13,6 +13,25 @@
 #include "gw_kernels.h"
 #include "gw_tc.h"
 
+namespace gw {
+
+size_t chi0_omega_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, gw_prec prec, int rb) {
+  const size_t es = csize(prec);
+  const size_t slab = (size_t)g.nr * n_chi;
+  Carver probe(nullptr);
+  probe.take<int>(n_chi);
+  probe.take<int>(g.nr);
+  probe.take<double>((size_t)n * n_b);
+  probe.take<double>((size_t)n * n);
+  probe.take<char>(slab * n * es);
+  probe.take<char>((size_t)rb * g.nr * es);
+  probe.take<char>((size_t)rb * g.nr * es);
+  if (prec == GW_F16X3 || prec == GW_BF16X3) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
+  return probe.off;
+}
+
+}  // namespace gw
+
 using namespace gw;
 
 extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
@@ -38,16 +57,7 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   const int rb = r_block > 0 ? std::min(r_block, g.nr) : std::min(g.nr, 2048);
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
   const size_t slab = (size_t)g.nr * n_chi;
-  Carver probe(nullptr);
-  probe.take<int>(n_chi);
-  probe.take<int>(g.nr);
-  probe.take<double>((size_t)n * n_b);
-  probe.take<double>((size_t)n * n);
-  probe.take<char>(slab * n * es);
-  probe.take<char>((size_t)rb * g.nr * es);
-  probe.take<char>((size_t)rb * g.nr * es);
-  if (tc) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
-  if ((st = reserve(ctx, probe.off))) return st;
+  if ((st = reserve(ctx, chi0_omega_scratch(g, n_b, n_occ, n, n_chi, prec, rb)))) return st;
   Carver cv(ctx->arena);
   int* dmap = cv.take<int>(n_chi);
   int* dinv = cv.take<int>(g.nr);

@@ -208,6 +208,25 @@ static gw_status launch_sigma_rows(gw_ctx* ctx, const GridInfo& g, gw_prec prec,
   return fail(ctx, GW_ERR_UNSUPPORTED, "no kernels compiled for this grid");
 }
 
+size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec) {
+  const size_t es = csize(prec);
+  const int rb = std::min(g.nr, 2048);
+  Carver probe(nullptr);
+  probe.take<int>(n_chi);
+  probe.take<int>(g.nr);
+  probe.take<int>(n_n);
+  probe.take<double>((size_t)n * n_b);
+  probe.take<double>(4 * (size_t)n * n + 2 * n + std::max(n_real, 1));
+  probe.take<double>(2 * (size_t)n_n * n);
+  probe.take<double2>((size_t)n_n * n + (size_t)n_n * std::max(n_real, 1));
+  probe.take<int>(n_n);
+  probe.take<char>((size_t)g.nr * n_chi * es);
+  probe.take<char>((size_t)rb * g.nr * es);
+  probe.take<char>((size_t)rb * g.nr * es);
+  if (prec == GW_F16X3 || prec == GW_BF16X3) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
+  return probe.off;
+}
+
 }  // namespace gw
 
 using namespace gw;
@@ -240,21 +259,8 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   cudaStream_t s = as_stream(stream);
   const size_t es = csize(prec);
   const int rb = std::min(g.nr, 2048);
-  Carver probe(nullptr);
-  probe.take<int>(n_chi);
-  probe.take<int>(g.nr);
-  probe.take<int>(n_n);
-  probe.take<double>((size_t)n * n_b);
-  probe.take<double>(4 * (size_t)n * n + 2 * n + std::max(n_real, 1));
-  probe.take<double>(2 * (size_t)n_n * n);
-  probe.take<double2>((size_t)n_n * n + (size_t)n_n * std::max(n_real, 1));
-  probe.take<int>(n_n);
-  probe.take<char>((size_t)g.nr * n_chi * es);
-  probe.take<char>((size_t)rb * g.nr * es);
-  probe.take<char>((size_t)rb * g.nr * es);
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
-  if (tc) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
-  if ((st = reserve(ctx, probe.off))) return st;
+  if ((st = reserve(ctx, sigma_scratch(g, n_b, n_occ, n, n_chi, n_n, n_real, prec)))) return st;
   Carver cv(ctx->arena);
   int* dmap = cv.take<int>(n_chi);
   int* dinv = cv.take<int>(g.nr);

@@ -26,7 +26,7 @@ STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "G
 EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes",
            "gw_ctx_set_timing", "gw_ctx_kernel_stats", "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
-           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc"]
+           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size"]
 
 
 class GwError(RuntimeError):
@@ -64,6 +64,8 @@ _SIGS = {
     "gw_chi0_rtau_fused": (_I, [_P, _G, _I, _I, _P, _DP, _D, _D, _I, _I, _I, _P, _P]),
     "gw_rr_to_GG_fft": (_I, [_P, _G, _I, _I, _I, _IP, _I, _I, _I, _P, _P, _P]),
     "gw_rr_to_GG_fft_noalloc": (_I, [_G, _I, _I, _I, _IP, _I, _I, _I, _P, _P, _P]),
+    "gw_workspace_size": (_I, [_G, _I, _I, _I, _I, _I, _I, _I, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t),
+                               ct.POINTER(ct.c_size_t)]),
     "gw_tau_to_omega": (_I, [_P, _I, _I, _DP, ct.c_size_t, _I, _P, _P, _P]),
     "gw_screen_W": (_I, [_P, _G, _I, _IP, _I, _I, _P, _P, _DP, _P]),
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
@@ -203,6 +205,14 @@ def fit_transform(tau, omega, x_min, x_max, n_x=4000, ridge=1e-6):
     _check(lib().gw_fit_transform(n, _dp(tau), _dp(omega), float(x_min), float(x_max), int(n_x), float(ridge),
                                   _dp(C), _dp(S), _dp(Ci), _dp(err)))
     return {"C": C, "S": S, "Cinv": Ci, "fit_err_cos": err[0], "fit_err_sin": err[1]}
+
+
+def workspace_size(grid, n_b, n_occ, n, n_chi, n_n, prec, r_block=0):
+    """(chi0_omega, screen_W, sigma_diag) scratch bytes of the context arena."""
+    a, s, g = ct.c_size_t(0), ct.c_size_t(0), ct.c_size_t(0)
+    _check(lib().gw_workspace_size(ct.byref(grid), int(n_b), int(n_occ), int(n), int(n_chi), int(n_n), prec_of(prec),
+                                   int(r_block), ct.byref(a), ct.byref(s), ct.byref(g)))
+    return int(a.value), int(s.value), int(g.value)
 
 
 # ------------------------------------------------------------------ device calls
