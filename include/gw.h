@@ -228,7 +228,8 @@ gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t
  *   Sigma_nn(i omega_k) = sum_j C_kj Sigma^c(tau_j) + i sum_j S_kj Sigma^s(tau_j).
  * Thiele coefficients through z_k = i omega_k, evaluated at the real
  * frequencies w_real_h (measured from mu).
- * bands_h [n_n]; tau_h, omega_h [n]; C_h, S_h [n][n].
+ * bands_h [n_n]; tau_h, omega_h [n]; C_h, S_h [n][n].  psi (device, [n_b][N_r])
+ * must be 16-byte aligned (GW_ERR_ARG otherwise).
  * Outputs (host, FP64): sigma_tau_h [2][n_n][n] = (Su, So) (may be NULL);
  * sigma_iw_h [n_n][n] complex; sigma_real_h [n_n][n_real] complex (may be NULL).
  * Synchronous.  GW_ERR_NUMERIC if a Thiele denominator vanishes (|.| < 1e-300);

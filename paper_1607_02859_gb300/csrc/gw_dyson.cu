@@ -491,10 +491,18 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
                        p + (long)(k0 + kb) * n, -1.0f, true, 0, B)))
           return rc;
       }
-      // 3. P^H P (lower), one frequency per launch
-      for (int b = 0; b < B; ++b)
-        if ((rc = gemm(n, n, n, p + b * nn, true, true, p + b * nn, false, false, e + b * nn, 1.0f, false, 2, 1)))
+      // 3. P^H P (lower) in K blocks of kTB rows of P.  P is lower triangular,
+      //    so block [k1, k2) touches only the leading k2 x k2 part; going from
+      //    the last block (which writes the whole lower triangle) to the first,
+      //    each block is added to C by the epilogue in round-to-nearest FP32.
+      //    One accumulation over all N rows would take ~3N/8 truncating
+      //    tensor-core adds per element (5000 at N = 13824) and lose ~1e-4.
+      for (int k1 = (n - 1) / kTB * kTB; k1 >= 0; k1 -= kTB) {
+        const int k2 = std::min(n, k1 + kTB);
+        if ((rc = gemm(k2, k2, k2 - k1, p + (long)k1 * n, true, true, p + (long)k1 * n, false, false, e, 1.0f,
+                       k2 < n, 1, B)))
           return rc;
+      }
     }
   }
   assemble_kernel<T><<<gb, tb, 0, st>>>(e, nn, p, nn, n);
@@ -524,7 +532,7 @@ size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* n
   probe.take<char>(bsz * nn * es);
   probe.take<char>(bsz * nn * es);
   probe.take<double2>(4 * (size_t)n_chi);
-  if (tc) probe.take<char>(std::max(tc_gemm_scratch(n_chi, n_chi, n_chi, 1), tc_gemm_scratch(n_chi, n_chi, kTB, bsz)));
+  if (tc) probe.take<char>(tc_gemm_scratch(n_chi, n_chi, kTB, bsz));
   if (bsz_out) *bsz_out = bsz;
   if (nbatch_out) *nbatch_out = nbatch;
   return probe.off;
@@ -570,7 +578,7 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
   int bsz = 0, nbatch = 0;
   const size_t need = screen_scratch(n_chi, n_omega, prec, &bsz, &nbatch);
   const size_t tcs_bytes =
-      tc ? std::max(tc_gemm_scratch(n_chi, n_chi, n_chi, 1), tc_gemm_scratch(n_chi, n_chi, kTB, bsz)) : 0;
+      tc ? tc_gemm_scratch(n_chi, n_chi, kTB, bsz) : 0;
   if ((st = reserve(ctx, need))) return st;
   Carver cv(ctx->arena);
   double* dvh = cv.take<double>(n_chi);

@@ -131,6 +131,30 @@ __global__ void __launch_bounds__(256) col_line_kernel(const typename cpx<T>::t*
   }
 }
 
+// Weighted sums of the transforms in FP32.  The weights of the time/frequency
+// transforms reach |c_kj| ~ 10^2 with both signs; rounded to FP32 they alone
+// would perturb sum_j c_kj x_j by ~4e-7 relative.  The FP32 path keeps each
+// weight as an unevaluated pair hi + lo (hi = fl32(c), lo = fl32(c - hi)) and
+// accumulates c x as fma(hi, x, fma(lo, x, s)), which removes the weight
+// rounding for one extra FMA per term; the remaining FP32 accumulation error
+// is below the rounding already present in the x_j themselves.  FP64 keeps the
+// plain sum.
+template <typename T>
+struct WSum {
+  T s = 0;
+  __device__ void add(T wh, T, T x) { s += wh * x; }
+  __device__ T value() const { return s; }
+};
+template <>
+struct WSum<float> {
+  float s = 0.f;
+  __device__ void add(float wh, float wl, float x) { s = __fmaf_rn(wh, x, __fmaf_rn(wl, x, s)); }
+  __device__ float value() const { return s; }
+};
+// The weight arrays hold hi[n_k][n_j] and, for FP32, lo[n_k][n_j] right after.
+template <typename T>
+constexpr int kWParts = sizeof(T) == 4 ? 2 : 1;
+
 // Last column pass of the chi chain: i1 FFT (-i) of every tau slab, then
 // out[k][inv[pos]][c] = sum_j cw[k][j] * slab_j(pos, c)  (Eq. CTX with the
 // dV^2/Omega of Eq. FFTX2 folded into cw).  32 columns x 8 warps per CTA.
@@ -144,11 +168,12 @@ __global__ void __launch_bounds__(256) col_line_ct_kernel(const typename cpx<T>:
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);                       // [ntau][N1][32]
-  T* w = reinterpret_cast<T*>(s + (size_t)ntau * N1 * 32);      // [nw][ntau]
+  T* w = reinterpret_cast<T*>(s + (size_t)ntau * N1 * 32);      // [parts][nw][ntau]
+  const T* wl = w + (kWParts<T> - 1) * nw * ntau;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
   const int i23 = blockIdx.y;
-  for (int e = threadIdx.x; e < nw * ntau; e += blockDim.x) w[e] = cw[e];
+  for (int e = threadIdx.x; e < kWParts<T> * nw * ntau; e += blockDim.x) w[e] = cw[e];
   for (int j = warp; j < ntau; j += 8) {
     C x[N1];
     const C* src = slabs + (long)j * slab_stride;
@@ -165,14 +190,14 @@ __global__ void __launch_bounds__(256) col_line_ct_kernel(const typename cpx<T>:
     const int k = q / N1, i1 = q - k * N1;
     const int row = inv[(long)i1 * plane + i23];
     if (row < 0) continue;
-    T re = 0, im = 0;
+    WSum<T> re, im;
     for (int j = 0; j < ntau; ++j) {
       const C v = s[(j * N1 + i1) * 32 + lane];
-      const T wt = w[k * ntau + j];
-      re += wt * v.x;
-      im += wt * v.y;
+      const T wh = w[k * ntau + j], wlo = wl[k * ntau + j];
+      re.add(wh, wlo, v.x);
+      im.add(wh, wlo, v.y);
     }
-    out[(long)k * out_slice + (long)row * ldo + c] = mk(re, im);
+    out[(long)k * out_slice + (long)row * ldo + c] = mk(re.value(), im.value());
   }
 }
 
@@ -182,8 +207,9 @@ __global__ void __launch_bounds__(256) ct_kernel(const typename cpx<T>::t* __res
                                                  typename cpx<T>::t* __restrict__ out, size_t elems, int n,
                                                  const T* __restrict__ M) {
   using C = typename cpx<T>::t;
-  __shared__ T w[32 * 32];
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) w[e] = M[e];
+  __shared__ T w[kWParts<T> * 32 * 32];
+  const T* wl = w + (kWParts<T> - 1) * n * n;
+  for (int e = threadIdx.x; e < kWParts<T> * n * n; e += blockDim.x) w[e] = M[e];
   __syncthreads();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < elems; e += (size_t)gridDim.x * blockDim.x) {
     C x[32];
@@ -191,14 +217,14 @@ __global__ void __launch_bounds__(256) ct_kernel(const typename cpx<T>::t* __res
     for (int j = 0; j < 32; ++j)
       if (j < n) x[j] = in[(size_t)j * elems + e];
     for (int k = 0; k < n; ++k) {
-      T re = 0, im = 0;
+      WSum<T> re, im;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (j < n) {
-          re += w[k * n + j] * x[j].x;
-          im += w[k * n + j] * x[j].y;
+          re.add(w[k * n + j], wl[k * n + j], x[j].x);
+          im.add(w[k * n + j], wl[k * n + j], x[j].y);
         }
-      out[(size_t)k * elems + e] = ST ? mk(-im, re) : mk(re, im);
+      out[(size_t)k * elems + e] = ST ? mk(-im.value(), re.value()) : mk(re.value(), im.value());
     }
   }
 }
@@ -269,7 +295,7 @@ struct GridOps {
   }
   static gw_status line_ct(gw_ctx* ctx, const void* slabs, long slab_stride, long ld, int ntau, const void* cw, int nw,
                            void* out, long out_slice, long ldo, const int* inv, int ncols, cudaStream_t st) {
-    const size_t bytes = (size_t)ntau * N1 * 32 * sizeof(C) + (size_t)nw * ntau * sizeof(T);
+    const size_t bytes = (size_t)ntau * N1 * 32 * sizeof(C) + (size_t)kWParts<T> * nw * ntau * sizeof(T);
     auto kernel = col_line_ct_kernel<T, N1>;
     gw_status s = set_smem(ctx, kernel, bytes);
     if (s) return s;
@@ -351,6 +377,16 @@ gw_status launch_hadamard(gw_ctx* ctx, gw_prec prec, size_t count, const void* a
 
 // Upload a host array into arena memory (pageable copy; the host buffer may be
 // released on return).
+std::vector<float> split_weights(const double* w, int count, double fac) {
+  std::vector<float> out(2 * (size_t)count);
+  for (int e = 0; e < count; ++e) {
+    const double v = w[e] * fac;
+    out[e] = (float)v;
+    out[count + e] = (float)(v - (double)out[e]);
+  }
+  return out;
+}
+
 gw_status upload(gw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return GW_OK;
   return cuda_check(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload");
@@ -438,8 +474,8 @@ extern "C" gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double*
   if (is_fp64(prec)) {
     if ((st = upload(ctx, ctx->arena, M_h, sizeof(double) * n * n, s))) return st;
   } else {
-    std::vector<float> m(M_h, M_h + n * n);
-    if ((st = upload(ctx, ctx->arena, m.data(), sizeof(float) * n * n, s))) return st;
+    const std::vector<float> m = split_weights(M_h, n * n, 1.0);
+    if ((st = upload(ctx, ctx->arena, m.data(), sizeof(float) * 2 * n * n, s))) return st;
   }
   return launch_ct(ctx, prec, kind == GW_ST, n, ctx->arena, elems, in, out, s);
 }

@@ -21,6 +21,8 @@ gw_status launch_ct(gw_ctx* ctx, gw_prec prec, bool st_kind, int n, const void* 
 gw_status launch_hadamard(gw_ctx* ctx, gw_prec prec, size_t count, const void* a, const void* b, double scale,
                           void* out, cudaStream_t st);
 gw_status upload(gw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st);
+// FP32 weights of a transform as hi[count] then lo[count], hi + lo = fac * w to ~2^-48.
+std::vector<float> split_weights(const double* w, int count, double fac);
 gw_status index_maps(gw_ctx* ctx, const GridInfo& g, const int32_t* fft_index_h, int n_chi, std::vector<int>& map,
                      std::vector<int>& inv);
 

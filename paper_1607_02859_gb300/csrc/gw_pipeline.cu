@@ -76,9 +76,8 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
     for (auto& v : cw) v *= fac;
     if ((st = upload(ctx, dcw, cw.data(), sizeof(double) * n * n, s))) return st;
   } else {
-    std::vector<float> cw(n * n);
-    for (int e = 0; e < n * n; ++e) cw[e] = (float)(C_h[e] * fac);
-    if ((st = upload(ctx, dcw, cw.data(), sizeof(float) * n * n, s))) return st;
+    const std::vector<float> cw = split_weights(C_h, n * n, fac);
+    if ((st = upload(ctx, dcw, cw.data(), sizeof(float) * 2 * n * n, s))) return st;
   }
   for (int j = 0; j < n; ++j) {
     GreenScales gs = green_scales(eps_h, n_b, n_occ, mu, tau_h[j]);

@@ -23,45 +23,98 @@ namespace gw {
 
 constexpr int kSigBands = 8;   // bands accumulated per pass over a row
 
+constexpr int kSigThreads = 512;   // one CTA per row; its W~ row (up to 115 KB) leaves room for one CTA per SM
+
+// Two consecutive complex elements (16-byte aligned) in one 16-byte load for FP32.
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+  a = __ldg(p);
+  b = __ldg(p + 1);
+}
+
+// One row r per CTA: W~(r,G') is scattered into the FFT grid in shared memory
+// and transformed to W~(r,R'); then, streaming G_occ(r,.), G_unocc(r,.) and
+// psi_n(.) two R' at a time (16-byte loads, two pairs in flight per thread),
+// V_n = sum_R' G(r,R') W~(r,R') psi_n(R') for kSigBands bands per pass.
 template <typename T, int N1, int N2, int N3>
-__global__ void __launch_bounds__(256) sigma_row_kernel(
+__global__ void __launch_bounds__(kSigThreads) sigma_row_kernel(
     const typename cpx<T>::t* __restrict__ wrg, long ldw, const int* __restrict__ map, int n_chi,
     const typename cpx<T>::t* __restrict__ go, const typename cpx<T>::t* __restrict__ gu, long ldg,
     const typename cpx<T>::t* __restrict__ psi, const int* __restrict__ bands, int n_n, int r0, double coef,
     double* __restrict__ acc_u, double* __restrict__ acc_o, int acc_stride) {
   using C = typename cpx<T>::t;
   using L = RowLayout<N1, N2, N3>;
+  static_assert(N3 % 2 == 0 && L::NR % 2 == 0, "pairs along i3");
+  constexpr int NW = kSigThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  __shared__ T red[8][kSigBands * 4];
+  __shared__ T red[NW][kSigBands * 4];
   const long row = blockIdx.x;
   const int r = r0 + (int)row;
   for (int e = threadIdx.x; e < L::TOT; e += blockDim.x) s[e] = mk(T(0), T(0));
   __syncthreads();
   const C* src = wrg + (long)r * ldw;
-  for (int j = threadIdx.x; j < n_chi; j += blockDim.x) s[L::pos(map[j])] = src[j];
+  for (int j0 = threadIdx.x; j0 < n_chi; j0 += 4 * kSigThreads) {
+    C v[4];
+    int m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u * kSigThreads;
+      if (j < n_chi) {
+        v[u] = src[j];
+        m[u] = map[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (j0 + u * kSigThreads < n_chi) s[L::pos(m[u])] = v[u];
+  }
   __syncthreads();
   fft3_smem<N1, N2, N3, -1>(s);
   const C* pgo = go + row * ldg;
   const C* pgu = gu + row * ldg;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NP = L::NR / 2;
   for (int b0 = 0; b0 < n_n; b0 += kSigBands) {
     const int nb = min(kSigBands, n_n - b0);
+    const C* pb[kSigBands];
+#pragma unroll
+    for (int b = 0; b < kSigBands; ++b) pb[b] = psi + (long)bands[b0 + (b < nb ? b : 0)] * L::NR;
     T vo[kSigBands][2], vu[kSigBands][2];
 #pragma unroll
     for (int b = 0; b < kSigBands; ++b) vo[b][0] = vo[b][1] = vu[b][0] = vu[b][1] = T(0);
-    for (int rp = threadIdx.x; rp < L::NR; rp += blockDim.x) {
-      const C w = s[L::pos(rp)];
-      const C ho = cmul(pgo[rp], w);
-      const C hu = cmul(pgu[rp], w);
+    for (int q0 = threadIdx.x; q0 < NP; q0 += 2 * kSigThreads) {
+      C xo[2][2], xu[2][2];
 #pragma unroll
-      for (int b = 0; b < kSigBands; ++b) {
-        if (b < nb) {
-          const C p = psi[(long)bands[b0 + b] * L::NR + rp];
-          vo[b][0] += ho.x * p.x - ho.y * p.y;
-          vo[b][1] += ho.x * p.y + ho.y * p.x;
-          vu[b][0] += hu.x * p.x - hu.y * p.y;
-          vu[b][1] += hu.x * p.y + hu.y * p.x;
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + u * kSigThreads;
+        if (q < NP) {
+          ld_pair(pgo + 2 * q, xo[u][0], xo[u][1]);
+          ld_pair(pgu + 2 * q, xu[u][0], xu[u][1]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int q = q0 + u * kSigThreads;
+        if (q >= NP) continue;
+        const int p0 = L::pos(2 * q);            // 2q and 2q+1 share an i3 pencil
+        const C w0 = s[p0], w1 = s[p0 + 1];
+        const C ho0 = cmul(xo[u][0], w0), ho1 = cmul(xo[u][1], w1);
+        const C hu0 = cmul(xu[u][0], w0), hu1 = cmul(xu[u][1], w1);
+#pragma unroll
+        for (int b = 0; b < kSigBands; ++b) {
+          if (b < nb) {
+            C a0, a1;
+            ld_pair(pb[b] + 2 * q, a0, a1);
+            vo[b][0] += ho0.x * a0.x - ho0.y * a0.y + ho1.x * a1.x - ho1.y * a1.y;
+            vo[b][1] += ho0.x * a0.y + ho0.y * a0.x + ho1.x * a1.y + ho1.y * a1.x;
+            vu[b][0] += hu0.x * a0.x - hu0.y * a0.y + hu1.x * a1.x - hu1.y * a1.y;
+            vu[b][1] += hu0.x * a0.y + hu0.y * a0.x + hu1.x * a1.y + hu1.y * a1.x;
+          }
         }
       }
     }
@@ -86,7 +139,7 @@ __global__ void __launch_bounds__(256) sigma_row_kernel(
     if (threadIdx.x < nb) {
       const int b = threadIdx.x;
       double o_re = 0, o_im = 0, u_re = 0, u_im = 0;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      for (int w = 0; w < NW; ++w) {
         o_re += red[w][4 * b + 0];
         o_im += red[w][4 * b + 1];
         u_re += red[w][4 * b + 2];
@@ -187,7 +240,7 @@ struct SigmaOps {
       if (rc) return rc;
     }
     KTimer kt(ctx, KF_SIGMA_ROW, (double)n_rows * (n_chi + 2.0 * RowLayout<N1, N2, N3>::NR) * sizeof(C), st);
-    kernel<<<n_rows, 256, bytes, st>>>((const C*)wrg, ldw, map, n_chi, (const C*)go, (const C*)gu, ldg,
+    kernel<<<n_rows, kSigThreads, bytes, st>>>((const C*)wrg, ldw, map, n_chi, (const C*)go, (const C*)gu, ldg,
                                        (const C*)psi, bands, n_n, r0, coef, acc_u, acc_o, acc_stride);
     return launch_check(ctx, "sigma_row_kernel");
   }
@@ -246,6 +299,7 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   if (!psi || !w_tau || !bands_h || !tau_h || !omega_h || !C_h || !S_h || !sigma_iw_h)
     return fail(ctx, GW_ERR_ARG, "NULL pointer");
   if (n_b < 2 || n_b > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 2 <= n_b <= N_r");
+  if (reinterpret_cast<uintptr_t>(psi) % 16) return fail(ctx, GW_ERR_ARG, "psi must be 16-byte aligned");
   if ((st = check_energies(ctx, eps_h, n_b, n_occ, mu))) return st;
   if (n < 1 || n > kMaxN) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
   if (n_n < 1 || n_n > 1024) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_n <= 1024");

@@ -19,11 +19,12 @@
 // Tile: 128 rows r x 128 complex columns R' (MMA 128 x 256 x 16), K staged 32
 // real elements (64 B, SWIZZLE_64B) at a time through a 4-stage TMA/mbarrier
 // pipeline; the epilogue stages rows in shared memory and writes 128-byte row
-// segments.  G_occ and G_unocc accumulate in two 256-column halves of tensor
-// memory; the epilogue either writes both (gw_green_tau) or their product
+// segments.  G_unocc is summed blockwise through the two 256-column halves of
+// tensor memory into registers, G_occ accumulates last in one half; the
+// epilogue either writes both (gw_green_tau) or their product
 // chi = -2 G_occ conj(G_unocc) (gw_chi0_rtau_fused), so for chi neither G tile
 // ever reaches HBM.  Warp roles: 0 = TMA producer, 1 = MMA issuer (and tensor
-// memory owner), 2..5 = epilogue.  Every wait is bounded; on time-out the
+// memory owner), 2..9 = epilogue.  Every wait is bounded; on time-out the
 // kernel records it in the status word, drains its own copies and MMAs, frees
 // its tensor memory and returns.
 #include <cuda.h>
@@ -45,13 +46,16 @@ constexpr int BM = 128;                 // rows per tile
 constexpr int BNC = 128;                // complex columns per tile (MMA N = 256)
 constexpr int BK = 32;                  // real K per stage (one 64-byte swizzle row)
 constexpr int STAGES = 4;
+constexpr int CH = 4;                   // stages per accumulation block (128 real K)
+constexpr int EPI_WARPS = 8;            // two per tensor-memory lane quarter, one per column half
 constexpr int A_BYTES = BM * BK * 2;            // 8 KB
 constexpr int B_BYTES = 2 * BNC * BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int EPI_COLS = 16;                    // complex columns per epilogue round
-constexpr int EPI_BYTES = 4 * 32 * EPI_COLS * 8;
+constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_COLS * 8;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
-constexpr int THREADS = 192;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
 struct Params {
   int m_rows;             // valid output rows
@@ -68,6 +72,17 @@ struct Params {
   int* status;            // device: [0] time-out flag, [1] where
 };
 
+// Blocked accumulation.  The tensor cores add each MMA's products into the FP32
+// accumulator without rounding to nearest, so the relative error of a long
+// accumulation grows about linearly with the number of MMAs (3 per 16 real K
+// here): ~1e-5 for a thousand bands.  G_unocc is therefore summed in blocks of
+// CH stages: each block accumulates from zero in one of the two 256-column
+// halves of tensor memory while the epilogue warps add the other half's
+// finished block into FP32 registers (round to nearest), which keeps the
+// error at the level of one block.  G_occ (the short sum over the occupied
+// bands) follows as the last block and stays in tensor memory for the
+// epilogue.
+//
 // MODE 0: out0 = -2 G_occ conj(G_unocc);  MODE 1: out0 = G_occ, out1 = G_unocc.
 template <int MODE, uint32_t FMT>
 __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_constant__ CUtensorMap mA_hi,
@@ -76,10 +91,12 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap mB_lo, Params p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float2* epi = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);     // [4 warps][32 rows][16]
+  float2* epi = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);     // [8 warps][32 rows][16]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + EPI_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* tfull = empty + STAGES;      // [2] block finished in tensor-memory half b
+  uint64_t* tempty = tfull + 2;          // [2] half b drained by the epilogue
+  uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -87,11 +104,17 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
   const int m0 = blockIdx.y * BM;
   const int n0 = blockIdx.x * BNC;
   const int total = p.k_occ_steps + p.k_un_steps;
+  const int n_un_blocks = (p.k_un_steps + CH - 1) / CH;
+  const bool have_occ = p.k_occ_steps > 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -111,9 +134,18 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
     *abort_flag = 1;
     if (atomicCAS(p.status, 0, 1) == 0) p.status[1] = where;
   };
+  // bounded wait that also gives up once another role has aborted
+  auto wait_or_abort = [&](uint64_t* bar, uint32_t parity) -> bool {
+    const unsigned long long t0 = gtimer();
+    while (!mbar_test(bar, parity)) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kWaitNs) return false;
+    }
+    return true;
+  };
 
   if (warp == 0 && lane == 0) {
-    // ---------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------- TMA producer (unoccupied K first)
     int issued = 0;
     for (int it = 0; it < total && !*abort_flag; ++it) {
       const int s = it % STAGES;
@@ -122,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
         break;
       }
       uint8_t* st = smem + s * STAGE_BYTES;
-      const int x = it < p.k_occ_steps ? it * BK : p.k_un_x + (it - p.k_occ_steps) * BK;
+      const int x = it < p.k_un_steps ? p.k_un_x + it * BK : (it - p.k_un_steps) * BK;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mA_hi, &full[s], x, m0, 0);
       tma_load_3d(st + A_BYTES, &mA_lo, &full[s], x, m0, 0);
@@ -138,67 +170,118 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = make_idesc(FMT, 2 * BNC, BM);
+    const int n_blocks = n_un_blocks + (have_occ ? 1 : 0);
     int it = 0;
-    for (; it < total && !*abort_flag; ++it) {
-      const int s = it % STAGES;
-      if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
-        timed_out(2);
+    bool ok = true;
+    for (int c = 0; c < n_blocks && ok; ++c) {
+      const int b = c & 1, use = c >> 1;
+      const int first = c < n_un_blocks ? c * CH : p.k_un_steps;
+      const int last = c < n_un_blocks ? min(p.k_un_steps, (c + 1) * CH) : total;
+      if (use > 0 && !wait_or_abort(&tempty[b], (use - 1) & 1)) {
+        if (!*abort_flag) timed_out(4);
+        ok = false;
         break;
       }
       tc_fence_after();
-      const bool un = it >= p.k_occ_steps;
-      const int kin = un ? it - p.k_occ_steps : it;
-      const uint32_t d = tmem + (un ? 256u : 0u);
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const uint64_t ah = sw64_desc(st), al = sw64_desc(st + A_BYTES);
-      const uint64_t bh = sw64_desc(st + 2 * A_BYTES), bl = sw64_desc(st + 2 * A_BYTES + B_BYTES);
+      const uint32_t d = tmem + (uint32_t)(b * 256);
+      for (; it < last; ++it) {
+        const int s = it % STAGES;
+        if (!wait_or_abort(&full[s], (it / STAGES) & 1)) {
+          if (!*abort_flag) timed_out(2);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const uint64_t ah = sw64_desc(st), al = sw64_desc(st + A_BYTES);
+        const uint64_t bh = sw64_desc(st + 2 * A_BYTES), bl = sw64_desc(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t off = (uint64_t)(kk * 32) >> 4;    // 16 elements = 32 bytes along K
-        umma(d, ah + off, bh + off, idesc, (kin > 0 || kk > 0) ? 1u : 0u);
-        umma(d, ah + off, bl + off, idesc, 1u);
-        umma(d, al + off, bh + off, idesc, 1u);
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;    // 16 elements = 32 bytes along K
+          umma(d, ah + off, bh + off, idesc, (it > first || kk > 0) ? 1u : 0u);
+          umma(d, ah + off, bl + off, idesc, 1u);
+          umma(d, al + off, bh + off, idesc, 1u);
+        }
+        umma_commit(&empty[s]);
       }
-      umma_commit(&empty[s]);
+      if (ok) umma_commit(&tfull[b]);
     }
     umma_commit(done);     // arrives once every MMA issued above has completed
+    if (!mbar_wait(done, 0)) timed_out(5);
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
-    const bool ok = mbar_wait(done, 0);
-    if (!ok) timed_out(3);
-    tc_fence_after();
+    const int ew = warp - 2;
+    const int q = warp & 3;                       // tensor-memory lane quarter of this warp
+    const int h = ew >> 2;                        // column half: real columns h*128 .. h*128+127
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    float tot[128];                               // this thread's row of G_unocc, FP32 round-to-nearest sums
+#pragma unroll
+    for (int i = 0; i < 128; ++i) tot[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < n_un_blocks; ++c) {
+      const int b = c & 1;
+      const bool got = wait_or_abort(&tfull[b], (c >> 1) & 1);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0 && !*abort_flag) timed_out(3);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + lane_addr + (uint32_t)(b * 256 + h * 128);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        uint32_t x[16];
+        tmem_ld16(base + 16 * u, x);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tot[16 * u + i] += __uint_as_float(x[i]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+    const int bo = n_un_blocks & 1;
+    if (ok && have_occ) {
+      const bool got = wait_or_abort(&tfull[bo], (n_un_blocks >> 1) & 1);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0 && !*abort_flag) timed_out(3);
+        ok = false;
+      }
+      tc_fence_after();
+    }
     // tcgen05.ld is warp-collective: the whole warp takes the same branch
     if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
-      const int q = warp & 3;                       // tensor-memory lane quarter of this warp
       const int r0 = m0 + q * 32;                   // first output row of this warp
       const float sc = ldexpf(1.0f, -2 * (*p.dexp));
       const float ao = p.alpha_occ * sc, au = p.alpha_un * sc;
-      const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-      float2* stg = epi + q * 32 * EPI_COLS;
-#pragma unroll 1
-      for (int c = 0; c < 2 * BNC; c += 2 * EPI_COLS) {
-        uint32_t ro[2][16], ru[2][16];
+      float2* stg = epi + ew * 32 * EPI_COLS;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          tmem_ld16(tmem + lane_addr + c + 16 * u, ro[u]);
-          tmem_ld16(tmem + lane_addr + 256 + c + 16 * u, ru[u]);
-        }
-        tmem_wait_ld();
-        const int nc0 = n0 + c / 2;
-#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        const int nc0 = n0 + h * 64 + cc * 16;
+#pragma unroll
         for (int pass = 0; pass < (MODE == 0 ? 1 : 2); ++pass) {
           // row `lane` of the chunk to shared memory (rotated), then 128-byte row segments out
 #pragma unroll
-          for (int u = 0; u < 2; ++u)
+          for (int u = 0; u < 2; ++u) {
+            uint32_t ro[16];
+            const bool need_occ = MODE == 0 || pass == 0;
+            if (need_occ && have_occ) {
+              tmem_ld16(tmem + lane_addr + (uint32_t)(bo * 256 + h * 128 + 32 * cc + 16 * u), ro);
+              tmem_wait_ld();
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) ro[i] = 0u;
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const float gor = __uint_as_float(ro[u][2 * j]) * ao, goi = __uint_as_float(ro[u][2 * j + 1]) * ao;
-              const float gur = __uint_as_float(ru[u][2 * j]) * au, gui = __uint_as_float(ru[u][2 * j + 1]) * au;
+              const float gor = __uint_as_float(ro[2 * j]) * ao, goi = __uint_as_float(ro[2 * j + 1]) * ao;
+              const float gur = tot[32 * cc + 16 * u + 2 * j] * au, gui = tot[32 * cc + 16 * u + 2 * j + 1] * au;
               float2 v;
               if (MODE == 0) v = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
               else v = pass == 0 ? make_float2(gor, goi) : make_float2(gur, gui);
               stg[lane * EPI_COLS + ((u * 8 + j + lane) & (EPI_COLS - 1))] = v;
             }
+          }
           __syncwarp();
           float2* outp = (MODE == 0 || pass == 0) ? p.out0 : p.out1;
 #pragma unroll
