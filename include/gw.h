@@ -80,6 +80,12 @@ const char* gw_last_error(const gw_ctx* ctx);
 unsigned long long gw_ctx_launches(const gw_ctx* ctx);
 /* Current size of the context's device scratch arena in bytes. */
 size_t gw_ctx_scratch_bytes(const gw_ctx* ctx);
+/* Grow the scratch arena to at least `bytes` now (e.g. the largest
+ * gw_workspace_size of the problems a server will run), so that later calls
+ * do not reallocate it.  Growing frees and reallocates the arena, which
+ * synchronises the device; a smaller request does nothing.  GW_ERR_OOM if the
+ * allocation fails (the arena is then empty). */
+gw_status gw_ctx_reserve(gw_ctx* ctx, size_t bytes);
 /* Per-kernel timing for benchmarks.  While enabled, the library brackets every
  * launch of its main kernels with CUDA events on the launch stream and records,
  * per kernel family, the number of launches, their summed device time and their
@@ -216,6 +222,17 @@ gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double* M_h, size_
 gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h,
                       int n_omega, gw_prec prec, const void* chi_w, void* w_w,
                       double* resid_h, void* stream);
+/* gw_screen_W followed by refine_iters (0..8) FP64 refinement steps per
+ * frequency of X = eps~^{-1} - 1 before W~ is formed: with the residual
+ * R = chi~ - eps~ X = chi~ - X + chi~ X (chi~ = v^1/2 chi v^1/2), X <- X + (1 + X) R,
+ * which squares the relative error of X each step (Newton-Schulz for the
+ * inverse of eps~; the same solve of Eq. W_correlated).  Costs two N^3 FP64
+ * complex GEMMs per step and frequency and 64 n_chi^2 bytes more scratch; the
+ * result is then limited by the working precision of w_w.  refine_iters = 0 is
+ * gw_screen_W. */
+gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h,
+                             int n_omega, gw_prec prec, int refine_iters, const void* chi_w,
+                             void* w_w, double* resid_h, void* stream);
 
 /* Diagonal correlation self-energy (Eqs. Sigma_occ, Sigma_rr and the first term
  * of Sigma_occ_reduce; even/odd split Eqs. cos_sin_sigma_matrix1/2; CT+ST Eqs.

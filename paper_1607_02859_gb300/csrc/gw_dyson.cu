@@ -394,12 +394,90 @@ static gw_status residual_probe(gw_ctx* ctx, int n, const typename cpx<T>::t* ch
   return GW_OK;
 }
 
+// Refinement of X = eps~^{-1} - 1 in FP64 after the working-precision solve.
+// With chi~ = v^1/2 chi v^1/2 and eps~ = 1 - chi~, X = eps~^{-1} chi~ solves
+// eps~ X = chi~.  For an approximate X with error E, the residual
+//   R = chi~ - eps~ X = chi~ - X + chi~ X
+// and the update X <- X + (1 + X) R (the current 1 + X standing in for
+// eps~^{-1}) leave the error -E eps~ E: Newton-Schulz, quadratic convergence,
+// two N^3 FP64 GEMMs per step.
+template <typename T>
+__global__ void refine_expand_kernel(const typename cpx<T>::t* __restrict__ Xl, const typename cpx<T>::t* __restrict__ chi,
+                                     const double* __restrict__ vh, double2* __restrict__ X, double2* __restrict__ Ct,
+                                     int n) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (b >= n) return;
+  const long e = (long)a * n + b;
+  const auto x = b <= a ? Xl[e] : Xl[(long)b * n + a];
+  X[e] = b <= a ? make_double2(x.x, x.y) : make_double2(x.x, -x.y);
+  const auto c = chi[e];
+  const double sc = vh[a] * vh[b];
+  Ct[e] = make_double2(sc * c.x, sc * c.y);
+}
+
+__global__ void refine_resid_kernel(const double2* __restrict__ Ct, const double2* __restrict__ X, double2* R, long nn) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x)
+    R[e] = make_double2(Ct[e].x - X[e].x + R[e].x, Ct[e].y - X[e].y + R[e].y);
+}
+
+__global__ void refine_update_kernel(double2* X, const double2* __restrict__ R, const double2* __restrict__ XR, long nn) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x)
+    X[e] = make_double2(X[e].x + R[e].x + XR[e].x, X[e].y + R[e].y + XR[e].y);
+}
+
+// Lower triangle back in the working precision, Hermitian part of X.
+template <typename T>
+__global__ void refine_store_kernel(const double2* __restrict__ X, typename cpx<T>::t* __restrict__ Xl, int n) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (b > a || b >= n) return;
+  const double2 u = X[(long)a * n + b], w = X[(long)b * n + a];
+  Xl[(long)a * n + b] = mk(T(0.5 * (u.x + w.x)), T(0.5 * (u.y - w.y)));
+}
+
+template <typename T>
+static gw_status refine_one(gw_ctx* ctx, int n, const typename cpx<T>::t* chi, const double* dvh,
+                            typename cpx<T>::t* xl, double2* ws, int iters, cudaStream_t st) {
+  const long nn = (long)n * n;
+  double2* X = ws;
+  double2* Ct = ws + nn;
+  double2* R = ws + 2 * nn;
+  double2* XR = ws + 3 * nn;
+  const dim3 tb(128), gb((n + 127) / 128, n);
+  const int eb = (int)std::min<long>((nn + 255) / 256, (long)ctx->num_sms * 8);
+  gw_status rc;
+  refine_expand_kernel<T><<<gb, tb, 0, st>>>(xl, chi, dvh, X, Ct, n);
+  if ((rc = launch_check(ctx, "refine_expand_kernel"))) return rc;
+  for (int it = 0; it < iters; ++it) {
+    GemmArgs g{};
+    g.M = g.N = g.K = n;
+    g.alpha_re = 1.0;
+    g.lda = g.ldb = g.ldc = n;
+    g.A = Ct;                 // R = chi~ X
+    g.B = X;
+    g.C = R;
+    if ((rc = launch_gemm(ctx, GW_FP64, g, st))) return rc;
+    refine_resid_kernel<<<eb, 256, 0, st>>>(Ct, X, R, nn);
+    if ((rc = launch_check(ctx, "refine_resid_kernel"))) return rc;
+    g.A = X;                  // XR = X R
+    g.B = R;
+    g.C = XR;
+    if ((rc = launch_gemm(ctx, GW_FP64, g, st))) return rc;
+    refine_update_kernel<<<eb, 256, 0, st>>>(X, R, XR, nn);
+    if ((rc = launch_check(ctx, "refine_update_kernel"))) return rc;
+  }
+  refine_store_kernel<T><<<gb, tb, 0, st>>>(X, xl, n);
+  return launch_check(ctx, "refine_store_kernel");
+}
+
 // One batch of frequencies: chi[B][n][n] -> W[B][n][n] (may alias chi), with
 // work buffers E and P of the same shape.  tcs: tensor-core scratch (NULL for
 // the CUDA-core precisions).
 template <typename T>
 static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const void* chi, const double* dvh, void* E,
-                              void* Pm, void* W, double2* probe, double* resid_h, void* tcs, cudaStream_t st) {
+                              void* Pm, void* W, double2* probe, double* resid_h, void* tcs, int refine,
+                              double2* rws, cudaStream_t st) {
   using C = typename cpx<T>::t;
   gw_status rc;
   C* e = static_cast<C*>(E);
@@ -507,6 +585,10 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
   }
   assemble_kernel<T><<<gb, tb, 0, st>>>(e, nn, p, nn, n);
   if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
+  if (refine > 0)
+    for (int b = 0; b < B; ++b)
+      if ((rc = refine_one<T>(ctx, n, static_cast<const C*>(chi) + b * nn, dvh, e + b * nn, rws, refine, st)))
+        return rc;
   if (resid_h)
     for (int b = 0; b < B; ++b)
       if ((rc = residual_probe<T>(ctx, n, static_cast<const C*>(chi) + b * nn, dvh, e + b * nn, probe, resid_h + b,
@@ -518,7 +600,7 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
 
 // Frequencies per batch (the two work matrices of a batch within 64 GB) and
 // the scratch gw_screen_W needs.
-size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* nbatch_out) {
+size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* nbatch_out, bool refine) {
   const size_t es = csize(prec);
   const size_t nn = (size_t)n_chi * n_chi;
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
@@ -533,6 +615,7 @@ size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* n
   probe.take<char>(bsz * nn * es);
   probe.take<double2>(4 * (size_t)n_chi);
   if (tc) probe.take<char>(tc_gemm_scratch(n_chi, n_chi, kTB, bsz));
+  if (refine) probe.take<double2>(4 * nn);
   if (bsz_out) *bsz_out = bsz;
   if (nbatch_out) *nbatch_out = nbatch;
   return probe.off;
@@ -560,6 +643,12 @@ extern "C" gw_status gw_workspace_size(const gw_grid* grid, int n_b, int n_occ, 
 
 extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h, int n_omega,
                                  gw_prec prec, const void* chi_w, void* w_w, double* resid_h, void* stream) {
+  return gw_screen_W_refine(ctx, grid, n_chi, gvec_h, n_omega, prec, 0, chi_w, w_w, resid_h, stream);
+}
+
+extern "C" gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h,
+                                        int n_omega, gw_prec prec, int refine_iters, const void* chi_w, void* w_w,
+                                        double* resid_h, void* stream) {
   if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
   GridInfo g;
   gw_status st = grid_info(ctx, grid, &g);
@@ -569,6 +658,7 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
   if (n_omega < 0) return fail(ctx, GW_ERR_SHAPE, "n_omega < 0");
   if (n_omega == 0) return GW_OK;
   if (!gvec_h || !chi_w || !w_w) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  if (refine_iters < 0 || refine_iters > 8) return fail(ctx, GW_ERR_ARG, "need 0 <= refine_iters <= 8");
   cudaStream_t s = as_stream(stream);
   std::vector<double> vh(n_chi);
   if ((st = gw_coulomb_sqrt(grid, gvec_h, n_chi, vh.data()))) return fail(ctx, st, gw_last_error(nullptr));
@@ -576,7 +666,7 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
   const size_t nn = (size_t)n_chi * n_chi;
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
   int bsz = 0, nbatch = 0;
-  const size_t need = screen_scratch(n_chi, n_omega, prec, &bsz, &nbatch);
+  const size_t need = screen_scratch(n_chi, n_omega, prec, &bsz, &nbatch, refine_iters > 0);
   const size_t tcs_bytes =
       tc ? tc_gemm_scratch(n_chi, n_chi, kTB, bsz) : 0;
   if ((st = reserve(ctx, need))) return st;
@@ -586,6 +676,7 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
   void* M = cv.take<char>(bsz * nn * es);
   double2* pr = cv.take<double2>(4 * (size_t)n_chi);
   void* tcs = tc ? cv.take<char>(tcs_bytes) : nullptr;
+  double2* rws = refine_iters > 0 ? cv.take<double2>(4 * nn) : nullptr;
   if ((st = upload(ctx, dvh, vh.data(), sizeof(double) * n_chi, s))) return st;
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 8 * sizeof(int), s), "memset flag"))) return st;
   int first_bad = -1;
@@ -594,8 +685,9 @@ extern "C" gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, co
     const char* in = static_cast<const char*>(chi_w) + k0 * nn * es;
     char* out = static_cast<char*>(w_w) + k0 * nn * es;
     double* rk = resid_h ? resid_h + k0 : nullptr;
-    if (is_fp64(prec)) st = screen_batch<double>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, nullptr, s);
-    else st = screen_batch<float>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, tcs, s);
+    if (is_fp64(prec))
+      st = screen_batch<double>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, nullptr, refine_iters, rws, s);
+    else st = screen_batch<float>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, tcs, refine_iters, rws, s);
     if (st) return st;
     if (nbatch > 1 && first_bad < 0) {
       int f[3] = {0, 0, 0};

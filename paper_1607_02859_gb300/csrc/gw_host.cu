@@ -210,6 +210,11 @@ extern "C" const char* gw_last_error(const gw_ctx* ctx) {
 
 extern "C" unsigned long long gw_ctx_launches(const gw_ctx* ctx) { return ctx ? ctx->launches : 0ull; }
 extern "C" size_t gw_ctx_scratch_bytes(const gw_ctx* ctx) { return ctx ? ctx->arena_bytes : 0; }
+
+extern "C" gw_status gw_ctx_reserve(gw_ctx* ctx, size_t bytes) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  return reserve(ctx, bytes);
+}
 extern "C" int gw_version(void) { return 100; }
 
 // ---------------------------------------------------------------------- G set

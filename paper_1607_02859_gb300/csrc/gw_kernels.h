@@ -60,7 +60,7 @@ gw_status green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
 namespace gw {
 // scratch each composite call reserves in the context arena
 size_t chi0_omega_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, gw_prec prec, int rb);
-size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* nbatch_out);
+size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* nbatch_out, bool refine = false);
 size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec);
 gw_status upload_scales(gw_ctx* ctx, void* dst, const GreenScales& gs, gw_prec prec, cudaStream_t st);
 }  // namespace gw

@@ -23,10 +23,10 @@ STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "G
           5: "GW_ERR_NUMERIC", 6: "GW_ERR_TIMEOUT", 7: "GW_ERR_UNSUPPORTED"}
 
 # every symbol declared in include/gw.h
-EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes",
+EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes", "gw_ctx_reserve",
            "gw_ctx_set_timing", "gw_ctx_kernel_stats", "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
-           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size"]
+           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine"]
 
 
 class GwError(RuntimeError):
@@ -53,6 +53,7 @@ _SIGS = {
     "gw_last_error": (ct.c_char_p, [_P]),
     "gw_ctx_launches": (ct.c_ulonglong, [_P]),
     "gw_ctx_scratch_bytes": (ct.c_size_t, [_P]),
+    "gw_ctx_reserve": (ct.c_int, [_P, ct.c_size_t]),
     "gw_version": (_I, []),
     "gw_ctx_set_timing": (_I, [_P, _I]),
     "gw_ctx_kernel_stats": (_I, [_P, ct.c_char_p, ct.POINTER(ct.c_ulonglong), _DP, _DP, ct.POINTER(ct.c_int)]),
@@ -68,6 +69,7 @@ _SIGS = {
                                ct.POINTER(ct.c_size_t)]),
     "gw_tau_to_omega": (_I, [_P, _I, _I, _DP, ct.c_size_t, _I, _P, _P, _P]),
     "gw_screen_W": (_I, [_P, _G, _I, _IP, _I, _I, _P, _P, _DP, _P]),
+    "gw_screen_W_refine": (_I, [_P, _G, _I, _IP, _I, _I, _I, _P, _P, _DP, _P]),
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                            _DP, _DP, _DP, _I, _DP, _P]),
     "gw_chi0_omega": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
@@ -158,6 +160,10 @@ class Context:
     @property
     def scratch_bytes(self) -> int:
         return int(lib().gw_ctx_scratch_bytes(self.handle))
+
+    def reserve(self, nbytes: int):
+        """Grow the scratch arena to at least nbytes now (synchronises the device when it grows)."""
+        _check(lib().gw_ctx_reserve(self.handle, int(nbytes)), self)
 
     FAMILIES = ("green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft", "col_line_ct", "sigma_row")
 
@@ -282,13 +288,19 @@ def tau_to_omega(ctx, kind, M, inp, out, prec):
                                  _dev(out, "out", p), _stream()), ctx)
 
 
-def screen_W(ctx, grid, gvec, prec, chi_w, w_w, resid=True):
+def screen_W(ctx, grid, gvec, prec, chi_w, w_w, resid=True, refine=0):
+    """W~(i omega) from chi0(i omega); refine > 0 adds that many FP64 refinement
+    steps per frequency (gw_screen_W_refine).  Returns the residuals or None."""
     p = prec_of(prec)
     gv = _i32(gvec)
     n_omega = chi_w.shape[0]
     res = np.zeros(n_omega) if resid else None
-    _check(lib().gw_screen_W(ctx.handle, ct.byref(grid), len(gv), _ip(gv), n_omega, p, _dev(chi_w, "chi_w", p),
-                             _dev(w_w, "w_w", p), _dp(res), _stream()), ctx)
+    if refine:
+        _check(lib().gw_screen_W_refine(ctx.handle, ct.byref(grid), len(gv), _ip(gv), n_omega, p, int(refine),
+                                        _dev(chi_w, "chi_w", p), _dev(w_w, "w_w", p), _dp(res), _stream()), ctx)
+    else:
+        _check(lib().gw_screen_W(ctx.handle, ct.byref(grid), len(gv), _ip(gv), n_omega, p, _dev(chi_w, "chi_w", p),
+                                 _dev(w_w, "w_w", p), _dp(res), _stream()), ctx)
     return res
 
 

@@ -184,3 +184,21 @@ def tiny(seed=11, n=(6, 6, 6), a=(6.0, 6.5, 7.0), n_occ=4, n_unocc=20, n_tau=6, 
     return make_problem(n, a, n_occ, n_unocc, (-0.6, -0.05), (0.05, 2.0), 0.0, n_tau, seed,
                         n_bands_sigma=4, real=real, n_chi=n_chi, pin_edges=True,
                         name="tiny_%dx%dx%d" % n)
+
+
+def serve_mix(count=6, seed=40, n_chi_cap=1536):
+    """Systems of uneven sizes for the request server: grid n^3 with n in
+    {12, 16, 20} (cell a = n * 10.26 / 12), 128-512 complex bands (multiples of
+    64, one eighth occupied), 8, 12 or 16 tau points, the G set capped at
+    n_chi_cap, Sigma for 4 bands.  The si8 energy windows and gap."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([12, 16, 20]))
+        n_b = int(rng.choice(np.arange(128, 513, 64)))
+        n_occ = n_b // 8
+        n_tau = int(rng.choice([8, 12, 16]))
+        out.append(make_problem((n, n, n), n * 10.26 / 12, n_occ, n_b - n_occ, (-0.5, 0.0), (0.04, 4.0), 0.02,
+                                n_tau, seed + 1 + i, n_bands_sigma=4, n_chi=min(n ** 3, n_chi_cap),
+                                pin_edges=True, name="mix%d_%d^3_%db_%dt" % (i, n, n_b, n_tau)))
+    return out

@@ -138,6 +138,9 @@ class GpuSlot:
     def arena_bytes(self):
         return self.ctx.scratch_bytes
 
+    def reserve(self, nbytes):
+        self.ctx.reserve(nbytes)
+
     def close(self):
         self.ctx.close()
 
@@ -214,6 +217,17 @@ class Server:
     def held_bytes(self):
         """Device bytes held now: slot arenas, outputs in flight, resident inputs."""
         return sum(w.arena for w in self.workers) + self.inflight_bytes + sum(self.resident.values())
+
+    def prepare(self, systems):
+        """Size every idle slot's arena for the largest of `systems` up front,
+        as far as the budget allows, so that no arena grows (a device-wide
+        synchronisation) while requests are in flight."""
+        need = max(s.scratch_bytes() for s in systems)
+        with self.lock:
+            for w in self.workers:
+                if w.job is None and w.arena < need and self.held_bytes() - w.arena + need <= self.budget:
+                    w.slot.reserve(need)
+                    w.arena = max(need, w.slot.arena_bytes())
 
     def submit(self, system, kind):
         if kind not in ("chi0", "sigma"):
@@ -310,8 +324,27 @@ def poisson_run(server, systems, rate, n_requests, kinds=("chi0", "sigma"), seed
     return reqs
 
 
+def _burst(server, systems, picks):
+    """All requests at once: saturation throughput."""
+    reqs = [server.submit(systems[i], k) for (i, k) in picks]
+    server.drain()
+    return reqs
+
+
+def _warm(server, systems):
+    server.prepare(systems)
+    for s in systems:                       # one untimed request per system
+        server.submit(s, "sigma")
+    big = max(systems, key=lambda s: s.output_bytes("sigma"))
+    for _ in server.workers:                # and the largest outputs once on every slot's stream
+        server.submit(big, "sigma")
+    server.drain()
+    server.done.clear()
+    server.max_concurrent = 0
+
+
 def main(argv=None):
-    """Poisson serving run over a mix of systems; prints one JSON line."""
+    """Serving runs over a mix of systems; prints JSON lines."""
     import argparse
     import json
     from . import inputs
@@ -319,24 +352,67 @@ def main(argv=None):
     ap.add_argument("--prec", default="f16x3", choices=["fp64", "fp32", "f16x3", "bf16x3"])
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=150.0)
-    ap.add_argument("--rate", type=float, default=8.0, help="mean arrivals per second")
+    ap.add_argument("--rates", default="8", help="comma-separated mean arrival rates (req/s) for Poisson runs")
     ap.add_argument("--requests", type=int, default=48)
-    ap.add_argument("--systems", default="gamma_toy,mid", help="comma-separated workload names")
+    ap.add_argument("--systems", default="mix", help="'mix' or comma-separated workload names")
+    ap.add_argument("--mix-count", type=int, default=6)
+    ap.add_argument("--compare-fp64", type=int, default=0, metavar="N",
+                    help="also serve N burst requests through the plain FP64 path and compare Sigma")
     args = ap.parse_args(argv)
-    systems = [register(getattr(inputs, name)(), args.prec) for name in args.systems.split(",")]
-    server = Server(args.slots, int(args.budget_gb * (1 << 30)))
+    problems = (inputs.serve_mix(args.mix_count) if args.systems == "mix"
+                else [getattr(inputs, name)() for name in args.systems.split(",")])
+    systems = [register(p, args.prec) for p in problems]
+    names = [s.name for s in systems]
+    budget = int(args.budget_gb * (1 << 30))
+    server = Server(args.slots, budget)
+    rng = np.random.default_rng(7)
+    n_cmp = args.compare_fp64 or 16
+    picks = [(int(rng.integers(0, len(systems))), ("chi0", "sigma")[int(rng.integers(0, 2))]) for _ in range(n_cmp)]
     try:
-        for s in systems:                       # one untimed request per system sizes the arenas
-            server.submit(s, "sigma")
+        _warm(server, systems)
+        first = [server.submit(s, "sigma") for s in systems]
         server.drain()
+        mixed_sigma = {i: r.result["sigma_iw"] for i, r in enumerate(first) if not r.error}
         server.done.clear()
-        server.max_concurrent = 0
-        reqs = poisson_run(server, systems, args.rate, args.requests)
+        reqs = _burst(server, systems, picks)
         st = server.stats(reqs)
-        st.update({"errors": [r.error for r in reqs if r.error][:3], "prec": args.prec, "slots": args.slots,
-                   "rate": args.rate, "systems": [s.name for s in systems],
-                   "held_gb": server.held_bytes() / (1 << 30)})
-        print(json.dumps(st))
+        st.update({"run": "burst", "prec": args.prec, "slots": args.slots, "systems": names})
+        print(json.dumps(st), flush=True)
+        for rate in [float(x) for x in args.rates.split(",") if x]:
+            server.done.clear()
+            server.max_concurrent = 0
+            reqs = poisson_run(server, systems, rate, args.requests)
+            st = server.stats(reqs)
+            st.update({"run": "poisson", "rate": rate, "prec": args.prec, "slots": args.slots,
+                       "errors": [r.error for r in reqs if r.error][:3],
+                       "held_gb": server.held_bytes() / (1 << 30)})
+            print(json.dumps(st), flush=True)
+    finally:
+        server.close()
+    if not args.compare_fp64:
+        return
+    import torch
+    del systems
+    torch.cuda.empty_cache()
+    ref = [register(p, "fp64") for p in problems]
+    server = Server(args.slots, budget)
+    try:
+        _warm(server, ref)
+        reqs = _burst(server, ref, picks)
+        st = server.stats(reqs)
+        fp64_sigma = {}
+        for (i, k), r in zip(picks, reqs):
+            if k == "sigma" and not r.error:
+                fp64_sigma[i] = r.result["sigma_iw"]
+        for i, s in enumerate(ref):
+            if i not in fp64_sigma:
+                r = server.submit(s, "sigma")
+                server.drain()
+                fp64_sigma[i] = r.result["sigma_iw"]
+        dev = {names[i]: float(np.max(np.abs(mixed_sigma[i] - fp64_sigma[i])) / 3.674932e-5) for i in mixed_sigma}
+        st.update({"run": "burst", "prec": "fp64", "slots": args.slots,
+                   "sigma_max_dev_mev_%s_vs_fp64" % args.prec: dev})
+        print(json.dumps(st), flush=True)
     finally:
         server.close()
 

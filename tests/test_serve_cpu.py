@@ -43,6 +43,9 @@ class FakeSlot:
     def arena_bytes(self):
         return self.arena
 
+    def reserve(self, nbytes):
+        self.arena = max(self.arena, nbytes)
+
     def close(self):
         pass
 
@@ -210,3 +213,17 @@ def test_autotune_candidates_and_cache(tmp_path):
     autotune.store(p, {k: {"r_block": 512, "ms": {"512": 1.0}}})
     assert autotune.load(p)[k]["r_block"] == 512
     assert autotune.load(str(tmp_path / "none.json")) == {}
+
+
+def test_prepare_sizes_arenas_within_budget():
+    srv, log = make(3, 50 * GB)
+    try:
+        a = FakeSystem("a", 10 * GB, GB)
+        b = FakeSystem("b", 20 * GB, GB)
+        srv.prepare([a, b])
+        assert sorted(w.arena for w in srv.workers) == [0, 20 * GB, 20 * GB]   # a third would pass 50 GB
+        r = srv.submit(b, "chi0")
+        srv.drain(timeout=10)
+        assert r.error == "" and sorted(w.arena for w in srv.workers) == [0, 20 * GB, 20 * GB]
+    finally:
+        srv.close()
