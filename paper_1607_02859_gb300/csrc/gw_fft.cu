@@ -33,37 +33,88 @@ bool grid_supported(int a, int b, int c) {
 // MODE 0: x = scale * a * conj(b) (Eq. chi_rr), forward (+i), gather the G' set.
 // MODE 1: x = a, forward (+i), gather.            (Eq. FFTX1)
 // MODE 2: scatter a[j] to fft positions, backward (-i), times scale.   (Eq. FFTW, 2nd step)
-template <typename T, int N1, int N2, int N3, int MODE>
-__global__ void __launch_bounds__(256) row_fft_kernel(const typename cpx<T>::t* __restrict__ a,
-                                                      const typename cpx<T>::t* __restrict__ b, long lda,
-                                                      typename cpx<T>::t* __restrict__ out, long ldo,
-                                                      const int* __restrict__ map, int n_chi, T scale) {
+// VEC: rows 16-byte aligned with even lengths; contiguous rows move as pairs of
+// elements, four pairs in flight per thread.
+template <typename T, int N1, int N2, int N3, int MODE, int THREADS, bool VEC>
+__global__ void __launch_bounds__(THREADS) row_fft_kernel(const typename cpx<T>::t* __restrict__ a,
+                                                          const typename cpx<T>::t* __restrict__ b, long lda,
+                                                          typename cpx<T>::t* __restrict__ out, long ldo,
+                                                          const int* __restrict__ map, int n_chi, T scale) {
   using C = typename cpx<T>::t;
   using L = RowLayout<N1, N2, N3>;
+  constexpr int NP = L::NR / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const long row = blockIdx.x;
   if (MODE == 2) {
-    for (int e = threadIdx.x; e < L::TOT; e += blockDim.x) s[e] = mk(T(0), T(0));
+    for (int e = threadIdx.x; e < L::TOT; e += THREADS) s[e] = mk(T(0), T(0));
     __syncthreads();
     const C* src = a + row * lda;
-    for (int j = threadIdx.x; j < n_chi; j += blockDim.x) s[L::pos(map[j])] = src[j];
+    for (int j0 = threadIdx.x; j0 < n_chi; j0 += 4 * THREADS) {
+      C v[4];
+      int m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * THREADS;
+        if (j < n_chi) {
+          v[u] = src[j];
+          m[u] = map[j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u * THREADS < n_chi) s[L::pos(m[u])] = v[u];
+    }
   } else {
     const C* pa = a + row * lda;
     const C* pb = b + row * lda;
-    for (int r = threadIdx.x; r < L::NR; r += blockDim.x) {
-      C v = pa[r];
-      if (MODE == 0) v = cscale(cmulc(v, pb[r]), scale);
-      s[L::pos(r)] = v;
+    if (VEC) {
+      for (int q0 = threadIdx.x; q0 < NP; q0 += 4 * THREADS) {
+        C v[4][2], w[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * THREADS;
+          if (q < NP) {
+            ld_pair(pa + 2 * q, v[u][0], v[u][1]);
+            if (MODE == 0) ld_pair(pb + 2 * q, w[u][0], w[u][1]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * THREADS;
+          if (q >= NP) continue;
+          const int p = L::pos(2 * q);           // 2q and 2q+1 share an i3 pencil (N3 even)
+          s[p] = MODE == 0 ? cscale(cmulc(v[u][0], w[u][0]), scale) : v[u][0];
+          s[p + 1] = MODE == 0 ? cscale(cmulc(v[u][1], w[u][1]), scale) : v[u][1];
+        }
+      }
+    } else {
+      for (int r = threadIdx.x; r < L::NR; r += THREADS) {
+        C v = pa[r];
+        if (MODE == 0) v = cscale(cmulc(v, pb[r]), scale);
+        s[L::pos(r)] = v;
+      }
     }
   }
   __syncthreads();
   fft3_smem<N1, N2, N3, MODE == 2 ? -1 : +1>(s);
   C* dst = out + row * ldo;
   if (MODE == 2) {
-    for (int r = threadIdx.x; r < L::NR; r += blockDim.x) dst[r] = cscale(s[L::pos(r)], scale);
+    if (VEC) {
+      for (int q = threadIdx.x; q < NP; q += THREADS) {
+        const int p = L::pos(2 * q);
+        st_pair(dst + 2 * q, cscale(s[p], scale), cscale(s[p + 1], scale));
+      }
+    } else {
+      for (int r = threadIdx.x; r < L::NR; r += THREADS) dst[r] = cscale(s[L::pos(r)], scale);
+    }
   } else {
-    for (int j = threadIdx.x; j < n_chi; j += blockDim.x) dst[j] = s[L::pos(map[j])];
+    if (VEC) {
+      for (int q = threadIdx.x; q < n_chi / 2; q += THREADS)
+        st_pair(dst + 2 * q, s[L::pos(map[2 * q])], s[L::pos(map[2 * q + 1])]);
+    } else {
+      for (int j = threadIdx.x; j < n_chi; j += THREADS) dst[j] = s[L::pos(map[j])];
+    }
   }
 }
 
@@ -255,16 +306,25 @@ struct GridOps {
     const size_t bytes = RowLayout<N1, N2, N3>::TOT * sizeof(C);
     const double rd = mode == 0 ? 2.0 * RowLayout<N1, N2, N3>::NR : (mode == 1 ? RowLayout<N1, N2, N3>::NR : n_chi);
     const double wr = mode == 2 ? RowLayout<N1, N2, N3>::NR : n_chi;
-    auto go = [&](auto kernel) -> gw_status {
+    auto al = [](const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    const bool vec = al(a) && al(b) && al(out) && lda % 2 == 0 && ldo % 2 == 0 && n_chi % 2 == 0 && N3 % 2 == 0;
+    auto go = [&](auto kernel, int threads) -> gw_status {
       gw_status s = set_smem(ctx, kernel, bytes);
       if (s) return s;
       KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (rd + wr) * sizeof(C), st);
-      kernel<<<n_rows, 256, bytes, st>>>((const C*)a, (const C*)b, lda, (C*)out, ldo, map, n_chi, (T)scale);
+      kernel<<<n_rows, threads, bytes, st>>>((const C*)a, (const C*)b, lda, (C*)out, ldo, map, n_chi, (T)scale);
       return launch_check(ctx, "row_fft_kernel");
     };
-    if (mode == 0) return go(row_fft_kernel<T, N1, N2, N3, 0>);
-    if (mode == 1) return go(row_fft_kernel<T, N1, N2, N3, 1>);
-    return go(row_fft_kernel<T, N1, N2, N3, 2>);
+    constexpr bool big = N1 * N2 * N3 >= 4096;
+    constexpr int TH = big ? 512 : 256;
+#define GW_ROW_GO(M)                                                              \
+    if (mode == M) return vec ? go(row_fft_kernel<T, N1, N2, N3, M, TH, N3 % 2 == 0>, TH) \
+                              : go(row_fft_kernel<T, N1, N2, N3, M, TH, false>, TH);
+    GW_ROW_GO(0)
+    GW_ROW_GO(1)
+    GW_ROW_GO(2)
+#undef GW_ROW_GO
+    return fail(ctx, GW_ERR_ARG, "bad row transform mode");
   }
   static gw_status plane(gw_ctx* ctx, int dir, void* buf, long ld, int ncols, double scale, cudaStream_t st) {
     const size_t bytes = (size_t)N2 * N3 * kPlaneW * sizeof(C);

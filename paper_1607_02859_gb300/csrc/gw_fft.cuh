@@ -20,6 +20,24 @@ struct RowLayout {
   }
 };
 
+// Two consecutive complex elements in one 16-byte access (FP32), two for FP64.
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+  a = __ldg(p);
+  b = __ldg(p + 1);
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
+  p[0] = a;
+  p[1] = b;
+}
+
 template <int N, int DIR, typename C, typename BaseF>
 __device__ __forceinline__ void pencil_pass(C* s, int count, int stride, BaseF base) {
   for (int p = threadIdx.x; p < count; p += blockDim.x) {

@@ -3,9 +3,9 @@
 // For each tau_j:
 //   W~(G,G',tau_j) -> W~(r,G')  (i1 pass gathering the G rows, then (i2,i3)
 //                                planes; first step of Eq. FFTW)
-//   per r-block: G_occ / G_unocc rows recomputed (Eqs. Green_occ/unocc), and
-//   one CTA per row r forms W~(r,R') in shared memory (second step of Eq. FFTW)
-//   and contracts (first term of Eq. Sigma_occ_reduce)
+//   per r-block: G_occ / G_unocc rows recomputed (Eqs. Green_occ/unocc),
+//   W~(r,R') by the row transform (second step of Eq. FFTW), and the
+//   contraction (first term of Eq. Sigma_occ_reduce)
 //      V_n(r) = sum_R' G(r,R') W~(r,R') psi_n(R'),
 //      Sigma_nn += -/+ dV^2 Re( psi_n^*(r) V_n(r) )
 //   with FP64 atomics into Sigma_unocc_nn(tau_j), Sigma_occ_nn(-tau_j).
@@ -14,6 +14,7 @@
 // Thiele continued fraction (Eqs. pade1, pade2).
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "gw_fft.cuh"
 #include "gw_kernels.h"
@@ -23,137 +24,128 @@ namespace gw {
 
 constexpr int kSigBands = 8;   // bands accumulated per pass over a row
 
-constexpr int kSigThreads = 512;   // one CTA per row; its W~ row (up to 115 KB) leaves room for one CTA per SM
+// Sigma contraction for a block of rows r (first term of Eq. Sigma_occ_reduce):
+//   V_n(r) = sum_R' G(r,R') W~(r,R') psi_n(R')   for G_occ and G_unocc,
+//   Sigma_occ_nn += -coef Re(conj(psi_n(r)) V_n^occ),  Sigma_unocc_nn += coef Re(...)
+// with W~(r,R') already in real space.  One row per warp, kSigRows rows per
+// CTA; R' runs in chunks whose psi_n values are copied asynchronously
+// (cp.async, double-buffered) into shared memory once for all the CTA's rows.
+// Lanes take pairs of consecutive R' (16-byte loads), four pairs of each of the
+// three streams in flight.
+constexpr int kSigRows = 8;
+constexpr int kSigThreads = 32 * kSigRows;
+constexpr int kSigUnroll = 4;
 
-// Two consecutive complex elements (16-byte aligned) in one 16-byte load for FP32.
-__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-  a = make_float2(v.x, v.y);
-  b = make_float2(v.z, v.w);
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
-__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
-  a = __ldg(p);
-  b = __ldg(p + 1);
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// One row r per CTA: W~(r,G') is scattered into the FFT grid in shared memory
-// and transformed to W~(r,R'); then, streaming G_occ(r,.), G_unocc(r,.) and
-// psi_n(.) two R' at a time (16-byte loads, two pairs in flight per thread),
-// V_n = sum_R' G(r,R') W~(r,R') psi_n(R') for kSigBands bands per pass.
-template <typename T, int N1, int N2, int N3>
-__global__ void __launch_bounds__(kSigThreads) sigma_row_kernel(
-    const typename cpx<T>::t* __restrict__ wrg, long ldw, const int* __restrict__ map, int n_chi,
-    const typename cpx<T>::t* __restrict__ go, const typename cpx<T>::t* __restrict__ gu, long ldg,
+template <typename T>
+__global__ void __launch_bounds__(kSigThreads) sigma_contract_kernel(
+    const typename cpx<T>::t* __restrict__ wrr, const typename cpx<T>::t* __restrict__ go,
+    const typename cpx<T>::t* __restrict__ gu, long ld, int nr, int rows,
     const typename cpx<T>::t* __restrict__ psi, const int* __restrict__ bands, int n_n, int r0, double coef,
     double* __restrict__ acc_u, double* __restrict__ acc_o, int acc_stride) {
   using C = typename cpx<T>::t;
-  using L = RowLayout<N1, N2, N3>;
-  static_assert(N3 % 2 == 0 && L::NR % 2 == 0, "pairs along i3");
-  constexpr int NW = kSigThreads / 32;
+  constexpr int CHUNK = sizeof(T) == 4 ? 512 : 256;          // R' per chunk: 32 KB of psi per buffer
+  constexpr int PAIRS = CHUNK / 2;
+  constexpr int EPP = sizeof(C) == 8 ? 2 : 1;                 // elements per 16-byte copy
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* s = reinterpret_cast<C*>(smem_raw);
-  __shared__ T red[NW][kSigBands * 4];
-  const long row = blockIdx.x;
-  const int r = r0 + (int)row;
-  for (int e = threadIdx.x; e < L::TOT; e += blockDim.x) s[e] = mk(T(0), T(0));
-  __syncthreads();
-  const C* src = wrg + (long)r * ldw;
-  for (int j0 = threadIdx.x; j0 < n_chi; j0 += 4 * kSigThreads) {
-    C v[4];
-    int m[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = j0 + u * kSigThreads;
-      if (j < n_chi) {
-        v[u] = src[j];
-        m[u] = map[j];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (j0 + u * kSigThreads < n_chi) s[L::pos(m[u])] = v[u];
-  }
-  __syncthreads();
-  fft3_smem<N1, N2, N3, -1>(s);
-  const C* pgo = go + row * ldg;
-  const C* pgu = gu + row * ldg;
+  C* sp = reinterpret_cast<C*>(smem_raw);                      // [2][kSigBands][CHUNK]
+  __shared__ double red[kSigRows][kSigBands][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NP = L::NR / 2;
+  const int rl = warp, r = blockIdx.x * kSigRows + rl;
+  const bool active = r < rows;
+  const long off = (long)r * ld;
+  const int nchunks = (nr + CHUNK - 1) / CHUNK;
   for (int b0 = 0; b0 < n_n; b0 += kSigBands) {
     const int nb = min(kSigBands, n_n - b0);
-    const C* pb[kSigBands];
-#pragma unroll
-    for (int b = 0; b < kSigBands; ++b) pb[b] = psi + (long)bands[b0 + (b < nb ? b : 0)] * L::NR;
+    auto stage = [&](int buf, int k0) {
+      const int kn = min(CHUNK, nr - k0);
+      C* dst = sp + buf * kSigBands * CHUNK;
+      for (int e = threadIdx.x; e < kSigBands * CHUNK / EPP; e += kSigThreads) {
+        const int b = e / (CHUNK / EPP), k = (e - b * (CHUNK / EPP)) * EPP;
+        const bool ok = b < nb && k < kn;
+        cp_async16(dst + b * CHUNK + k, ok ? psi + (long)bands[b0 + b] * nr + k0 + k : psi, ok);
+      }
+    };
     T vo[kSigBands][2], vu[kSigBands][2];
 #pragma unroll
     for (int b = 0; b < kSigBands; ++b) vo[b][0] = vo[b][1] = vu[b][0] = vu[b][1] = T(0);
-    for (int q0 = threadIdx.x; q0 < NP; q0 += 2 * kSigThreads) {
-      C xo[2][2], xu[2][2];
+    __syncthreads();                       // the previous band pass is done with both buffers
+    stage(0, 0);
+    cp_async_commit();
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + 1 < nchunks) stage((c + 1) & 1, (c + 1) * CHUNK);
+      cp_async_commit();
+      cp_async_wait1();
+      __syncthreads();
+      const C* ps = sp + (c & 1) * kSigBands * CHUNK;
+      const int k0 = c * CHUNK, kp = min(CHUNK, nr - k0) / 2;
+      if (active) {
+        for (int q0 = lane; q0 < PAIRS; q0 += 32 * kSigUnroll) {
+          C o[kSigUnroll][2], u[kSigUnroll][2], w[kSigUnroll][2];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int q = q0 + u * kSigThreads;
-        if (q < NP) {
-          ld_pair(pgo + 2 * q, xo[u][0], xo[u][1]);
-          ld_pair(pgu + 2 * q, xu[u][0], xu[u][1]);
-        }
-      }
+          for (int v = 0; v < kSigUnroll; ++v) {
+            const int q = q0 + 32 * v;
+            if (q < kp) {
+              ld_pair(go + off + k0 + 2 * q, o[v][0], o[v][1]);
+              ld_pair(gu + off + k0 + 2 * q, u[v][0], u[v][1]);
+              ld_pair(wrr + off + k0 + 2 * q, w[v][0], w[v][1]);
+            }
+          }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int q = q0 + u * kSigThreads;
-        if (q >= NP) continue;
-        const int p0 = L::pos(2 * q);            // 2q and 2q+1 share an i3 pencil
-        const C w0 = s[p0], w1 = s[p0 + 1];
-        const C ho0 = cmul(xo[u][0], w0), ho1 = cmul(xo[u][1], w1);
-        const C hu0 = cmul(xu[u][0], w0), hu1 = cmul(xu[u][1], w1);
+          for (int v = 0; v < kSigUnroll; ++v) {
+            const int q = q0 + 32 * v;
+            if (q >= kp) continue;
+            const C ho0 = cmul(o[v][0], w[v][0]), ho1 = cmul(o[v][1], w[v][1]);
+            const C hu0 = cmul(u[v][0], w[v][0]), hu1 = cmul(u[v][1], w[v][1]);
 #pragma unroll
-        for (int b = 0; b < kSigBands; ++b) {
-          if (b < nb) {
-            C a0, a1;
-            ld_pair(pb[b] + 2 * q, a0, a1);
-            vo[b][0] += ho0.x * a0.x - ho0.y * a0.y + ho1.x * a1.x - ho1.y * a1.y;
-            vo[b][1] += ho0.x * a0.y + ho0.y * a0.x + ho1.x * a1.y + ho1.y * a1.x;
-            vu[b][0] += hu0.x * a0.x - hu0.y * a0.y + hu1.x * a1.x - hu1.y * a1.y;
-            vu[b][1] += hu0.x * a0.y + hu0.y * a0.x + hu1.x * a1.y + hu1.y * a1.x;
+            for (int b = 0; b < kSigBands; ++b) {
+              const C a0 = ps[b * CHUNK + 2 * q], a1 = ps[b * CHUNK + 2 * q + 1];
+              vo[b][0] += ho0.x * a0.x - ho0.y * a0.y + ho1.x * a1.x - ho1.y * a1.y;
+              vo[b][1] += ho0.x * a0.y + ho0.y * a0.x + ho1.x * a1.y + ho1.y * a1.x;
+              vu[b][0] += hu0.x * a0.x - hu0.y * a0.y + hu1.x * a1.x - hu1.y * a1.y;
+              vu[b][1] += hu0.x * a0.y + hu0.y * a0.x + hu1.x * a1.y + hu1.y * a1.x;
+            }
           }
         }
       }
+      __syncthreads();                     // buffer c & 1 is staged again at chunk c + 2
     }
+    // warp sums, then Re(conj(psi_n(r)) V_n), then one atomic per band and CTA
 #pragma unroll
-    for (int b = 0; b < kSigBands; ++b)
+    for (int b = 0; b < kSigBands; ++b) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          vo[b][q] += __shfl_xor_sync(0xffffffffu, vo[b][q], off);
-          vu[b][q] += __shfl_xor_sync(0xffffffffu, vu[b][q], off);
+      for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        vo[b][0] += __shfl_xor_sync(0xffffffffu, vo[b][0], o2);
+        vo[b][1] += __shfl_xor_sync(0xffffffffu, vo[b][1], o2);
+        vu[b][0] += __shfl_xor_sync(0xffffffffu, vu[b][0], o2);
+        vu[b][1] += __shfl_xor_sync(0xffffffffu, vu[b][1], o2);
+      }
+      if (lane == b) {
+        double so = 0, su = 0;
+        if (b < nb && active) {
+          const C pn = psi[(long)bands[b0 + b] * nr + r0 + r];
+          so = -coef * ((double)pn.x * vo[b][0] + (double)pn.y * vo[b][1]);
+          su = coef * ((double)pn.x * vu[b][0] + (double)pn.y * vu[b][1]);
         }
-    if (lane == 0)
-#pragma unroll
-      for (int b = 0; b < kSigBands; ++b) {
-        red[warp][4 * b + 0] = vo[b][0];
-        red[warp][4 * b + 1] = vo[b][1];
-        red[warp][4 * b + 2] = vu[b][0];
-        red[warp][4 * b + 3] = vu[b][1];
+        red[rl][b][0] = so;
+        red[rl][b][1] = su;
       }
-    __syncthreads();
-    if (threadIdx.x < nb) {
-      const int b = threadIdx.x;
-      double o_re = 0, o_im = 0, u_re = 0, u_im = 0;
-      for (int w = 0; w < NW; ++w) {
-        o_re += red[w][4 * b + 0];
-        o_im += red[w][4 * b + 1];
-        u_re += red[w][4 * b + 2];
-        u_im += red[w][4 * b + 3];
-      }
-      const C pn = psi[(long)bands[b0 + b] * L::NR + r];
-      // Re(conj(pn) * V)
-      const double so = -coef * ((double)pn.x * o_re + (double)pn.y * o_im);
-      const double su = coef * ((double)pn.x * u_re + (double)pn.y * u_im);
-      atomicAdd(acc_o + (long)(b0 + b) * acc_stride, so);
-      atomicAdd(acc_u + (long)(b0 + b) * acc_stride, su);
     }
     __syncthreads();
+    if (threadIdx.x < 2 * nb) {
+      const int b = threadIdx.x >> 1, which = threadIdx.x & 1;
+      double t = 0;
+      for (int i = 0; i < kSigRows; ++i) t += red[i][b][which];
+      atomicAdd((which ? acc_u : acc_o) + (long)(b0 + b) * acc_stride, t);
+    }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
@@ -225,40 +217,24 @@ __global__ void sigma_finish_kernel(const double* __restrict__ acc_u, const doub
   status[b] = bad;
 }
 
-template <typename T, int N1, int N2, int N3>
-struct SigmaOps {
-  static gw_status row(gw_ctx* ctx, const void* wrg, long ldw, const int* map, int n_chi, const void* go,
-                       const void* gu, long ldg, const void* psi, const int* bands, int n_n, int r0, int n_rows,
-                       double coef, double* acc_u, double* acc_o, int acc_stride, cudaStream_t st) {
-    using C = typename cpx<T>::t;
-    const size_t bytes = RowLayout<N1, N2, N3>::TOT * sizeof(C);
-    auto kernel = sigma_row_kernel<T, N1, N2, N3>;
-    if (bytes > 200 * 1024) return fail(ctx, GW_ERR_UNSUPPORTED, "grid row too large for shared memory");
-    if (bytes > 48 * 1024) {
-      gw_status rc = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
-                                "cudaFuncSetAttribute");
-      if (rc) return rc;
-    }
-    KTimer kt(ctx, KF_SIGMA_ROW, (double)n_rows * (n_chi + 2.0 * RowLayout<N1, N2, N3>::NR) * sizeof(C), st);
-    kernel<<<n_rows, kSigThreads, bytes, st>>>((const C*)wrg, ldw, map, n_chi, (const C*)go, (const C*)gu, ldg,
-                                       (const C*)psi, bands, n_n, r0, coef, acc_u, acc_o, acc_stride);
-    return launch_check(ctx, "sigma_row_kernel");
-  }
-};
-
-static gw_status launch_sigma_rows(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* wrg, long ldw,
-                                   const int* map, int n_chi, const void* go, const void* gu, long ldg,
-                                   const void* psi, const int* bands, int n_n, int r0, int n_rows, double coef,
-                                   double* acc_u, double* acc_o, int acc_stride, cudaStream_t st) {
-#define X(a, b, c)                                                                                               \
-  if (g.n1 == a && g.n2 == b && g.n3 == c)                                                                       \
-    return is_fp64(prec) ? SigmaOps<double, a, b, c>::row(ctx, wrg, ldw, map, n_chi, go, gu, ldg, psi, bands,   \
-                                                          n_n, r0, n_rows, coef, acc_u, acc_o, acc_stride, st) \
-                         : SigmaOps<float, a, b, c>::row(ctx, wrg, ldw, map, n_chi, go, gu, ldg, psi, bands,    \
-                                                         n_n, r0, n_rows, coef, acc_u, acc_o, acc_stride, st);
-  GW_GRIDS(X)
-#undef X
-  return fail(ctx, GW_ERR_UNSUPPORTED, "no kernels compiled for this grid");
+static gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wrr, const void* go, const void* gu,
+                                       long ld, int nr, int rows, const void* psi, const int* bands, int n_n, int r0,
+                                       double coef, double* acc_u, double* acc_o, int acc_stride, cudaStream_t st) {
+  if (rows <= 0) return GW_OK;
+  const dim3 grid((rows + kSigRows - 1) / kSigRows);
+  auto go_ = [&](auto kernel, size_t esz, int chunk, auto* tag) -> gw_status {
+    using C = std::remove_pointer_t<decltype(tag)>;
+    const size_t bytes = (size_t)kSigBands * chunk * esz;
+    gw_status rc = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+                              "cudaFuncSetAttribute");
+    if (rc) return rc;
+    KTimer kt(ctx, KF_SIGMA, 3.0 * rows * (double)nr * esz, st);
+    kernel<<<grid, kSigThreads, bytes, st>>>((const C*)wrr, (const C*)go, (const C*)gu, ld, nr, rows, (const C*)psi,
+                                             bands, n_n, r0, coef, acc_u, acc_o, acc_stride);
+    return launch_check(ctx, "sigma_contract_kernel");
+  };
+  if (is_fp64(prec)) return go_(sigma_contract_kernel<double>, sizeof(double2), 2 * 256, (double2*)nullptr);
+  return go_(sigma_contract_kernel<float>, sizeof(float2), 2 * 512, (float2*)nullptr);
 }
 
 size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec) {
@@ -274,6 +250,7 @@ size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, in
   probe.take<double2>((size_t)n_n * n + (size_t)n_n * std::max(n_real, 1));
   probe.take<int>(n_n);
   probe.take<char>((size_t)g.nr * n_chi * es);
+  probe.take<char>((size_t)rb * g.nr * es);
   probe.take<char>((size_t)rb * g.nr * es);
   probe.take<char>((size_t)rb * g.nr * es);
   if (prec == GW_F16X3 || prec == GW_BF16X3) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
@@ -331,6 +308,7 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   char* wrg = cv.take<char>((size_t)g.nr * n_chi * es);
   char* gob = cv.take<char>((size_t)rb * g.nr * es);
   char* gub = cv.take<char>((size_t)rb * g.nr * es);
+  char* wrr = cv.take<char>((size_t)rb * g.nr * es);
   void* tcs = tc ? cv.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false)) : nullptr;
   if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
   if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
@@ -362,8 +340,12 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
       }
       else st = green_rows(ctx, g, n_b, n_occ, psi, dscale + (size_t)j * n_b * 8, scales[j], r0, rows, prec, gob, gub, s);
       if (st) return st;
-      if ((st = launch_sigma_rows(ctx, g, prec, wrg, n_chi, dmap, n_chi, gob, gub, g.nr, psi, dbands, n_n, r0, rows,
-                                  coef, acc_u + j, acc_o + j, n, s)))
+      // W~(r,R') of the block (second step of Eq. FFTW), then the contraction
+      if ((st = launch_row_fft(ctx, g, prec, 2, wrg + (size_t)r0 * n_chi * es, nullptr, n_chi, wrr, g.nr, dmap, n_chi,
+                               rows, 1.0, s)))
+        return st;
+      if ((st = launch_sigma_contract(ctx, prec, wrr, gob, gub, g.nr, g.nr, rows, psi, dbands, n_n, r0, coef,
+                                      acc_u + j, acc_o + j, n, s)))
         return st;
     }
   }
