@@ -92,8 +92,9 @@ gw_status gw_ctx_reserve(gw_ctx* ctx, size_t bytes);
  * summed algorithmic work (flops of the method for the contractions, bytes of
  * the minimal HBM traffic for the transforms).  Enabling or disabling clears
  * the totals.  Families: "green_tc", "cgemm_tc", "cgemm_simt", "row_fft",
- * "col_fft", "col_line_ct", "sigma_contract".  gw_ctx_kernel_stats synchronises on
- * the recorded events; any output pointer may be NULL. */
+ * "col_fft", "col_line_ct", "sigma_contract", "ct" (the standalone transform
+ * over tau/omega).  gw_ctx_kernel_stats synchronises on the recorded events;
+ * any output pointer may be NULL. */
 gw_status gw_ctx_set_timing(gw_ctx* ctx, int enabled);
 gw_status gw_ctx_kernel_stats(gw_ctx* ctx, const char* family, unsigned long long* launches,
                               double* ms, double* work, int* work_is_bytes);

@@ -15,6 +15,7 @@
 //    chain also applies the cosine transform over all tau (Eq. CTX) before
 //    anything is written, saving a full read+write of chi(G,G',tau).
 #include <mutex>
+#include <type_traits>
 
 #include "gw_common.cuh"
 #include "gw_kernels.h"
@@ -252,6 +253,85 @@ __global__ void __launch_bounds__(256) col_line_ct_kernel(const typename cpx<T>:
   }
 }
 
+// Same pass with a compile-time count of tau points (FP32): each lane keeps the
+// NT values of its column and one i1 in registers and the weights come from a
+// kernel-parameter block (constant bank), so the transform costs one
+// shared-memory read per input instead of three per multiply-add.
+template <int NT>
+struct CtWeights {
+  float hi[NT * NT];
+  float lo[NT * NT];
+};
+
+template <int N1, int NT>
+__global__ void __launch_bounds__(256, 2) col_line_ct_reg_kernel(const float2* __restrict__ slabs, long slab_stride,
+                                                              long ld, const __grid_constant__ CtWeights<NT> cw,
+                                                              float2* __restrict__ out, long out_slice, long ldo,
+                                                              const int* __restrict__ inv, int plane, int ncols) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* s = reinterpret_cast<float2*>(smem_raw);             // [NT][N1][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const int i23 = blockIdx.y;
+  for (int j = warp; j < NT; j += 8) {
+    float2 x[N1];
+    const float2* src = slabs + (long)j * slab_stride;
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1)
+      x[i1] = c < ncols ? src[((long)i1 * plane + i23) * ld + c] : make_float2(0.f, 0.f);
+    RegFFT<N1, -1>::run(x);
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) s[(j * N1 + i1) * 32 + lane] = x[i1];
+  }
+  __syncthreads();
+  if (c >= ncols) return;
+  for (int i1 = warp; i1 < N1; i1 += 8) {
+    const int row = inv[(long)i1 * plane + i23];
+    if (row < 0) continue;
+    float2 x[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) x[j] = s[(j * N1 + i1) * 32 + lane];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      WSum<float> re, im;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        re.add(cw.hi[k * NT + j], cw.lo[k * NT + j], x[j].x);
+        im.add(cw.hi[k * NT + j], cw.lo[k * NT + j], x[j].y);
+      }
+      out[(long)k * out_slice + (long)row * ldo + c] = make_float2(re.value(), im.value());
+    }
+  }
+}
+
+// Same map with a compile-time size (FP32, weights in a kernel-parameter
+// block): each thread takes two consecutive elements (16-byte loads and
+// stores) of all n slices in registers.
+template <int NT, bool ST>
+__global__ void __launch_bounds__(256) ct_reg_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                     size_t pairs, size_t elems, const __grid_constant__ CtWeights<NT> w) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < pairs; q += (size_t)gridDim.x * blockDim.x) {
+    float2 x0[NT], x1[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) ld_pair(in + (size_t)j * elems + 2 * q, x0[j], x1[j]);
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      WSum<float> r0, i0, r1, i1;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const float h = w.hi[k * NT + j], l = w.lo[k * NT + j];
+        r0.add(h, l, x0[j].x);
+        i0.add(h, l, x0[j].y);
+        r1.add(h, l, x1[j].x);
+        i1.add(h, l, x1[j].y);
+      }
+      const float2 a = ST ? make_float2(-i0.value(), r0.value()) : make_float2(r0.value(), i0.value());
+      const float2 b = ST ? make_float2(-i1.value(), r1.value()) : make_float2(r1.value(), i1.value());
+      st_pair(out + (size_t)k * elems + 2 * q, a, b);
+    }
+  }
+}
+
 // out[k][e] = (i if ST) sum_j M[k][j] in[j][e]
 template <typename T, bool ST>
 __global__ void __launch_bounds__(256) ct_kernel(const typename cpx<T>::t* __restrict__ in,
@@ -353,8 +433,37 @@ struct GridOps {
                                      : go(col_line_kernel<T, N1, -1, true, false>);
     return dir > 0 ? go(col_line_kernel<T, N1, +1, false, true>) : go(col_line_kernel<T, N1, -1, false, true>);
   }
+  template <int NT>
+  static gw_status line_ct_reg(gw_ctx* ctx, const void* slabs, long slab_stride, long ld, const float* cw_h, void* out,
+                               long out_slice, long ldo, const int* inv, int ncols, cudaStream_t st) {
+    CtWeights<NT> w;
+    for (int e = 0; e < NT * NT; ++e) {
+      w.hi[e] = cw_h[e];
+      w.lo[e] = cw_h[NT * NT + e];
+    }
+    const size_t bytes = (size_t)NT * N1 * 32 * sizeof(float2);
+    auto kernel = col_line_ct_reg_kernel<N1, NT>;
+    gw_status s = set_smem(ctx, kernel, bytes);
+    if (s) return s;
+    dim3 grid((ncols + 31) / 32, N2 * N3);
+    KTimer kt(ctx, KF_COL_LINE_CT, ((double)NT * N1 * N2 * N3 + (double)NT * ncols) * ncols * sizeof(float2), st);
+    kernel<<<grid, 256, bytes, st>>>((const float2*)slabs, slab_stride, ld, w, (float2*)out, out_slice, ldo, inv,
+                                     N2 * N3, ncols);
+    return launch_check(ctx, "col_line_ct_reg_kernel");
+  }
   static gw_status line_ct(gw_ctx* ctx, const void* slabs, long slab_stride, long ld, int ntau, const void* cw, int nw,
-                           void* out, long out_slice, long ldo, const int* inv, int ncols, cudaStream_t st) {
+                           void* out, long out_slice, long ldo, const int* inv, int ncols, cudaStream_t st,
+                           const float* cw_h = nullptr) {
+    if (std::is_same<T, float>::value && cw_h && nw == ntau) {
+      switch (ntau) {
+        case 6: return line_ct_reg<6>(ctx, slabs, slab_stride, ld, cw_h, out, out_slice, ldo, inv, ncols, st);
+        case 8: return line_ct_reg<8>(ctx, slabs, slab_stride, ld, cw_h, out, out_slice, ldo, inv, ncols, st);
+        case 12: return line_ct_reg<12>(ctx, slabs, slab_stride, ld, cw_h, out, out_slice, ldo, inv, ncols, st);
+        case 16: return line_ct_reg<16>(ctx, slabs, slab_stride, ld, cw_h, out, out_slice, ldo, inv, ncols, st);
+        case 20: return line_ct_reg<20>(ctx, slabs, slab_stride, ld, cw_h, out, out_slice, ldo, inv, ncols, st);
+        default: break;
+      }
+    }
     const size_t bytes = (size_t)ntau * N1 * 32 * sizeof(C) + (size_t)kWParts<T> * nw * ntau * sizeof(T);
     auto kernel = col_line_ct_kernel<T, N1>;
     gw_status s = set_smem(ctx, kernel, bytes);
@@ -405,14 +514,41 @@ gw_status launch_col_line(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir,
 
 gw_status launch_col_line_ct(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* slabs, long slab_stride,
                              long ld, int ntau, const void* cw, int nw, void* out, long out_slice, long ldo,
-                             const int* inv, int ncols, cudaStream_t st) {
+                             const int* inv, int ncols, cudaStream_t st, const float* cw_h) {
   GW_DISPATCH(prec, g,
-              rc = O::line_ct(ctx, slabs, slab_stride, ld, ntau, cw, nw, out, out_slice, ldo, inv, ncols, st))
+              rc = O::line_ct(ctx, slabs, slab_stride, ld, ntau, cw, nw, out, out_slice, ldo, inv, ncols, st, cw_h))
+}
+
+template <int NT>
+static gw_status launch_ct_reg(gw_ctx* ctx, bool st_kind, const float* w_h, size_t elems, const void* in, void* out,
+                               cudaStream_t st) {
+  CtWeights<NT> w;
+  for (int e = 0; e < NT * NT; ++e) {
+    w.hi[e] = w_h[e];
+    w.lo[e] = w_h[NT * NT + e];
+  }
+  const size_t pairs = elems / 2;
+  const int blocks = (int)std::min<size_t>((pairs + 255) / 256, (size_t)ctx->num_sms * 8);
+  KTimer kt(ctx, KF_CT, 2.0 * NT * (double)elems * sizeof(float2), st);
+  if (st_kind) ct_reg_kernel<NT, true><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, pairs, elems, w);
+  else ct_reg_kernel<NT, false><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, pairs, elems, w);
+  return launch_check(ctx, "ct_reg_kernel");
 }
 
 gw_status launch_ct(gw_ctx* ctx, gw_prec prec, bool st_kind, int n, const void* dM, size_t elems, const void* in,
-                    void* out, cudaStream_t st) {
+                    void* out, cudaStream_t st, const float* w_h) {
   if (elems == 0) return GW_OK;
+  const bool al = reinterpret_cast<uintptr_t>(in) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0;
+  if (!is_fp64(prec) && w_h && al && elems % 2 == 0) {
+    switch (n) {
+      case 6: return launch_ct_reg<6>(ctx, st_kind, w_h, elems, in, out, st);
+      case 8: return launch_ct_reg<8>(ctx, st_kind, w_h, elems, in, out, st);
+      case 12: return launch_ct_reg<12>(ctx, st_kind, w_h, elems, in, out, st);
+      case 16: return launch_ct_reg<16>(ctx, st_kind, w_h, elems, in, out, st);
+      case 20: return launch_ct_reg<20>(ctx, st_kind, w_h, elems, in, out, st);
+      default: break;
+    }
+  }
   int blocks = (int)std::min<size_t>((elems + 255) / 256, (size_t)ctx->num_sms * 8);
   if (is_fp64(prec)) {
     if (st_kind) ct_kernel<double, true><<<blocks, 256, 0, st>>>((const double2*)in, (double2*)out, elems, n, (const double*)dM);
@@ -531,13 +667,14 @@ extern "C" gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double*
   cudaStream_t s = as_stream(stream);
   gw_status st = reserve(ctx, 8 * 32 * 32);
   if (st) return st;
+  std::vector<float> m32;
   if (is_fp64(prec)) {
     if ((st = upload(ctx, ctx->arena, M_h, sizeof(double) * n * n, s))) return st;
   } else {
-    const std::vector<float> m = split_weights(M_h, n * n, 1.0);
-    if ((st = upload(ctx, ctx->arena, m.data(), sizeof(float) * 2 * n * n, s))) return st;
+    m32 = split_weights(M_h, n * n, 1.0);
+    if ((st = upload(ctx, ctx->arena, m32.data(), sizeof(float) * 2 * n * n, s))) return st;
   }
-  return launch_ct(ctx, prec, kind == GW_ST, n, ctx->arena, elems, in, out, s);
+  return launch_ct(ctx, prec, kind == GW_ST, n, ctx->arena, elems, in, out, s, m32.empty() ? nullptr : m32.data());
 }
 
 // ---------------------------------------------------------------------- no-allocation variant

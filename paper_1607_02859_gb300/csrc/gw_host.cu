@@ -138,7 +138,7 @@ static void drain_timers(gw_ctx* ctx) {
 using namespace gw;
 
 static const char* kFamNames[KF_COUNT] = {"green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft",
-                                          "col_line_ct", "sigma_contract"};
+                                          "col_line_ct", "sigma_contract", "ct"};
 
 extern "C" gw_status gw_ctx_set_timing(gw_ctx* ctx, int enabled) {
   if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");

@@ -15,9 +15,9 @@ gw_status launch_col_line(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir,
                           long ldi, void* out, long ldo, int ncols, const int* inv, double scale, cudaStream_t st);
 gw_status launch_col_line_ct(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* slabs, long slab_stride,
                              long ld, int ntau, const void* cw, int nw, void* out, long out_slice, long ldo,
-                             const int* inv, int ncols, cudaStream_t st);
+                             const int* inv, int ncols, cudaStream_t st, const float* cw_h = nullptr);
 gw_status launch_ct(gw_ctx* ctx, gw_prec prec, bool st_kind, int n, const void* dM, size_t elems, const void* in,
-                    void* out, cudaStream_t st);
+                    void* out, cudaStream_t st, const float* w_h = nullptr);
 gw_status launch_hadamard(gw_ctx* ctx, gw_prec prec, size_t count, const void* a, const void* b, double scale,
                           void* out, cudaStream_t st);
 gw_status upload(gw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st);

@@ -71,13 +71,14 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
   if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
   const double fac = g.dv * g.dv / g.volume;   // Eq. FFTX2 normalisation
+  std::vector<float> cw32;                     // FP32 weights (hi, lo) for the register variant of the last pass
   if (is_fp64(prec)) {
     std::vector<double> cw(C_h, C_h + n * n);
     for (auto& v : cw) v *= fac;
     if ((st = upload(ctx, dcw, cw.data(), sizeof(double) * n * n, s))) return st;
   } else {
-    const std::vector<float> cw = split_weights(C_h, n * n, fac);
-    if ((st = upload(ctx, dcw, cw.data(), sizeof(float) * 2 * n * n, s))) return st;
+    cw32 = split_weights(C_h, n * n, fac);
+    if ((st = upload(ctx, dcw, cw32.data(), sizeof(float) * 2 * n * n, s))) return st;
   }
   for (int j = 0; j < n; ++j) {
     GreenScales gs = green_scales(eps_h, n_b, n_occ, mu, tau_h[j]);
@@ -101,7 +102,7 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
     if ((st = launch_col_plane(ctx, g, prec, -1, slab_j, n_chi, n_chi, 1.0, s))) return st;
   }
   if ((st = launch_col_line_ct(ctx, g, prec, slabs, (long)slab, n_chi, n, dcw, n, chi_w, (long)n_chi * n_chi, n_chi,
-                               dinv, n_chi, s)))
+                               dinv, n_chi, s, cw32.empty() ? nullptr : cw32.data())))
     return st;
   return tc ? tc_check(ctx, tcs, s) : GW_OK;
 }
