@@ -305,29 +305,25 @@ __global__ void __launch_bounds__(256, 2) col_line_ct_reg_kernel(const float2* _
 }
 
 // Same map with a compile-time size (FP32, weights in a kernel-parameter
-// block): each thread takes two consecutive elements (16-byte loads and
-// stores) of all n slices in registers.
+// block, constant bank): each thread keeps one element of all n slices in
+// registers.  Capped at 80 registers for three CTAs (24 warps) per SM, which
+// keeps enough loads in flight to approach the HBM rate.
 template <int NT, bool ST>
-__global__ void __launch_bounds__(256) ct_reg_kernel(const float2* __restrict__ in, float2* __restrict__ out,
-                                                     size_t pairs, size_t elems, const __grid_constant__ CtWeights<NT> w) {
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < pairs; q += (size_t)gridDim.x * blockDim.x) {
-    float2 x0[NT], x1[NT];
+__global__ void __launch_bounds__(256, 3) ct_reg1_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                      size_t elems, const __grid_constant__ CtWeights<NT> w) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < elems; e += (size_t)gridDim.x * blockDim.x) {
+    float2 x[NT];
 #pragma unroll
-    for (int j = 0; j < NT; ++j) ld_pair(in + (size_t)j * elems + 2 * q, x0[j], x1[j]);
+    for (int j = 0; j < NT; ++j) x[j] = __ldg(in + (size_t)j * elems + e);
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-      WSum<float> r0, i0, r1, i1;
+      WSum<float> re, im;
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
-        const float h = w.hi[k * NT + j], l = w.lo[k * NT + j];
-        r0.add(h, l, x0[j].x);
-        i0.add(h, l, x0[j].y);
-        r1.add(h, l, x1[j].x);
-        i1.add(h, l, x1[j].y);
+        re.add(w.hi[k * NT + j], w.lo[k * NT + j], x[j].x);
+        im.add(w.hi[k * NT + j], w.lo[k * NT + j], x[j].y);
       }
-      const float2 a = ST ? make_float2(-i0.value(), r0.value()) : make_float2(r0.value(), i0.value());
-      const float2 b = ST ? make_float2(-i1.value(), r1.value()) : make_float2(r1.value(), i1.value());
-      st_pair(out + (size_t)k * elems + 2 * q, a, b);
+      out[(size_t)k * elems + e] = ST ? make_float2(-im.value(), re.value()) : make_float2(re.value(), im.value());
     }
   }
 }
@@ -527,19 +523,17 @@ static gw_status launch_ct_reg(gw_ctx* ctx, bool st_kind, const float* w_h, size
     w.hi[e] = w_h[e];
     w.lo[e] = w_h[NT * NT + e];
   }
-  const size_t pairs = elems / 2;
-  const int blocks = (int)std::min<size_t>((pairs + 255) / 256, (size_t)ctx->num_sms * 8);
   KTimer kt(ctx, KF_CT, 2.0 * NT * (double)elems * sizeof(float2), st);
-  if (st_kind) ct_reg_kernel<NT, true><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, pairs, elems, w);
-  else ct_reg_kernel<NT, false><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, pairs, elems, w);
+  const int blocks = (int)std::min<size_t>((elems + 255) / 256, (size_t)ctx->num_sms * 12);
+  if (st_kind) ct_reg1_kernel<NT, true><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, elems, w);
+  else ct_reg1_kernel<NT, false><<<blocks, 256, 0, st>>>((const float2*)in, (float2*)out, elems, w);
   return launch_check(ctx, "ct_reg_kernel");
 }
 
 gw_status launch_ct(gw_ctx* ctx, gw_prec prec, bool st_kind, int n, const void* dM, size_t elems, const void* in,
                     void* out, cudaStream_t st, const float* w_h) {
   if (elems == 0) return GW_OK;
-  const bool al = reinterpret_cast<uintptr_t>(in) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0;
-  if (!is_fp64(prec) && w_h && al && elems % 2 == 0) {
+  if (!is_fp64(prec) && w_h) {
     switch (n) {
       case 6: return launch_ct_reg<6>(ctx, st_kind, w_h, elems, in, out, st);
       case 8: return launch_ct_reg<8>(ctx, st_kind, w_h, elems, in, out, st);
