@@ -283,20 +283,27 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_tc_kernel(const __grid_const
   }
 }
 
-// max |component| of op(X), rows x K elements of a strided matrix.
-__global__ void maxabs2d_kernel(const float2* __restrict__ X, long ld, int outer, int inner, long sx,
-                                unsigned int* __restrict__ out) {
+// max |component| of an outer x inner block of a strided matrix (batch entry
+// blockIdx.y): one warp per row, lanes along the row, four loads in flight.
+__global__ void __launch_bounds__(256) maxabs2d_kernel(const float2* __restrict__ X, long ld, int outer, int inner,
+                                                       long sx, unsigned int* __restrict__ out) {
   X += blockIdx.y * sx;
   out += blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
   float m = 0.f;
-  const long n = (long)outer * inner;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    const long i = e / inner, j = e - i * inner;
-    const float2 v = X[i * ld + j];
-    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < outer; i += gridDim.x * wpb) {
+    const float2* row = X + (long)i * ld;
+    for (int j0 = lane; j0 < inner; j0 += 128) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = j0 + 32 * u < inner ? __ldg(row + j0 + 32 * u) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m = fmaxf(m, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+  if (lane == 0) atomicMax(out, __float_as_uint(m));   // non-negative floats order as uints
 }
 
 // Split operand rows.  Element (i, k) of op(X) (i < rows, k < K; padding
@@ -383,14 +390,22 @@ gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cud
   uint16_t* blo = cv.take<uint16_t>((size_t)batch * 2 * g.N * kp);
   gw_status rc;
   if ((rc = cuda_check(ctx, cudaMemsetAsync(words, 0, 2 * batch * sizeof(unsigned int), st), "memset"))) return rc;
-  const int blocks = std::max(1, ctx->num_sms * 4 / batch);
   // A is [M][K] (or [K][M] if transposed); B's op is [K][N]: stored [K][N], or [N][K] if transposed
-  maxabs2d_kernel<<<dim3(blocks, batch), 256, 0, st>>>(g.A, g.lda, g.a_trans ? g.K : g.M, g.a_trans ? g.M : g.K, g.sA,
-                                                       words);
-  maxabs2d_kernel<<<dim3(blocks, batch), 256, 0, st>>>(g.B, g.ldb, g.b_trans ? g.N : g.K, g.b_trans ? g.K : g.N, g.sB,
-                                                       words + batch);
+  const int a_out = g.a_trans ? g.K : g.M, a_in = g.a_trans ? g.M : g.K;
+  const int b_out = g.b_trans ? g.N : g.K, b_in = g.b_trans ? g.K : g.N;
+  // the same stored elements (A A^H-type products) share one scan
+  const bool same = g.A == g.B && g.lda == g.ldb && g.sA == g.sB && a_out == b_out && a_in == b_in;
+  auto blocks_for = [&](int outer) {
+    return (int)std::max(1L, std::min<long>((outer + 7) / 8, (long)ctx->num_sms * 8 / batch));
+  };
+  maxabs2d_kernel<<<dim3(blocks_for(a_out), batch), 256, 0, st>>>(g.A, g.lda, a_out, a_in, g.sA, words);
+  if (!same)
+    maxabs2d_kernel<<<dim3(blocks_for(b_out), batch), 256, 0, st>>>(g.B, g.ldb, b_out, b_in, g.sB, words + batch);
+  else if ((rc = cuda_check(ctx, cudaMemcpyAsync(words + batch, words, batch * sizeof(unsigned int),
+                                                  cudaMemcpyDeviceToDevice, st), "copy max")))
+    return rc;
   if ((rc = launch_check(ctx, "maxabs2d_kernel"))) return rc;
-  ctx->launches++;
+  if (!same) ctx->launches++;            // launch_check counted one
   const dim3 tb(32, 8);
   const dim3 ga((g.M + 31) / 32, (kp / 2 + 31) / 32, batch), gb((g.N + 31) / 32, (kp / 2 + 31) / 32, batch);
   // B operand rows are indexed by n with k along the row: element (n, k) = opB(k, n), i.e.
