@@ -197,19 +197,37 @@ __global__ void assemble_kernel(typename cpx<T>::t* __restrict__ X, long s_x, co
   X[blockIdx.z * s_x + e] = x;
 }
 
-// W~[a][b] = v_a X[a][b] v_b, both triangles from the lower one.
+// W~[a][b] = v_a X[a][b] v_b, both triangles from the lower one.  One 32 x 32
+// tile pair (ta >= tb) per CTA through shared memory, so that the mirrored
+// (conjugate-transposed) writes are row segments too.
 template <typename T>
-__global__ void finalize_kernel(const typename cpx<T>::t* __restrict__ Xl, long s_x, const double* __restrict__ vh,
-                                typename cpx<T>::t* __restrict__ W, long s_w, int n) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = blockIdx.y;
-  if (b > a || b >= n) return;
-  auto x = Xl[blockIdx.z * s_x + (long)a * n + b];
-  const T vv = T(vh[a] * vh[b]);
-  x = cscale(x, vv);
+__global__ void __launch_bounds__(256) finalize_kernel(const typename cpx<T>::t* __restrict__ Xl, long s_x,
+                                                       const double* __restrict__ vh, typename cpx<T>::t* __restrict__ W,
+                                                       long s_w, int n) {
+  using C = typename cpx<T>::t;
+  const int ta = blockIdx.y, tb = blockIdx.x;
+  if (tb > ta) return;
+  __shared__ C t[32][33];
+  Xl += blockIdx.z * s_x;
   W += blockIdx.z * s_w;
-  W[(long)a * n + b] = x;
-  if (a != b) W[(long)b * n + a] = cconj(x);
+  const int a0 = ta * 32, b0 = tb * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int a = a0 + y, b = b0 + threadIdx.x;
+    C v = mk(T(0), T(0));
+    if (a < n && b < n) {
+      // lower element, or the mirror of one inside a diagonal tile
+      v = b <= a ? Xl[(long)a * n + b] : cconj(Xl[(long)b * n + a]);
+      v = cscale(v, T(vh[a] * vh[b]));
+      W[(long)a * n + b] = v;
+    }
+    t[y][threadIdx.x] = v;
+  }
+  if (ta == tb) return;
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int b = b0 + y, a = a0 + threadIdx.x;
+    if (a < n && b < n) W[(long)b * n + a] = cconj(t[threadIdx.x][y]);
+  }
 }
 
 // y = F z in FP64 for the Hermitian F given by its lower triangle Mlow:
@@ -594,7 +612,8 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
       if ((rc = residual_probe<T>(ctx, n, static_cast<const C*>(chi) + b * nn, dvh, e + b * nn, probe, resid_h + b,
                                   st)))
         return rc;
-  finalize_kernel<T><<<gb, tb, 0, st>>>(e, nn, dvh, static_cast<C*>(W), nn, n);
+  const int nt = (n + 31) / 32;
+  finalize_kernel<T><<<dim3(nt, nt, B), dim3(32, 8), 0, st>>>(e, nn, dvh, static_cast<C*>(W), nn, n);
   return launch_check(ctx, "finalize_kernel");
 }
 
