@@ -36,15 +36,20 @@ namespace gw {
 constexpr int kNB = 64;     // CUDA-core panel width
 constexpr int kTB = 512;    // tensor-core panel width
 
+// One CTA per row a (and batch entry): the lower part b <= a of the row.
 template <typename T>
-__global__ void build_eps_kernel(const typename cpx<T>::t* __restrict__ chi, long s_chi,
-                                 const double* __restrict__ vh, typename cpx<T>::t* __restrict__ E, long s_e, int n) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = blockIdx.y;
-  if (b > a || b >= n) return;
-  const T vv = T(vh[a] * vh[b]);
-  const auto x = chi[blockIdx.z * s_chi + (long)a * n + b];
-  E[blockIdx.z * s_e + (long)a * n + b] = mk(-vv * x.x, -vv * x.y);
+__global__ void __launch_bounds__(256) build_eps_kernel(const typename cpx<T>::t* __restrict__ chi, long s_chi,
+                                                        const double* __restrict__ vh,
+                                                        typename cpx<T>::t* __restrict__ E, long s_e, int n) {
+  const int a = blockIdx.x;
+  const double va = vh[a];
+  const auto* src = chi + blockIdx.y * s_chi + (long)a * n;
+  auto* dst = E + blockIdx.y * s_e + (long)a * n;
+  for (int b = threadIdx.x; b <= a; b += blockDim.x) {
+    const T vv = T(va * vh[b]);
+    const auto x = src[b];
+    dst[b] = mk(-vv * x.x, -vv * x.y);
+  }
 }
 
 // Unblocked Cholesky (K form) of the kb x kb diagonal block, in shared memory.
@@ -182,19 +187,20 @@ __global__ void zero_block_kernel(typename cpx<T>::t* __restrict__ P, long ld, l
   P[blockIdx.z * s_p + (long)blockIdx.y * ld + b] = mk(T(0), T(0));
 }
 
-// X = P^H P + P + P^H (lower triangle, in place over P^H P).
+// X = P^H P + P + P^H (lower triangle, in place over P^H P); one CTA per row.
 template <typename T>
-__global__ void assemble_kernel(typename cpx<T>::t* __restrict__ X, long s_x, const typename cpx<T>::t* __restrict__ P,
-                                long s_p, int n) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = blockIdx.y;
-  if (b > a || b >= n) return;
-  const long e = (long)a * n + b;
-  auto x = X[blockIdx.z * s_x + e];
-  const auto p = P[blockIdx.z * s_p + e];
-  x.x += a == b ? T(2) * p.x : p.x;
-  x.y += a == b ? T(0) : p.y;
-  X[blockIdx.z * s_x + e] = x;
+__global__ void __launch_bounds__(256) assemble_kernel(typename cpx<T>::t* __restrict__ X, long s_x,
+                                                       const typename cpx<T>::t* __restrict__ P, long s_p, int n) {
+  const int a = blockIdx.x;
+  auto* xr = X + blockIdx.y * s_x + (long)a * n;
+  const auto* pr = P + blockIdx.y * s_p + (long)a * n;
+  for (int b = threadIdx.x; b <= a; b += blockDim.x) {
+    auto x = xr[b];
+    const auto p = pr[b];
+    x.x += a == b ? T(2) * p.x : p.x;
+    x.y += a == b ? T(0) : p.y;
+    xr[b] = x;
+  }
 }
 
 // W~[a][b] = v_a X[a][b] v_b, both triangles from the lower one.  One 32 x 32
@@ -503,8 +509,7 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
   const long nn = (long)n * n;
   const Batch bt{B, nn};
   if ((rc = set_attrs<T>(ctx))) return rc;
-  const dim3 tb(128), gb((n + 127) / 128, n, B);
-  build_eps_kernel<T><<<gb, tb, 0, st>>>(static_cast<const C*>(chi), nn, dvh, e, nn, n);
+  build_eps_kernel<T><<<dim3(n, B), 256, 0, st>>>(static_cast<const C*>(chi), nn, dvh, e, nn, n);
   if ((rc = launch_check(ctx, "build_eps_kernel"))) return rc;
   if (!tcs) {
     // CUDA cores, 64-column panels over the whole matrix
@@ -601,7 +606,7 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
       }
     }
   }
-  assemble_kernel<T><<<gb, tb, 0, st>>>(e, nn, p, nn, n);
+  assemble_kernel<T><<<dim3(n, B), 256, 0, st>>>(e, nn, p, nn, n);
   if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
   if (refine > 0)
     for (int b = 0; b < B; ++b)
