@@ -9,7 +9,7 @@ continuation (gw_sigma_diag).  The metric is the effective TFLOP/s of the
 method's algorithmic work (flop model below) divided by the device time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gw|reference]
-                  [--prec fp32|fp64|f16x3|bf16x3] [--workload si8|gamma_toy]
+                  [--prec fp32|fp64|f16x3|bf16x3] [--workload si8|mid|gamma_toy|si64]
 
 N > 1 (under torchrun): independent replicas, one per GPU (the path is not
 sharded); value = the work of all ranks / the slowest rank's time.
@@ -189,7 +189,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--prec", default="f16x3", choices=["fp32", "fp64", "f16x3", "bf16x3"])
-    ap.add_argument("--workload", default="si8", choices=["si8", "mid", "gamma_toy"])
+    ap.add_argument("--workload", default="si8", choices=["si8", "mid", "gamma_toy", "si64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-stage pass")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")

@@ -119,6 +119,104 @@ __global__ void __launch_bounds__(THREADS) row_fft_kernel(const typename cpx<T>:
   }
 }
 
+// Rows too long for shared memory (36^3 = 46656 points, 373 KB) take two
+// passes through HBM.  The plane pass does the (i2, i3) 2-D transform of
+// kRowPlanes consecutive planes of one row per CTA; the line pass does the i1
+// transforms of one row per CTA in registers, with the G-set side of the row
+// (n_chi values) held in shared memory: forward, the results are scattered
+// there through inv and the row is written out in order; backward, the input
+// row is staged there and gathered through inv.
+constexpr int kRowPlanes = 4;
+
+// MODE 0: x = scale a conj(b) -> out;  MODE 1: x = a -> out;  MODE 2: out in place, times scale.
+template <typename T, int N1, int N2, int N3, int MODE, int DIR>
+__global__ void __launch_bounds__(256) row_plane_kernel(const typename cpx<T>::t* a,
+                                                        const typename cpx<T>::t* b, long lda,
+                                                        typename cpx<T>::t* out, long ldo, T scale) {
+  using C = typename cpx<T>::t;
+  constexpr int S2 = N3 % 2 == 0 ? N3 + 1 : N3;      // odd pencil stride
+  constexpr int PL = N2 * N3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);               // [kRowPlanes][N2][S2]
+  const long row = blockIdx.y;
+  const int i10 = blockIdx.x * kRowPlanes;
+  const int np = min(kRowPlanes, N1 - i10);
+  const long base = (long)i10 * PL;
+  for (int e = threadIdx.x; e < np * PL; e += blockDim.x) {
+    const int p = e / PL, rem = e - p * PL, i2 = rem / N3, i3 = rem - i2 * N3;
+    C v;
+    if (MODE == 2) {
+      v = out[row * ldo + base + e];
+    } else {
+      v = a[row * lda + base + e];
+      if (MODE == 0) v = cscale(cmulc(v, b[row * lda + base + e]), scale);
+    }
+    s[(p * N2 + i2) * S2 + i3] = v;
+  }
+  __syncthreads();
+  pencil_pass<N3, DIR>(s, np * N2, 1, [](int q) { return q * S2; });
+  __syncthreads();
+  pencil_pass<N2, DIR>(s, np * N3, S2, [](int q) { return (q / N3) * (N2 * S2) + (q % N3); });
+  __syncthreads();
+  for (int e = threadIdx.x; e < np * PL; e += blockDim.x) {
+    const int p = e / PL, rem = e - p * PL, i2 = rem / N3, i3 = rem - i2 * N3;
+    const C v = s[(p * N2 + i2) * S2 + i3];
+    out[row * ldo + base + e] = MODE == 2 ? cscale(v, scale) : v;
+  }
+}
+
+// Forward line pass: i1 transforms (+i) of tmp's row, the G set scattered into
+// shared memory through inv, then out[row][j], j < n_chi, in order.
+template <typename T, int N1, int N2, int N3>
+__global__ void __launch_bounds__(256) row_line_fwd_kernel(const typename cpx<T>::t* __restrict__ tmp, long ldt,
+                                                           typename cpx<T>::t* __restrict__ out, long ldo,
+                                                           const int* __restrict__ inv, int n_chi) {
+  using C = typename cpx<T>::t;
+  constexpr int PL = N2 * N3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* so = reinterpret_cast<C*>(smem_raw);              // [n_chi]
+  const long row = blockIdx.x;
+  for (int i23 = threadIdx.x; i23 < PL; i23 += blockDim.x) {
+    C x[N1];
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) x[i1] = tmp[row * ldt + (long)i1 * PL + i23];
+    RegFFT<N1, +1>::run(x);
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int j = inv[i1 * PL + i23];
+      if (j >= 0) so[j] = x[i1];
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n_chi; j += blockDim.x) out[row * ldo + j] = so[j];
+}
+
+// Backward line pass: a's row (n_chi values of the G set) staged in shared
+// memory, gathered through inv into the grid, i1 transforms (-i) into out.
+template <typename T, int N1, int N2, int N3>
+__global__ void __launch_bounds__(256) row_line_bwd_kernel(const typename cpx<T>::t* __restrict__ a, long lda,
+                                                           typename cpx<T>::t* __restrict__ out, long ldo,
+                                                           const int* __restrict__ inv, int n_chi) {
+  using C = typename cpx<T>::t;
+  constexpr int PL = N2 * N3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* si = reinterpret_cast<C*>(smem_raw);              // [n_chi]
+  const long row = blockIdx.x;
+  for (int j = threadIdx.x; j < n_chi; j += blockDim.x) si[j] = a[row * lda + j];
+  __syncthreads();
+  for (int i23 = threadIdx.x; i23 < PL; i23 += blockDim.x) {
+    C x[N1];
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int j = inv[i1 * PL + i23];
+      x[i1] = j >= 0 ? si[j] : mk(T(0), T(0));
+    }
+    RegFFT<N1, -1>::run(x);
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) out[row * ldo + (long)i1 * PL + i23] = x[i1];
+  }
+}
+
 constexpr int kPlaneW = 16;
 
 // In-place 2-D FFT over (i2, i3) of the rows of plane i1 = blockIdx.y, for 16
@@ -264,7 +362,7 @@ struct CtWeights {
 };
 
 template <int N1, int NT>
-__global__ void __launch_bounds__(256, 2) col_line_ct_reg_kernel(const float2* __restrict__ slabs, long slab_stride,
+__global__ void __launch_bounds__(256, (NT * N1 * 32 * 8 <= 110 * 1024) ? 2 : 1) col_line_ct_reg_kernel(const float2* __restrict__ slabs, long slab_stride,
                                                               long ld, const __grid_constant__ CtWeights<NT> cw,
                                                               float2* __restrict__ out, long out_slice, long ldo,
                                                               const int* __restrict__ inv, int plane, int ncols) {
@@ -377,9 +475,51 @@ static gw_status set_smem(gw_ctx* ctx, K kernel, size_t bytes) {
 template <typename T, int N1, int N2, int N3>
 struct GridOps {
   using C = typename cpx<T>::t;
+  static gw_status row_two_pass(gw_ctx* ctx, int mode, const void* a, const void* b, long lda, void* out, long ldo,
+                                const int* inv, void* tmp, int n_chi, int n_rows, double scale, cudaStream_t st) {
+    constexpr int NR = N1 * N2 * N3;
+    constexpr int S2 = N3 % 2 == 0 ? N3 + 1 : N3;
+    const size_t pbytes = (size_t)kRowPlanes * N2 * S2 * sizeof(C);
+    const size_t lbytes = (size_t)n_chi * sizeof(C);
+    if (!inv || (mode != 2 && !tmp))
+      return fail(ctx, GW_ERR_UNSUPPORTED, "this grid's rows need the two-pass transform (index map and workspace)");
+    if (lbytes > 200 * 1024) return fail(ctx, GW_ERR_UNSUPPORTED, "G set too large for the two-pass row transform");
+    const dim3 pgrid((N1 + kRowPlanes - 1) / kRowPlanes, n_rows);
+    const double rd = mode == 0 ? 2.0 * NR : (mode == 1 ? NR : n_chi);
+    const double wr = mode == 2 ? NR : n_chi;
+    gw_status rc;
+    auto plane = [&](auto kernel, const void* pa, const void* pb, long pld, void* po, long pldo) -> gw_status {
+      gw_status r = set_smem(ctx, kernel, pbytes);
+      if (r) return r;
+      KTimer kt(ctx, KF_ROW_FFT, 0.0, st);
+      kernel<<<pgrid, 256, pbytes, st>>>((const C*)pa, (const C*)pb, pld, (C*)po, pldo, (T)scale);
+      return launch_check(ctx, "row_plane_kernel");
+    };
+    if (mode == 2) {
+      auto kl = row_line_bwd_kernel<T, N1, N2, N3>;
+      if ((rc = set_smem(ctx, kl, lbytes))) return rc;
+      {
+        KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (rd + wr) * sizeof(C), st);
+        kl<<<n_rows, 256, lbytes, st>>>((const C*)a, lda, (C*)out, ldo, inv, n_chi);
+        if ((rc = launch_check(ctx, "row_line_bwd_kernel"))) return rc;
+      }
+      return plane(row_plane_kernel<T, N1, N2, N3, 2, -1>, nullptr, nullptr, 0, out, ldo);
+    }
+    if (mode == 0) rc = plane(row_plane_kernel<T, N1, N2, N3, 0, +1>, a, b, lda, tmp, NR);
+    else rc = plane(row_plane_kernel<T, N1, N2, N3, 1, +1>, a, nullptr, lda, tmp, NR);
+    if (rc) return rc;
+    auto kl = row_line_fwd_kernel<T, N1, N2, N3>;
+    if ((rc = set_smem(ctx, kl, lbytes))) return rc;
+    KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (rd + wr) * sizeof(C), st);
+    kl<<<n_rows, 256, lbytes, st>>>((const C*)tmp, NR, (C*)out, ldo, inv, n_chi);
+    return launch_check(ctx, "row_line_fwd_kernel");
+  }
   static gw_status row(gw_ctx* ctx, int mode, const void* a, const void* b, long lda, void* out, long ldo,
-                       const int* map, int n_chi, int n_rows, double scale, cudaStream_t st) {
+                       const int* map, int n_chi, int n_rows, double scale, cudaStream_t st, const int* inv,
+                       void* tmp) {
     const size_t bytes = RowLayout<N1, N2, N3>::TOT * sizeof(C);
+    if (bytes > kRowSmemMax)
+      return row_two_pass(ctx, mode, a, b, lda, out, ldo, inv, tmp, n_chi, n_rows, scale, st);
     const double rd = mode == 0 ? 2.0 * RowLayout<N1, N2, N3>::NR : (mode == 1 ? RowLayout<N1, N2, N3>::NR : n_chi);
     const double wr = mode == 2 ? RowLayout<N1, N2, N3>::NR : n_chi;
     auto al = [](const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; };
@@ -493,9 +633,14 @@ static bool with_grid(const GridInfo& g, F&& f) {
 
 gw_status launch_row_fft(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int mode, const void* a, const void* b,
                          long lda, void* out, long ldo, const int* map, int n_chi, int n_rows, double scale,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int* inv, void* tmp) {
   if (n_rows <= 0) return GW_OK;
-  GW_DISPATCH(prec, g, rc = O::row(ctx, mode, a, b, lda, out, ldo, map, n_chi, n_rows, scale, st))
+  GW_DISPATCH(prec, g, rc = O::row(ctx, mode, a, b, lda, out, ldo, map, n_chi, n_rows, scale, st, inv, tmp))
+}
+
+bool row_two_pass(const GridInfo& g, gw_prec prec) {
+  const size_t s2 = g.n3 % 2 == 0 ? g.n3 + 1 : g.n3;
+  return (size_t)g.n1 * g.n2 * s2 * csize(prec) > kRowSmemMax;
 }
 
 gw_status launch_col_plane(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, void* buf, long ld, int ncols,
@@ -626,18 +771,24 @@ extern "C" gw_status gw_rr_to_GG_fft(gw_ctx* ctx, const gw_grid* grid, int direc
   if ((st = index_maps(ctx, g, fft_index_h, n_chi, map, inv))) return st;
   if (stage == 1 && (n_rows < 0 || r0 < 0 || r0 + n_rows > g.nr)) return fail(ctx, GW_ERR_SHAPE, "rows out of range");
   cudaStream_t s = as_stream(stream);
+  // rows too long for shared memory need a [n_rows][N_r] workspace forward
+  const bool work_rows = stage == 1 && direction > 0 && row_two_pass(g, prec);
   Carver probe(nullptr);
   probe.take<int>(n_chi);
   probe.take<int>(g.nr);
+  if (work_rows) probe.take<char>((size_t)n_rows * g.nr * csize(prec));
   if ((st = reserve(ctx, probe.off))) return st;
   Carver cv(ctx->arena);
   int* dmap = cv.take<int>(n_chi);
   int* dinv = cv.take<int>(g.nr);
+  void* tmp = work_rows ? cv.take<char>((size_t)n_rows * g.nr * csize(prec)) : nullptr;
   if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
   if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
   if (stage == 1) {
-    if (direction > 0) return launch_row_fft(ctx, g, prec, 1, in, nullptr, g.nr, out, n_chi, dmap, n_chi, n_rows, 1.0, s);
-    return launch_row_fft(ctx, g, prec, 2, in, nullptr, n_chi, out, g.nr, dmap, n_chi, n_rows, 1.0 / g.volume, s);
+    if (direction > 0)
+      return launch_row_fft(ctx, g, prec, 1, in, nullptr, g.nr, out, n_chi, dmap, n_chi, n_rows, 1.0, s, dinv, tmp);
+    return launch_row_fft(ctx, g, prec, 2, in, nullptr, n_chi, out, g.nr, dmap, n_chi, n_rows, 1.0 / g.volume, s,
+                          dinv);
   }
   if (direction > 0) {
     // in [N_r][n_chi] is the work buffer: (i2,i3) planes in place, then the i1 pass writes the G rows of out.

@@ -6,9 +6,14 @@
 namespace gw {
 
 // gw_fft.cu
+// Rows whose shared-memory copy exceeds kRowSmemMax go through two passes
+// (row_two_pass(g, prec)); those need inv (grid position -> G index or -1) and,
+// forward, a [n_rows][N_r] workspace tmp (which may be a itself for mode 0).
+constexpr size_t kRowSmemMax = 227 * 1024;
 gw_status launch_row_fft(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int mode, const void* a, const void* b,
                          long lda, void* out, long ldo, const int* map, int n_chi, int n_rows, double scale,
-                         cudaStream_t st);
+                         cudaStream_t st, const int* inv = nullptr, void* tmp = nullptr);
+bool row_two_pass(const GridInfo& g, gw_prec prec);
 gw_status launch_col_plane(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, void* buf, long ld, int ncols,
                            double scale, cudaStream_t st);
 gw_status launch_col_line(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, int variant, const void* in,

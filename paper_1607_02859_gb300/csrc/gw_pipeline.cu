@@ -91,11 +91,11 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
         if ((st = tc_chi_rows(ctx, g, n_b, n_occ, psi, gs, r0, rows, prec, ga, tcs, first, s))) return st;
         first = false;
         st = launch_row_fft(ctx, g, prec, 1, ga, nullptr, g.nr, slab_j + (size_t)r0 * n_chi * es, n_chi, dmap, n_chi,
-                            rows, 1.0, s);
+                            rows, 1.0, s, dinv, gb);
       } else {
         if ((st = green_rows(ctx, g, n_b, n_occ, psi, sj, gs, r0, rows, prec, ga, gb, s))) return st;
         st = launch_row_fft(ctx, g, prec, 0, ga, gb, g.nr, slab_j + (size_t)r0 * n_chi * es, n_chi, dmap, n_chi, rows,
-                            -2.0, s);
+                            -2.0, s, dinv, ga);
       }
       if (st) return st;
     }

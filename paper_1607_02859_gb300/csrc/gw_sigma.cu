@@ -342,7 +342,7 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
       if (st) return st;
       // W~(r,R') of the block (second step of Eq. FFTW), then the contraction
       if ((st = launch_row_fft(ctx, g, prec, 2, wrg + (size_t)r0 * n_chi * es, nullptr, n_chi, wrr, g.nr, dmap, n_chi,
-                               rows, 1.0, s)))
+                               rows, 1.0, s, dinv)))
         return st;
       if ((st = launch_sigma_contract(ctx, prec, wrr, gob, gub, g.nr, g.nr, rows, psi, dbands, n_n, r0, coef,
                                       acc_u + j, acc_o + j, n, s)))
