@@ -115,6 +115,36 @@ class ClockSampler:
         return out
 
 
+# DRAM bytes per launch of a kernel family from an ncu capture (profiles/), valid
+# only for the kernel source it was taken on: the sha1 of those files is checked
+# at run time and a mismatch reports null.
+MEASURED_TRAFFIC = {
+    ("si8", "f16x3", "cgemm_tc"): {
+        "bytes_per_launch": 1.3816e10,
+        "sources": {"paper_1607_02859_gb300/csrc/gw_tcgemm.cu": "c27907371a5f4c4ce666246524600209b3efb43e",
+                    "paper_1607_02859_gb300/csrc/gw_tcgen05.cuh": "9b50b7a589cc5e99cff2a95e30ffc334ce4d64ad"},
+        "profile": "profiles/cgemm_tc_si8_f16x3_dram.md",
+    },
+}
+
+
+def measured_traffic(workload, prec, family):
+    """Bytes per launch recorded for this kernel, or None if none was recorded or its source changed."""
+    import hashlib
+    rec = MEASURED_TRAFFIC.get((workload, prec, family))
+    if rec is None:
+        return None
+    root = os.path.dirname(os.path.abspath(__file__))
+    for path, sha in rec["sources"].items():
+        try:
+            with open(os.path.join(root, path), "rb") as f:
+                if hashlib.sha1(f.read()).hexdigest() != sha:
+                    return None
+        except OSError:
+            return None
+    return rec["bytes_per_launch"]
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -322,8 +352,12 @@ def main():
             ach = k["work"] / (k["ms"] / 1e3) / 1e12
             roof = {"bound": "alu", "unit": "TFLOP/s", "peak": sm_peak_fp32(sm_max),
                     "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x %.0f MHz" % sm_max}
+        traffic = measured_traffic(args.workload, args.prec, dom)
         roof.update({"kernel": dom, "launches": k["launches"], "achieved": ach, "frac": ach / roof["peak"],
-                     "traffic": None, "share_of_step": k["ms"] / (1e3 * t_dev / args.steps)})
+                     "traffic": traffic, "share_of_step": k["ms"] / (1e3 * t_dev / args.steps)})
+        if traffic is not None:
+            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, %s"
+                                      % MEASURED_TRAFFIC[(args.workload, args.prec, dom)]["profile"])
 
     # end to end through the public API: orbitals copied from pinned host memory every step,
     # Sigma read back to the host inside the call
