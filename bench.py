@@ -154,7 +154,10 @@ def measured_peaks():
 
 # ---------------------------------------------------------------------- reference arm (CPU oracle)
 
-def oracle_sample(p, rows=96, n_solve=1536):
+SAMPLE_ROWS, SAMPLE_SOLVE = 768, 3072      # ~10 s of the FP64 oracle on 16 host cores at si8
+
+
+def oracle_sample(p, rows=SAMPLE_ROWS, n_solve=SAMPLE_SOLVE):
     """Time the FP64 oracle on a bounded slice of the workload: G_occ/G_unocc rows and the
     real-space chi product for `rows` rows at every tau, plus one screening solve of size
     n_solve.  Returns (flops, seconds) under the same flop model."""
@@ -199,7 +202,8 @@ def run_reference(args, p, workload):
         tot_f += f
         tot_t += t
     val = tot_f / tot_t / 1e12
-    sample = "FP64 numpy oracle: G_occ/G_unocc rows + chi product for 96 of %d rows at all %d tau, plus one 1536^2 screening solve" % (p.n_r, len(p.tau))
+    sample = ("FP64 numpy oracle: G_occ/G_unocc rows + chi product for %d of %d rows at all %d tau, plus one %d^2 "
+              "screening solve" % (SAMPLE_ROWS, p.n_r, len(p.tau), SAMPLE_SOLVE))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -390,7 +394,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         f, t = oracle_sample(p)
         line["cpu_baseline"] = {"value": f / t / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
-                                "sample": "FP64 numpy oracle: G rows + chi product for 96 of %d rows at all %d tau, plus one 1536^2 screening solve (%.1f s)" % (p.n_r, n_tau, t)}
+                                "sample": "FP64 numpy oracle: G rows + chi product for %d of %d rows at all %d tau, plus "
+                                          "one %d^2 screening solve (%.1f s)" % (SAMPLE_ROWS, p.n_r, n_tau, SAMPLE_SOLVE, t)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
