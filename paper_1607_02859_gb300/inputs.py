@@ -202,3 +202,80 @@ def serve_mix(count=6, seed=40, n_chi_cap=1536):
                                 n_tau, seed + 1 + i, n_bands_sigma=4, n_chi=min(n ** 3, n_chi_cap),
                                 pin_edges=True, name="mix%d_%d^3_%db_%dt" % (i, n, n_b, n_tau)))
     return out
+
+
+@dataclass
+class KmeshProblem:
+    """A cell sampled on a Gamma-centred k mesh.  k index = (k1*nk2 + k2)*nk3 + k3
+    for k = sum_d (k_d / nk_d) b_d, k_d in [0, nk_d)."""
+
+    n: tuple
+    lattice: np.ndarray
+    nk: tuple
+    psi_k: np.ndarray        # [N_k][N_b][N_r] complex128: Bloch orbitals exp(i k.r) u_nk(r) on the cell grid
+    eps_k: np.ndarray        # [N_k][N_b], ascending per k
+    n_occ: int
+    mu: float
+    tau: np.ndarray
+    omega: np.ndarray
+    n_chi: int
+    x_min: float
+    x_max: float
+    n_x: int = 4000
+    ridge: float = 1e-6
+    name: str = ""
+
+    @property
+    def n_r(self) -> int:
+        return int(np.prod(self.n))
+
+    @property
+    def n_k(self) -> int:
+        return int(np.prod(self.nk))
+
+    @property
+    def n_b(self) -> int:
+        return self.psi_k.shape[1]
+
+    @property
+    def volume(self) -> float:
+        return abs(float(np.linalg.det(self.lattice)))
+
+
+def kmesh_problem(n=(6, 6, 6), a=(6.0, 6.5, 7.0), nk=(2, 2, 2), n_occ=4, n_unocc=20, n_tau=4, seed=51,
+                  eps_occ=(-0.6, -0.05), eps_unocc=(0.05, 2.0), mu=0.0, n_chi=None):
+    """Seeded k-mesh system: for every k, N_b orthonormal Bloch orbitals
+    exp(i k.r) sum_g U_k[g][n] exp(i g.r) / sqrt(Omega) over the lowest N_b plane
+    waves g (U_k from QR of a complex Gaussian), eigenvalues uniform in the
+    windows with the band edges pinned (gap eps_unocc[0] - eps_occ[1] at every k)."""
+    rng = np.random.default_rng(seed)
+    n = tuple(int(x) for x in n)
+    nk = tuple(int(x) for x in nk)
+    lengths = np.broadcast_to(np.asarray(a, dtype=float), (3,))
+    lattice = np.diag(lengths)
+    vol = float(np.prod(lengths))
+    n_b = n_occ + n_unocc
+    basis = _plane_waves_on_grid(n, _sorted_lattice_points(n)[:n_b])
+    i = [np.arange(nd) for nd in n]
+    psi_k, eps_k = [], []
+    for k1 in range(nk[0]):
+        for k2 in range(nk[1]):
+            for k3 in range(nk[2]):
+                kk = (k1, k2, k3)
+                e = [np.exp(2j * np.pi * kk[d] * i[d] / (nk[d] * n[d])) for d in range(3)]
+                bloch = (e[0][:, None, None] * e[1][None, :, None] * e[2][None, None, :]).reshape(-1)
+                z = rng.standard_normal((n_b, n_b)) + 1j * rng.standard_normal((n_b, n_b))
+                U, _ = np.linalg.qr(z)
+                psi_k.append(bloch[None, :] * (U.T @ basis) / np.sqrt(vol))
+                eo = np.sort(rng.uniform(eps_occ[0], eps_occ[1], n_occ))
+                eu = np.sort(rng.uniform(eps_unocc[0], eps_unocc[1], n_unocc))
+                eo[-1], eu[0] = eps_occ[1], eps_unocc[0]
+                eps_k.append(np.concatenate([eo, eu]))
+    eps_k = np.array(eps_k)
+    gap = eps_unocc[0] - eps_occ[1]
+    width = eps_k.max() - eps_k.min()
+    tau = np.geomspace(0.1 / width, 3.0 / gap, n_tau)
+    return KmeshProblem(n=n, lattice=lattice, nk=nk, psi_k=np.array(psi_k), eps_k=eps_k, n_occ=n_occ, mu=float(mu),
+                        tau=tau, omega=1.0 / tau[::-1], n_chi=int(np.prod(n)) if n_chi is None else int(n_chi),
+                        x_min=float(np.min(np.abs(eps_k - mu))), x_max=float(width + np.max(np.abs(eps_k - mu))),
+                        name="kmesh_%dx%dx%d_k%dx%dx%d" % (n + nk))

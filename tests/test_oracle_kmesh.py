@@ -1,0 +1,57 @@
+"""Pins of the k-mesh oracle (oracle/kmesh.py) against the Gamma-point oracle,
+which tests/test_oracle_pins.py pins to the paper: the stripe route on a
+Gamma-centred k mesh must give the q-diagonal blocks of the supercell's
+Gamma-point chi, whose blocks q != q' vanish; a 1 x 1 x 1 mesh is the Gamma
+point itself."""
+import numpy as np
+
+from oracle import chi as ochi
+from oracle import green as ogr
+from oracle import gvec as ogv
+from oracle import kmesh as okm
+from paper_1607_02859_gb300 import inputs
+
+
+def supercell_chi(p, gv, tau):
+    psi_s, eps_s, no_s = okm.supercell_orbitals(p.psi_k, p.eps_k, p.n_occ, p.n, p.nk)
+    ns = tuple(np.asarray(p.n) * np.asarray(p.nk))
+    lat_s = p.lattice * np.asarray(p.nk)[:, None]
+    x = ochi.chi_rr(ogr.green_occ(psi_s, eps_s, no_s, p.mu, tau), ogr.green_unocc(psi_s, eps_s, no_s, p.mu, tau))
+    return ochi.chi_gg(x, okm.supercell_gvecs(gv, p.nk), ns, lat_s)
+
+
+def test_stripe_route_equals_supercell_gamma_point():
+    p = inputs.kmesh_problem(n=(4, 4, 4), a=(5.0, 5.5, 6.0), nk=(2, 2, 1), n_occ=3, n_unocc=9, n_tau=2, seed=52)
+    gv = ogv.g_set(p.n, 40)
+    tau = p.tau[1]
+    cq = okm.chi_q_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk, p.lattice, gv)
+    cs = supercell_chi(p, gv, tau)
+    nq, nc = p.n_k, len(gv)
+    scale = np.linalg.norm(cs)
+    for a in range(nq):
+        for b in range(nq):
+            blk = cs[a * nc:(a + 1) * nc, b * nc:(b + 1) * nc]
+            if a == b:
+                assert np.linalg.norm(blk - cq[a]) < 1e-12 * scale
+            else:
+                assert np.linalg.norm(blk) < 1e-12 * scale
+
+
+def test_single_k_is_gamma_point():
+    p = inputs.kmesh_problem(n=(4, 4, 4), nk=(1, 1, 1), n_occ=3, n_unocc=9, n_tau=2, seed=53)
+    gv = ogv.g_set(p.n, 64)
+    tau = p.tau[0]
+    cq = okm.chi_q_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk, p.lattice, gv)
+    x = ochi.chi_rr(ogr.green_occ(p.psi_k[0], p.eps_k[0], p.n_occ, p.mu, tau),
+                    ogr.green_unocc(p.psi_k[0], p.eps_k[0], p.n_occ, p.mu, tau))
+    ref = ochi.chi_gg(x, gv, p.n, p.lattice)
+    assert np.linalg.norm(cq[0] - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_chi_q_hermitian_and_negative_semidefinite():
+    p = inputs.kmesh_problem(n=(4, 4, 4), nk=(2, 1, 2), n_occ=3, n_unocc=9, n_tau=2, seed=54)
+    gv = ogv.g_set(p.n, 32)
+    cq = okm.chi_q_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, p.tau[0], p.n, p.nk, p.lattice, gv)
+    for c in cq:
+        assert np.linalg.norm(c - c.conj().T) < 1e-12 * np.linalg.norm(c)
+        assert np.linalg.eigvalsh(0.5 * (c + c.conj().T)).max() < 1e-12 * np.linalg.norm(c)
