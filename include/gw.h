@@ -273,6 +273,29 @@ gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
                         const int32_t* fft_index_h, gw_prec prec, int r_block, void* chi_w,
                         void* stream);
 
+/* chi0(q+G, q+G', i omega_k) for every q of a Gamma-centred nk[0] x nk[1] x nk[2]
+ * k mesh, through the supercell stripe of Sec. II.A (spatial transform within
+ * a supercell, Eqs. FFT_G1, FFT_G2): for every tau_j and block of cell rows r,
+ * G_occ,k / G_unocc,k (Eqs. Green_occ/unocc over the orbitals of k), the stripe
+ *   G(r, r'+L) = (1/N_k) sum_k exp(-i k.L) G_k(r, r')     (L: cell lattice vectors of the supercell)
+ * and chi(r, R') = -2 G_occ(r, R') conj(G_unocc(r, R')) on the supercell grid,
+ * the transform over R' to the supercell G set {q + g'}, then per q the factor
+ * exp(-i q.r), the transform over r with dV^2/Omega (Eq. FFTX2) and the cosine
+ * transform (Eq. CTX):
+ *   chi_w [N_k][n][n_chi][n_chi] = chi_q(g, g', i omega_k),  q in k order.
+ * psi_k: device [N_k][n_b][N_r], the Bloch orbitals exp(i k.r) u_nk(r) of each k
+ * on the cell grid, normalised as at Gamma; k index (k1 nk[1] + k2) nk[2] + k3
+ * for k = sum_d (k_d / nk[d]) b_d, k_d in [0, nk[d]).  eps_k_h [N_k][n_b]
+ * ascending per k with mu in every gap.  gvec_h [n_chi][3]: the cell G set as
+ * integer triples with g_d in [-n_d/2, n_d/2).  At most 64 k points; the
+ * supercell grid nk[d] n_d must be one the library compiles.  r_block <= 0
+ * picks a default.  The result is the q-diagonal block of the Gamma-point
+ * chi0 of the supercell holding the N_k cells. */
+gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_b, int n_occ,
+                              const void* psi_k, const double* eps_k_h, double mu, int n,
+                              const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
+                              gw_prec prec, int r_block, void* chi_w, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "G
 EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes", "gw_ctx_reserve",
            "gw_ctx_set_timing", "gw_ctx_kernel_stats", "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
-           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine"]
+           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh"]
 
 
 class GwError(RuntimeError):
@@ -70,6 +70,7 @@ _SIGS = {
     "gw_tau_to_omega": (_I, [_P, _I, _I, _DP, ct.c_size_t, _I, _P, _P, _P]),
     "gw_screen_W": (_I, [_P, _G, _I, _IP, _I, _I, _P, _P, _DP, _P]),
     "gw_screen_W_refine": (_I, [_P, _G, _I, _IP, _I, _I, _I, _P, _P, _DP, _P]),
+    "gw_chi0_omega_kmesh": (_I, [_P, _G, _IP, _I, _I, _P, _DP, ct.c_double, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                            _DP, _DP, _DP, _I, _DP, _P]),
     "gw_chi0_omega": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
@@ -341,3 +342,17 @@ def chi0_omega(ctx, grid, psi, eps, n_occ, mu, tau, C, fft_index, prec, chi_w, r
     _check(lib().gw_chi0_omega(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p), _dp(eps),
                                float(mu), len(tau), _dp(tau), _dp(C), len(idx), _ip(idx), p, int(r_block),
                                _dev(chi_w, "chi_w", p), _stream()), ctx)
+
+
+def chi0_omega_kmesh(ctx, grid, nk, psi_k, eps_k, n_occ, mu, tau, C, gvec, prec, chi_w, r_block=0):
+    """chi0_q(G,G',i omega) for every q of a Gamma-centred k mesh (gw_chi0_omega_kmesh).
+    psi_k: device [N_k][N_b][N_r]; eps_k [N_k][N_b]; gvec [n_chi][3]; chi_w [N_k][n][n_chi][n_chi]."""
+    p = prec_of(prec)
+    nkv = _i32(nk)
+    eps_k = _f64(eps_k)
+    tau = _f64(tau)
+    C = _f64(C)
+    gv = _i32(gvec)
+    _check(lib().gw_chi0_omega_kmesh(ctx.handle, ct.byref(grid), _ip(nkv), psi_k.shape[1], int(n_occ),
+                                     _dev(psi_k, "psi_k", p), _dp(eps_k), float(mu), len(tau), _dp(tau), _dp(C),
+                                     len(gv), _ip(gv), p, int(r_block), _dev(chi_w, "chi_w", p), _stream()), ctx)

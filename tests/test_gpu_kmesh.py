@@ -1,0 +1,76 @@
+"""chi0 on a Gamma-centred k mesh (gw_chi0_omega_kmesh) against the k-mesh
+oracle: the stripe route of Sec. II.A (Eqs. FFT_G1, FFT_G2), pinned to the
+Gamma-point chi of the supercell in tests/test_oracle_kmesh.py, followed by
+the cosine transform (Eq. CTX)."""
+import numpy as np
+import pytest
+
+from oracle import chi as ochi
+from oracle import grids as ogrids
+from oracle import gvec as ogv
+from oracle import kmesh as okm
+from paper_1607_02859_gb300 import gw, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+TOL = {"fp64": 1e-12, "fp32": 1e-6, "f16x3": 5e-6}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import os
+    if not os.path.exists(gw.LIB_PATH):
+        from paper_1607_02859_gb300 import build
+        build.build()
+    c = gw.Context(0)
+    yield c
+    c.close()
+
+
+def reference(p, gv, C):
+    per_tau = np.array([okm.chi_q_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, t, p.n, p.nk, p.lattice, gv) for t in p.tau])
+    return np.stack([ochi.ct(per_tau[:, q], C) for q in range(p.n_k)])        # [N_q][n][n_chi][n_chi]
+
+
+CASES = {
+    "6^3_k2x2x2": dict(n=(6, 6, 6), a=(6.0, 6.5, 7.0), nk=(2, 2, 2), n_occ=4, n_unocc=20, n_tau=4, seed=61, n_chi=None),
+    "4^3_k3x3x3_partial": dict(n=(4, 4, 4), a=(5.0, 5.5, 6.0), nk=(3, 3, 3), n_occ=3, n_unocc=13, n_tau=4, seed=62,
+                               n_chi=40),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    kw = dict(CASES[request.param])
+    p = inputs.kmesh_problem(**kw)
+    gv = ogv.g_set(p.n, p.n_chi)
+    mats = ogrids.transform_matrices(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
+    return request.param, p, gv, mats, reference(p, gv, mats["C"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3", "fp64"])
+def test_chi0_kmesh(ctx, case, prec):
+    name, p, gv, mats, ref = case
+    grid = gw.make_grid(p.n, p.lattice)
+    dt = gw.cdtype(prec)
+    psi = torch.from_numpy(np.ascontiguousarray(p.psi_k)).to("cuda", dtype=dt)
+    out = torch.zeros((p.n_k, len(p.tau), p.n_chi, p.n_chi), dtype=dt, device="cuda")
+    gw.chi0_omega_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, p.mu, p.tau, mats["C"], gv, prec, out)
+    got = out.cpu().numpy().astype(np.complex128)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    per_q = [np.linalg.norm(got[q] - ref[q]) / np.linalg.norm(ref[q]) for q in range(p.n_k)]
+    print("%s %s: %.2e (worst q %.2e)" % (name, prec, err, max(per_q)))
+    assert err < TOL[prec] and max(per_q) < 3 * TOL[prec]
+
+
+def test_kmesh_argument_checks(ctx, case):
+    name, p, gv, mats, ref = case
+    grid = gw.make_grid(p.n, p.lattice)
+    psi = torch.from_numpy(np.ascontiguousarray(p.psi_k)).to("cuda", dtype=torch.complex64)
+    out = torch.zeros((p.n_k, len(p.tau), p.n_chi, p.n_chi), dtype=torch.complex64, device="cuda")
+    with pytest.raises(gw.GwError):       # a supercell grid the library does not compile (6 x 5 = 30)
+        gw.chi0_omega_kmesh(ctx, grid, (1, 1, 5), psi, p.eps_k, p.n_occ, p.mu, p.tau, mats["C"], gv, "fp32", out)
+    with pytest.raises(gw.GwError):       # mu outside a gap
+        gw.chi0_omega_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, 5.0, p.tau, mats["C"], gv, "fp32", out)
