@@ -296,6 +296,31 @@ gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, i
                               const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
                               gw_prec prec, int r_block, void* chi_w, void* stream);
 
+/* ---------------------------------------------------------------- plans
+ * gw_chi0_omega split into a set-up and a launch, for callers that replay the
+ * same chi0 evaluation (serving) or capture it in a CUDA graph: the launch
+ * issues kernels and device-side memsets only, with no host-device copy and no
+ * synchronisation.  The paper has no counterpart. */
+typedef struct gw_chi0_plan gw_chi0_plan;
+/* Everything of gw_chi0_omega but psi and chi_w: validates, computes the
+ * tables on the host, copies them to a device buffer the plan owns
+ * (synchronous) and grows ctx's arena to what a launch needs.  Plans made from
+ * one context share its arena: launch them in order (one stream or one graph),
+ * and do not interleave other calls on that context between a launch and its
+ * gw_chi0_plan_status. */
+gw_status gw_chi0_plan_create(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const double* eps_h,
+                              double mu, int n, const double* tau_h, const double* C_h, int n_chi,
+                              const int32_t* fft_index_h, gw_prec prec, int r_block, gw_chi0_plan** out);
+/* The kernels of gw_chi0_omega for this plan on `stream`: psi [n_b][N_r] and
+ * chi_w [n][n_chi][n_chi] on the device, as for gw_chi0_omega.  Asynchronous;
+ * pointers are read at launch (a captured graph keeps those of the capture). */
+gw_status gw_chi0_plan_launch(gw_chi0_plan* plan, const void* psi, void* chi_w, void* stream);
+/* Waits for `stream` and reports a time-out recorded by the tensor-core
+ * kernels of the last launch (GW_ERR_TIMEOUT). */
+gw_status gw_chi0_plan_status(gw_chi0_plan* plan, void* stream);
+/* Frees the plan's tables (synchronises the device). */
+gw_status gw_chi0_plan_destroy(gw_chi0_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -496,7 +496,7 @@ static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, b
 // same psi.
 static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
                      int r0, int n_rows, gw_prec prec, int mode, void* out0, void* out1, void* scratch, bool prep_b,
-                     cudaStream_t st) {
+                     cudaStream_t st, const float* sk_dev = nullptr, int* status_dev = nullptr) {
   const uint32_t fmt = prec == GW_BF16X3 ? 1u : 0u;
   const Layout L = layout(n_b, n_occ);
   gw_status rc;
@@ -504,7 +504,8 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
   Carver cv(scratch);
   unsigned int* dmax = cv.take<unsigned int>(64);
   int* dexp = reinterpret_cast<int*>(dmax + 1);
-  int* status = reinterpret_cast<int*>(dmax + 2);
+  // time-out status: in the scratch, or in a word the caller owns (kept past later uses of the scratch)
+  int* status = status_dev ? status_dev : reinterpret_cast<int*>(dmax + 2);
   float* dsk = cv.take<float>(n_b);
   uint16_t* bhi = cv.take<uint16_t>((size_t)2 * g.nr * L.kpad);
   uint16_t* blo = cv.take<uint16_t>((size_t)2 * g.nr * L.kpad);
@@ -515,12 +516,19 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
     if (!out0) out0 = tmp;
     if (!out1) out1 = tmp;
   }
-  std::vector<float> skf(gs.s.begin(), gs.s.end());
-  if ((rc = upload(ctx, dsk, skf.data(), sizeof(float) * n_b, st))) return rc;
+  // per-band factors: uploaded here, or already on the device (sk_dev: no host-to-device copy in this call)
+  const float* sk = sk_dev;
+  if (!sk) {
+    std::vector<float> skf(gs.s.begin(), gs.s.end());
+    if ((rc = upload(ctx, dsk, skf.data(), sizeof(float) * n_b, st))) return rc;
+    sk = dsk;
+  }
   const dim3 tb(32, 8);
   const int slots = L.kpad / 2;
   if (prep_b) {
     if ((rc = cuda_check(ctx, cudaMemsetAsync(dmax, 0, 64 * sizeof(unsigned int), st), "memset"))) return rc;
+    if (status_dev && (rc = cuda_check(ctx, cudaMemsetAsync(status_dev, 0, 2 * sizeof(int), st), "memset")))
+      return rc;
     const size_t nel = (size_t)n_b * g.nr;
     maxabs_kernel<<<std::min<size_t>((nel + 255) / 256, (size_t)ctx->num_sms * 8), 256, 0, st>>>(
         static_cast<const float2*>(psi), nel, dmax);
@@ -529,10 +537,10 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
     if ((rc = launch_check(ctx, "exponent_kernel"))) return rc;
     const dim3 gbB((g.nr + 31) / 32, (slots + 31) / 32);
     if (fmt == 0)
-      prep_kernel<true, 0><<<gbB, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, 0, g.nr, dsk, dexp,
+      prep_kernel<true, 0><<<gbB, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, 0, g.nr, sk, dexp,
                                                 L.k_occ_pad, L.k_un_x, L.kpad, bhi, blo);
     else
-      prep_kernel<true, 1><<<gbB, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, 0, g.nr, dsk, dexp,
+      prep_kernel<true, 1><<<gbB, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, 0, g.nr, sk, dexp,
                                                 L.k_occ_pad, L.k_un_x, L.kpad, bhi, blo);
     if ((rc = launch_check(ctx, "prep_kernel(B)"))) return rc;
   } else {
@@ -540,10 +548,10 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
   }
   const dim3 gbA((n_rows + 31) / 32, (slots + 31) / 32);
   if (fmt == 0)
-    prep_kernel<false, 0><<<gbA, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, r0, n_rows, dsk, dexp,
+    prep_kernel<false, 0><<<gbA, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, r0, n_rows, sk, dexp,
                                                L.k_occ_pad, L.k_un_x, L.kpad, ahi, alo);
   else
-    prep_kernel<false, 1><<<gbA, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, r0, n_rows, dsk, dexp,
+    prep_kernel<false, 1><<<gbA, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, r0, n_rows, sk, dexp,
                                                L.k_occ_pad, L.k_un_x, L.kpad, ahi, alo);
   if ((rc = launch_check(ctx, "prep_kernel(A)"))) return rc;
   CUtensorMap mah, mal, mbh, mbl;
@@ -602,8 +610,19 @@ gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, cons
 }
 
 gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
-                      int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st) {
-  return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 0, chi, nullptr, scratch, prep_b, st);
+                      int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st,
+                      const float* sk_dev, int* status_dev) {
+  return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 0, chi, nullptr, scratch, prep_b, st, sk_dev,
+                 status_dev);
+}
+
+gw_status tc_check_status(gw_ctx* ctx, const int* status_dev, cudaStream_t st) {
+  int hs[2] = {0, 0};
+  gw_status rc;
+  if ((rc = cuda_check(ctx, cudaMemcpyAsync(hs, status_dev, sizeof(hs), cudaMemcpyDeviceToHost, st), "status"))) return rc;
+  if ((rc = cuda_check(ctx, cudaStreamSynchronize(st), "tensor-core GEMM"))) return rc;
+  if (hs[0]) return fail(ctx, GW_ERR_TIMEOUT, "tensor-core pipeline wait timed out (role " + std::to_string(hs[1]) + ")");
+  return GW_OK;
 }
 
 gw_status tc_check(gw_ctx* ctx, void* scratch, cudaStream_t st) { return tc::check_status(ctx, scratch, st); }

@@ -17,8 +17,13 @@ gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, cons
                         const GreenScales& gs, int r0, int n_rows, gw_prec prec, void* g_occ, void* g_unocc,
                         void* scratch, bool prep_b, cudaStream_t st);
 // chi rows = -2 G_occ o conj(G_unocc) with both tiles accumulated in tensor memory.
+// sk_dev: the per-band factors gs.s already on the device as FP32 (then the
+// call copies nothing from the host).
 gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
-                      int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st);
+                      int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st,
+                      const float* sk_dev = nullptr, int* status_dev = nullptr);
+// As tc_check for a status word the caller owns (status_dev of tc_chi_rows).
+gw_status tc_check_status(gw_ctx* ctx, const int* status_dev, cudaStream_t st);
 // Synchronises and reports a time-out of the tensor-core pipeline waits
 // (GW_ERR_TIMEOUT) recorded in `scratch` since its last prep_b call.
 gw_status tc_check(gw_ctx* ctx, void* scratch, cudaStream_t st);

@@ -26,7 +26,8 @@ STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "G
 EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes", "gw_ctx_reserve",
            "gw_ctx_set_timing", "gw_ctx_kernel_stats", "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
-           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh"]
+           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh",
+           "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy"]
 
 
 class GwError(RuntimeError):
@@ -70,6 +71,10 @@ _SIGS = {
     "gw_tau_to_omega": (_I, [_P, _I, _I, _DP, ct.c_size_t, _I, _P, _P, _P]),
     "gw_screen_W": (_I, [_P, _G, _I, _IP, _I, _I, _P, _P, _DP, _P]),
     "gw_screen_W_refine": (_I, [_P, _G, _I, _IP, _I, _I, _I, _P, _P, _DP, _P]),
+    "gw_chi0_plan_create": (_I, [_P, _G, _I, _I, _DP, ct.c_double, _I, _DP, _DP, _I, _IP, _I, _I, ct.POINTER(_P)]),
+    "gw_chi0_plan_launch": (_I, [_P, _P, _P, _P]),
+    "gw_chi0_plan_status": (_I, [_P, _P]),
+    "gw_chi0_plan_destroy": (_I, [_P]),
     "gw_chi0_omega_kmesh": (_I, [_P, _G, _IP, _I, _I, _P, _DP, ct.c_double, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                            _DP, _DP, _DP, _I, _DP, _P]),
@@ -356,3 +361,40 @@ def chi0_omega_kmesh(ctx, grid, nk, psi_k, eps_k, n_occ, mu, tau, C, gvec, prec,
     _check(lib().gw_chi0_omega_kmesh(ctx.handle, ct.byref(grid), _ip(nkv), psi_k.shape[1], int(n_occ),
                                      _dev(psi_k, "psi_k", p), _dp(eps_k), float(mu), len(tau), _dp(tau), _dp(C),
                                      len(gv), _ip(gv), p, int(r_block), _dev(chi_w, "chi_w", p), _stream()), ctx)
+
+
+class Chi0Plan:
+    """gw_chi0_plan: the chi0 chain set up once; launch() issues only kernels
+    (no host-device copy, no synchronisation), so it can be captured in a CUDA
+    graph.  Plans of one Context share its scratch arena: launch them in order."""
+
+    def __init__(self, ctx, grid, n_b, eps, n_occ, mu, tau, C, fft_index, prec, r_block=0):
+        self.ctx = ctx
+        self.prec = prec
+        self.n = len(tau)
+        self._keep = (grid, _f64(eps), _f64(tau), _f64(C), _i32(fft_index))
+        h = _P()
+        _check(lib().gw_chi0_plan_create(ctx.handle, ct.byref(grid), int(n_b), int(n_occ), _dp(self._keep[1]),
+                                         float(mu), self.n, _dp(self._keep[2]), _dp(self._keep[3]),
+                                         len(self._keep[4]), _ip(self._keep[4]), prec_of(prec), int(r_block),
+                                         ct.byref(h)), ctx)
+        self.handle = h
+
+    def launch(self, psi, chi_w):
+        p = prec_of(self.prec)
+        _check(lib().gw_chi0_plan_launch(self.handle, _dev(psi, "psi", p), _dev(chi_w, "chi_w", p), _stream()),
+               self.ctx)
+
+    def status(self):
+        _check(lib().gw_chi0_plan_status(self.handle, _stream()), self.ctx)
+
+    def close(self):
+        if self.handle:
+            lib().gw_chi0_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
