@@ -145,6 +145,21 @@ def measured_traffic(workload, prec, family):
     return rec["bytes_per_launch"]
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """The largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, flops_per_step, steps, seconds):
+    """Whole-job TFLOP/s: every rank's work over the slowest rank's time."""
+    return world * flops_per_step * steps / seconds / 1e12
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -304,13 +319,10 @@ def main():
     torch.cuda.synchronize()
     launches = (ctx.launches - l0) // max(args.steps, 1)
     clocks = sampler.stop()
-    t_dev = float(np.sum(times))
+    t_dev = max_over_ranks(float(np.sum(times)), dist)
     if dist is not None:
-        t = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
         dist.barrier()
-    value = world * fl["total"] * args.steps / t_dev / 1e12
+    value = job_value(world, fl["total"], args.steps, t_dev)
 
     # per-stage breakdown and the dominant stage's roofline (same stream, CUDA events)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -375,12 +387,8 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1) / 1e3)
-    t_e2e = float(np.sum(e_times)) if e_times else float("nan")
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * fl["total"] * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
+    t_e2e = max_over_ranks(float(np.sum(e_times)) if e_times else float("nan"), dist)
+    e2e = {"value": job_value(world, fl["total"], args.steps, t_e2e), "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(psi_h.numel() * psi_h.element_size()),
            "d2h_bytes_per_step": int(len(p.bands) * (3 * n_tau + N_REAL) * 16)}
 

@@ -123,7 +123,7 @@ template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C
 // sin/cos of 2 pi m / n from their Taylor series (argument reduced to [-pi, pi]);
 // 40 terms put the truncation far below double rounding.  Only used for FFT
 // twiddle constants that the compiler folds into immediates.
-__host__ __device__ constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double kPi = 3.14159265358979323846264338327950288;
 __host__ __device__ constexpr double taylor_sin(double x) {
   double term = x, sum = x;
   for (int k = 1; k < 40; ++k) {

@@ -21,3 +21,44 @@ def test_flop_model_at_the_bench_size():
     fl = bench.flop_model(13824, 1024, 16, 13824, 8)
     assert abs(fl["green"] - 2 * 8 * 13824 ** 2 * 1024 * 16) < 1
     assert abs(fl["dyson"] - 4 * 13824 ** 3 * 16) < 1
+
+
+def _rank(rank, world, port, out_dir):
+    import os
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    seconds = [2.0, 5.0][rank]                       # the slowest rank decides the job's time
+    t = bench.max_over_ranks(seconds, dist, device="cpu")
+    v = bench.job_value(world, 1e12, 3, t)
+    with open(os.path.join(out_dir, "r%d" % rank), "w") as f:
+        f.write("%r %r" % (t, v))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replicas_timing_over_two_gloo_ranks(tmp_path):
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.spawn(_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        t, v = (float(x) for x in (tmp_path / ("r%d" % r)).read_text().split())
+        assert t == 5.0
+        assert abs(v - 2 * 1e12 * 3 / 5.0 / 1e12) < 1e-12      # all ranks' work over the slowest time
+    assert bench.max_over_ranks(7.0) == 7.0
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                        "gamma_toy", "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and r.stdout.strip() == ""
