@@ -107,3 +107,49 @@ def supercell_orbitals(psi_k, eps_k, n_occ, n, nk):
 def supercell_gvecs(gvecs, nk):
     """Integer triples m = k + nk g of the supercell for every q (outer) and g (inner)."""
     return np.concatenate([q[None, :] + np.asarray(nk)[None, :] * np.asarray(gvecs) for q in k_list(nk)])
+
+
+def w_stripe(w_q, n, nk, lattice, gvecs):
+    """W~(r, R') on the stripe from W~_q(g, g') for every q:
+    (1/Omega_S) sum_q sum_{g,g'} exp(+i(q+g).r) W~_q(g,g') exp(-i(q+g').R')
+    (Eq. FFTW on the supercell, whose W~ is block-diagonal in q)."""
+    n = np.asarray(n)
+    nk = np.asarray(nk)
+    ns = n * nk
+    vol_s = abs(np.linalg.det(lattice)) * int(np.prod(nk))
+    i_cell = np.stack(np.meshgrid(*[np.arange(d) for d in n], indexing="ij"), -1).reshape(-1, 3)
+    i_sup = np.stack(np.meshgrid(*[np.arange(d) for d in ns], indexing="ij"), -1).reshape(-1, 3)
+    out = np.zeros((len(i_cell), len(i_sup)), dtype=np.complex128)
+    for qi, q in enumerate(k_list(nk)):
+        m = q[None, :] + nk[None, :] * np.asarray(gvecs)
+        p_row = np.exp(2j * np.pi * i_cell @ (m / ns).T)       # exp(+i(q+g).r)   [N_r][N_chi]
+        p_col = np.exp(-2j * np.pi * (m / ns) @ i_sup.T)       # exp(-i(q+g').R') [N_chi][N_S]
+        out += p_row @ w_q[qi] @ p_col
+    return out / vol_s
+
+
+def bloch_extend(psi, kv, n, nk):
+    """psi_nk(r + L) = exp(i k.L) psi_nk(r) on the supercell grid (cell normalisation)."""
+    pos = supercell_index(n, nk)
+    out = np.zeros(pos.size, dtype=np.complex128)
+    for li, l in enumerate(k_list(nk)):
+        out[pos[li]] = np.exp(2j * np.pi * np.sum(np.asarray(kv) * l / np.asarray(nk))) * psi
+    return out
+
+
+def sigma_k_tau(psi_k, eps_k, n_occ, mu, tau, w_s, n, nk, lattice, bands_nk):
+    """(Sigma_unocc_nk(tau), Sigma_occ_nk(-tau)) for the (band, k index) pairs on
+    the stripe (Eqs. Sigma_rr, Sigma_occ_reduce first term, with Bloch orbitals):
+        Sigma_unocc = +dV^2 sum_{r in C} sum_{R' in S} psi*_nk(r) G_unocc(r,R') W~(r,R') psi_nk(R'),
+    likewise occupied with a minus sign; real parts."""
+    dv = abs(np.linalg.det(lattice)) / int(np.prod(n))
+    go, gu = green_stripe(psi_k, eps_k, n_occ, mu, tau, n, nk)
+    ks = k_list(nk)
+    su = np.empty(len(bands_nk))
+    so = np.empty(len(bands_nk))
+    for i, (b, k) in enumerate(bands_nk):
+        row = psi_k[k, b]
+        col = bloch_extend(row, ks[k], n, nk)
+        su[i] = (dv * dv * (row.conj() @ ((gu * w_s) @ col))).real
+        so[i] = -(dv * dv * (row.conj() @ ((go * w_s) @ col))).real
+    return su, so

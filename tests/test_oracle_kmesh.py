@@ -55,3 +55,41 @@ def test_chi_q_hermitian_and_negative_semidefinite():
     for c in cq:
         assert np.linalg.norm(c - c.conj().T) < 1e-12 * np.linalg.norm(c)
         assert np.linalg.eigvalsh(0.5 * (c + c.conj().T)).max() < 1e-12 * np.linalg.norm(c)
+
+
+def test_sigma_stripe_equals_supercell_gamma_point():
+    from oracle import sigma as osg
+    p = inputs.kmesh_problem(n=(4, 4, 4), a=(5.0, 5.5, 6.0), nk=(2, 1, 2), n_occ=3, n_unocc=9, n_tau=2, seed=55)
+    gv = ogv.g_set(p.n, 24)
+    rng = np.random.default_rng(56)
+    w_q = []
+    for _ in range(p.n_k):                       # Hermitian W~_q of moderate size
+        a = rng.standard_normal((len(gv), len(gv))) + 1j * rng.standard_normal((len(gv), len(gv)))
+        w_q.append(-(a @ a.conj().T) * 0.05)
+    w_q = np.array(w_q)
+    tau = p.tau[0]
+    w_s = okm.w_stripe(w_q, p.n, p.nk, p.lattice, gv)
+    bands = [(2, 0), (3, 1), (4, 3)]
+    su, so = okm.sigma_k_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, w_s, p.n, p.nk, p.lattice, bands)
+    # the same system as a Gamma-point problem of the supercell
+    psi_s, eps_s, no_s = okm.supercell_orbitals(p.psi_k, p.eps_k, p.n_occ, p.n, p.nk)
+    ns = tuple(np.asarray(p.n) * np.asarray(p.nk))
+    lat_s = p.lattice * np.asarray(p.nk)[:, None]
+    gs = okm.supercell_gvecs(gv, p.nk)
+    nc = len(gv)
+    w_full = np.zeros((len(gs), len(gs)), dtype=np.complex128)
+    for q in range(p.n_k):
+        w_full[q * nc:(q + 1) * nc, q * nc:(q + 1) * nc] = w_q[q]
+    pm = ogv.phase_matrix(gs, ns, -1.0)                     # exp(-i Gs.R)
+    w_rr = pm.conj().T @ w_full @ pm / abs(np.linalg.det(lat_s))
+    # supercell band index of (b, k): occupied (k outer, b inner), then unoccupied
+    def sband(b, k):
+        return k * p.n_occ + b if b < p.n_occ else p.n_k * p.n_occ + k * (p.n_b - p.n_occ) + (b - p.n_occ)
+    dv = abs(np.linalg.det(p.lattice)) / p.n_r
+    ref_u, ref_o = osg.sigma_tau(psi_s, eps_s, no_s, p.mu, tau, w_rr, [sband(b, k) for b, k in bands], dv)
+    scale = max(np.abs(ref_u).max(), np.abs(ref_o).max())
+    assert np.abs(su - ref_u).max() < 1e-11 * scale
+    assert np.abs(so - ref_o).max() < 1e-11 * scale
+    # and the stripe of W~ is the supercell's W~ restricted to rows in the cell
+    pos0 = okm.supercell_index(p.n, p.nk)[0]
+    assert np.linalg.norm(w_s - w_rr[pos0]) < 1e-12 * np.linalg.norm(w_rr)
