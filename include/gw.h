@@ -296,6 +296,25 @@ gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, i
                               const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
                               gw_prec prec, int r_block, void* chi_w, void* stream);
 
+/* Diagonal self-energy of Bloch states on the k mesh of gw_chi0_omega_kmesh:
+ * the space-time route of gw_sigma_diag on the supercell stripe.  For every
+ * tau_j, W~(r, R') = (1/Omega_S) sum_q sum_{g,g'} exp(i(q+g).r) W~_q(g,g') exp(-i(q+g').R')
+ * (Eq. FFTW on the supercell, whose W~ is block-diagonal in q), G_occ / G_unocc
+ * on the stripe as for chi0, and
+ *   Sigma_unocc_nk(tau) = +dV^2 sum_{r in C} sum_{R' in S} psi*_nk(r) G_unocc(r,R') W~(r,R') psi_nk(R')
+ *   Sigma_occ_nk(-tau)  = -dV^2 ... G_occ ...,   psi_nk(r'+L) = exp(i k.L) psi_nk(r'),
+ * then the even/odd split, CT + ST and Thiele continuation of gw_sigma_diag.
+ * bk_h [n_n][2]: (band, k index) pairs; w_tau [N_k][n][n_chi][n_chi]:
+ * W~_q(g, g', tau_j) for every q (e.g. gw_screen_W per q with the supercell G
+ * triples q + nk g, then gw_tau_to_omega); the other arguments and outputs as
+ * for gw_chi0_omega_kmesh and gw_sigma_diag (outputs per pair).  Synchronous. */
+gw_status gw_sigma_diag_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_b, int n_occ,
+                              const void* psi_k, const double* eps_k_h, double mu, const int32_t* bk_h, int n_n,
+                              int n, const double* tau_h, const double* omega_h, const double* C_h,
+                              const double* S_h, const void* w_tau, int n_chi, const int32_t* gvec_h,
+                              gw_prec prec, double* sigma_tau_h, double* sigma_iw_h, const double* w_real_h,
+                              int n_real, double* sigma_real_h, void* stream);
+
 /* ---------------------------------------------------------------- plans
  * gw_chi0_omega split into a set-up and a launch, for callers that replay the
  * same chi0 evaluation (serving) or capture it in a CUDA graph: the launch

@@ -14,6 +14,18 @@ gw_status launch_row_fft(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int mode,
                          long lda, void* out, long ldo, const int* map, int n_chi, int n_rows, double scale,
                          cudaStream_t st, const int* inv = nullptr, void* tmp = nullptr);
 bool row_two_pass(const GridInfo& g, gw_prec prec);
+
+// gw_sigma.cu: the Sigma contraction over rows of G_occ, G_unocc, W~ (length
+// nr, leading dimension ld) against psi_n (rows of length nr; the row's own
+// value read from psi_row [.][ld_row] if given, else from psi), and the finish
+// (even/odd split, CT + ST, Thiele, results to the host).
+gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wrr, const void* go, const void* gu, long ld,
+                                int nr, int rows, const void* psi, const int* bands, int n_n, int r0, double coef,
+                                double* acc_u, double* acc_o, int acc_stride, cudaStream_t st,
+                                const void* psi_row = nullptr, long ld_row = 0);
+gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* tab, int n_real, double2* out,
+                       int* stat, const int32_t* labels, double* sigma_tau_h, double* sigma_iw_h,
+                       double* sigma_real_h, cudaStream_t s);
 gw_status launch_col_plane(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, void* buf, long ld, int ncols,
                            double scale, cudaStream_t st);
 gw_status launch_col_line(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int dir, int variant, const void* in,

@@ -21,6 +21,8 @@
 // Then per slab: exp(-i q.r) on the block of each q, the (i2, i3) column planes;
 // last, per q, the i1 column pass fused with the cosine transform.
 #include <cmath>
+#include <cstring>
+#include <type_traits>
 
 #include "gw_kernels.h"
 #include "gw_tc.h"
@@ -32,12 +34,14 @@ constexpr int kMaxK = 64;   // k points per mesh (4 x 4 x 4)
 // One row r of the block and 32 consecutive r' per CTA: the N_k values of
 // G_occ,k and G_unocc,k are staged in shared memory, then every (L, r') output
 // takes its k sum with the phase table ph[k][L] = exp(-i k.L) / N_k.
-template <typename T>
+// PRODUCT: out = -2 G_occ conj(G_unocc) on the stripe; else out = G_occ and out2 = G_unocc.
+template <typename T, bool PRODUCT>
 __global__ void __launch_bounds__(256) stripe_chi_kernel(const typename cpx<T>::t* __restrict__ go,
                                                          const typename cpx<T>::t* __restrict__ gu, long k_stride,
                                                          int nr, const typename cpx<T>::t* __restrict__ ph, int n_k,
                                                          int n1, int n2, int n3, int nk1, int nk2, int nk3,
-                                                         typename cpx<T>::t* __restrict__ out, long ldo) {
+                                                         typename cpx<T>::t* __restrict__ out,
+                                                         typename cpx<T>::t* __restrict__ out2, long ldo) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* so = reinterpret_cast<C*>(smem_raw);            // [n_k][32]
@@ -68,14 +72,19 @@ __global__ void __launch_bounds__(256) stripe_chi_kernel(const typename cpx<T>::
     const int i1 = rp / (n2 * n3), rem = rp - i1 * n2 * n3, i2 = rem / n3, i3 = rem - i2 * n3;
     const int l1 = l / (nk2 * nk3), lr = l - l1 * nk2 * nk3, l2 = lr / nk3, l3 = lr - l2 * nk3;
     const long pos = ((long)(i1 + n1 * l1) * ns2 + (i2 + n2 * l2)) * ns3 + (i3 + n3 * l3);
-    out[row * ldo + pos] = cscale(cmulc(a, b), T(-2));
+    if (PRODUCT) {
+      out[row * ldo + pos] = cscale(cmulc(a, b), T(-2));
+    } else {
+      out[row * ldo + pos] = a;
+      out2[row * ldo + pos] = b;
+    }
   }
 }
 
-// slab[r][q*n_chi + j] *= exp(-i q.r) for every q of the mesh (r on the cell grid).
+// slab[r][q*n_chi + j] *= exp(sgn i q.r)
 template <typename T>
 __global__ void __launch_bounds__(256) q_phase_kernel(typename cpx<T>::t* slab, long ld, int n_chi, int n1, int n2,
-                                                      int n3, int nk1, int nk2, int nk3) {
+                                                      int n3, int nk1, int nk2, int nk3, double sgn) {
   const long r = blockIdx.x;
   const int i1 = (int)(r / (n2 * n3)), rem = (int)(r - (long)i1 * n2 * n3), i2 = rem / n3, i3 = rem - i2 * n3;
   const int n_k = nk1 * nk2 * nk3;
@@ -85,7 +94,7 @@ __global__ void __launch_bounds__(256) q_phase_kernel(typename cpx<T>::t* slab, 
     double f = (double)q1 * i1 / (nk1 * n1) + (double)q2 * i2 / (nk2 * n2) + (double)q3 * i3 / (nk3 * n3);
     f -= floor(f);
     double s, c;
-    sincospi(-2.0 * f, &s, &c);
+    sincospi(2.0 * sgn * f, &s, &c);
     const T cr = T(c), ci = T(s);
     auto* p = slab + r * ld + (long)q * n_chi;
     for (int j = threadIdx.x; j < n_chi; j += blockDim.x) {
@@ -95,20 +104,40 @@ __global__ void __launch_bounds__(256) q_phase_kernel(typename cpx<T>::t* slab, 
   }
 }
 
-}  // namespace gw
+// Orbitals of the requested (band, k) pairs: ext[i][pos(r', L)] = exp(i k.L) psi_bk(r')
+// over the supercell grid, and row[i][r'] = psi_bk(r') on the cell grid.
+template <typename T>
+__global__ void __launch_bounds__(256) bloch_extend_kernel(const typename cpx<T>::t* __restrict__ psi_k, long k_stride,
+                                                           int nr, const int* __restrict__ bk, int n1, int n2, int n3,
+                                                           int nk1, int nk2, int nk3, typename cpx<T>::t* __restrict__ ext,
+                                                           typename cpx<T>::t* __restrict__ row) {
+  const int rp = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = blockIdx.y, i = blockIdx.z;
+  if (rp >= nr) return;
+  const int b = bk[2 * i], k = bk[2 * i + 1];
+  const auto v = psi_k[(long)k * k_stride + (long)b * nr + rp];
+  const int k1 = k / (nk2 * nk3), kr = k - k1 * nk2 * nk3, k2 = kr / nk3, k3 = kr - k2 * nk3;
+  const int l1 = l / (nk2 * nk3), lr = l - l1 * nk2 * nk3, l2 = lr / nk3, l3 = lr - l2 * nk3;
+  double f = (double)k1 * l1 / nk1 + (double)k2 * l2 / nk2 + (double)k3 * l3 / nk3;   // k.L / 2 pi
+  f -= floor(f);
+  double sn, cs;
+  sincospi(2.0 * f, &sn, &cs);
+  const T c = T(cs), s = T(sn);
+  const int i1 = rp / (n2 * n3), rem = rp - i1 * n2 * n3, i2 = rem / n3, i3 = rem - i2 * n3;
+  const long ns = (long)n1 * nk1 * n2 * nk2 * n3 * nk3;
+  const long pos = ((long)(i1 + n1 * l1) * (n2 * nk2) + (i2 + n2 * l2)) * (n3 * nk3) + (i3 + n3 * l3);
+  ext[(long)i * ns + pos] = mk(v.x * c - v.y * s, v.x * s + v.y * c);
+  if (l == 0) row[(long)i * nr + rp] = v;
+}
 
-using namespace gw;
-
-extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_b, int n_occ,
-                                         const void* psi_k, const double* eps_k_h, double mu, int n,
-                                         const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
-                                         gw_prec prec, int r_block, void* chi_w, void* stream) {
-  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
-  GridInfo g;
-  gw_status st = grid_info(ctx, grid, &g);
+// The supercell grid of a k mesh, and the index maps of the cell G set (cell
+// grid) and of the supercell G set {q + g} (q outer, g inner) on the supercell grid.
+static gw_status kmesh_grids(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_chi, const int32_t* gvec_h,
+                             GridInfo* g, GridInfo* gs, std::vector<int>& map, std::vector<int>& inv,
+                             std::vector<int>& smap, std::vector<int>& sinv) {
+  gw_status st = grid_info(ctx, grid, g);
   if (st) return st;
-  if (!nk || !psi_k || !eps_k_h || !tau_h || !C_h || !gvec_h || !chi_w) return fail(ctx, GW_ERR_ARG, "NULL pointer");
-  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  if (!nk || !gvec_h) return fail(ctx, GW_ERR_ARG, "NULL pointer");
   for (int d = 0; d < 3; ++d)
     if (nk[d] < 1) return fail(ctx, GW_ERR_SHAPE, "k mesh dimensions must be >= 1");
   const int n_k = nk[0] * nk[1] * nk[2];
@@ -118,19 +147,11 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
     sgrid.n[d] = grid->n[d] * nk[d];
     for (int e = 0; e < 3; ++e) sgrid.lattice[3 * d + e] = grid->lattice[3 * d + e] * nk[d];
   }
-  GridInfo gs;
-  if ((st = grid_info(ctx, &sgrid, &gs))) return st;
-  if (!grid_supported(g.n1, g.n2, g.n3) || !grid_supported(gs.n1, gs.n2, gs.n3))
+  if ((st = grid_info(ctx, &sgrid, gs))) return st;
+  if (!grid_supported(g->n1, g->n2, g->n3) || !grid_supported(gs->n1, gs->n2, gs->n3))
     return fail(ctx, GW_ERR_UNSUPPORTED, "no kernels compiled for the cell or the supercell grid");
-  if (n_b < 2 || n_b > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 2 <= n_b <= N_r");
-  for (int k = 0; k < n_k; ++k)
-    if ((st = check_energies(ctx, eps_k_h + (size_t)k * n_b, n_b, n_occ, mu))) return st;
-  if (n < 1 || n > 32) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
-  for (int j = 0; j < n; ++j)
-    if (!(tau_h[j] > 0)) return fail(ctx, GW_ERR_ARG, "tau must be > 0");
-  if (n_chi < 1 || n_chi > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_chi <= N_r");
-  // cell G set -> cell grid positions, supercell G set {q + g} -> supercell grid positions
-  const int cn[3] = {g.n1, g.n2, g.n3}, sn[3] = {gs.n1, gs.n2, gs.n3};
+  if (n_chi < 1 || n_chi > g->nr) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_chi <= N_r");
+  const int cn[3] = {g->n1, g->n2, g->n3}, sn[3] = {gs->n1, gs->n2, gs->n3};
   std::vector<int32_t> fidx(n_chi), sidx((size_t)n_k * n_chi);
   for (int j = 0; j < n_chi; ++j) {
     int p = 0;
@@ -152,9 +173,89 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
       sidx[(size_t)q * n_chi + j] = p;
     }
   }
+  if ((st = index_maps(ctx, *g, fidx.data(), n_chi, map, inv))) return st;
+  return index_maps(ctx, *gs, sidx.data(), n_k * n_chi, smap, sinv);
+}
+
+// exp(-i k.L) / N_k for every k (rows) and L (columns), k.L / 2 pi = sum_d k_d l_d / nk_d.
+static std::vector<double> kl_phases(const int* nk) {
+  const int n_k = nk[0] * nk[1] * nk[2];
+  std::vector<double> ph(2 * (size_t)n_k * n_k);
+  const long den = (long)nk[0] * nk[1] * nk[2];
+  for (int k = 0; k < n_k; ++k)
+    for (int l = 0; l < n_k; ++l) {
+      const int kv[3] = {k / (nk[1] * nk[2]), (k / nk[2]) % nk[1], k % nk[2]};
+      const int lv[3] = {l / (nk[1] * nk[2]), (l / nk[2]) % nk[1], l % nk[2]};
+      long num = 0;
+      for (int d = 0; d < 3; ++d) num += (long)kv[d] * lv[d] * (den / nk[d]);
+      const double a = -2.0 * M_PI * (double)(num % den) / (double)den;
+      ph[2 * ((size_t)k * n_k + l)] = std::cos(a) / n_k;
+      ph[2 * ((size_t)k * n_k + l) + 1] = std::sin(a) / n_k;
+    }
+  return ph;
+}
+
+static gw_status upload_phases(gw_ctx* ctx, void* dst, const std::vector<double>& ph, gw_prec prec, cudaStream_t s) {
+  if (is_fp64(prec)) return upload(ctx, dst, ph.data(), sizeof(double) * ph.size(), s);
+  std::vector<float> f(ph.begin(), ph.end());
+  return upload(ctx, dst, f.data(), sizeof(float) * f.size(), s);
+}
+
+template <bool PRODUCT>
+static gw_status launch_stripe(gw_ctx* ctx, gw_prec prec, const GridInfo& g, const int* nk, const void* gok,
+                               const void* guk, long kstr, const void* dph, int rows, void* out, void* out2, long ldo,
+                               cudaStream_t s) {
+  const int n_k = nk[0] * nk[1] * nk[2];
+  const size_t smem = (size_t)(2 * n_k * 32 + n_k * n_k) * csize(prec);
+  const dim3 grd((g.nr + 31) / 32, rows);
+  gw_status st;
+  auto go = [&](auto kern, auto* tag) -> gw_status {
+    using C = std::remove_pointer_t<decltype(tag)>;
+    if (smem > 48 * 1024 &&
+        (st = cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                         "cudaFuncSetAttribute")))
+      return st;
+    kern<<<grd, 256, smem, s>>>((const C*)gok, (const C*)guk, kstr, g.nr, (const C*)dph, n_k, g.n1, g.n2, g.n3, nk[0],
+                                nk[1], nk[2], (C*)out, (C*)out2, ldo);
+    return launch_check(ctx, "stripe_chi_kernel");
+  };
+  if (is_fp64(prec)) return go(stripe_chi_kernel<double, PRODUCT>, (double2*)nullptr);
+  return go(stripe_chi_kernel<float, PRODUCT>, (float2*)nullptr);
+}
+
+static gw_status launch_q_phase(gw_ctx* ctx, gw_prec prec, const GridInfo& g, const int* nk, void* slab, long ld,
+                                int n_chi, double sgn, cudaStream_t s) {
+  const int n_k = nk[0] * nk[1] * nk[2];
+  const dim3 gq(g.nr, std::min(n_k, 8));
+  if (is_fp64(prec))
+    q_phase_kernel<double><<<gq, 256, 0, s>>>((double2*)slab, ld, n_chi, g.n1, g.n2, g.n3, nk[0], nk[1], nk[2], sgn);
+  else
+    q_phase_kernel<float><<<gq, 256, 0, s>>>((float2*)slab, ld, n_chi, g.n1, g.n2, g.n3, nk[0], nk[1], nk[2], sgn);
+  return launch_check(ctx, "q_phase_kernel");
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_b, int n_occ,
+                                         const void* psi_k, const double* eps_k_h, double mu, int n,
+                                         const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
+                                         gw_prec prec, int r_block, void* chi_w, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  if (!psi_k || !eps_k_h || !tau_h || !C_h || !chi_w) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  GridInfo g, gs;
   std::vector<int> map, inv, smap, sinv;
-  if ((st = index_maps(ctx, g, fidx.data(), n_chi, map, inv))) return st;
-  if ((st = index_maps(ctx, gs, sidx.data(), n_k * n_chi, smap, sinv))) return st;
+  gw_status st = kmesh_grids(ctx, grid, nk, n_chi, gvec_h, &g, &gs, map, inv, smap, sinv);
+  if (st) return st;
+  const int n_k = nk[0] * nk[1] * nk[2];
+  if (n_b < 2 || n_b > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 2 <= n_b <= N_r");
+  for (int k = 0; k < n_k; ++k)
+    if ((st = check_energies(ctx, eps_k_h + (size_t)k * n_b, n_b, n_occ, mu))) return st;
+  if (n < 1 || n > 32) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
+  for (int j = 0; j < n; ++j)
+    if (!(tau_h[j] > 0)) return fail(ctx, GW_ERR_ARG, "tau must be > 0");
   cudaStream_t s = as_stream(stream);
   const size_t es = csize(prec);
   const int rb = r_block > 0 ? std::min(r_block, g.nr) : std::min(g.nr, 1024);
@@ -162,7 +263,6 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
   const bool two_pass = row_two_pass(gs, prec);
   const long ld = (long)n_k * n_chi;                   // slab row: all q blocks
   const size_t slab = (size_t)g.nr * ld;
-  // scratch
   Carver probe(nullptr);
   probe.take<int>(n_chi);
   probe.take<int>(g.nr);
@@ -196,27 +296,7 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
   if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
   if ((st = upload(ctx, dsmap, smap.data(), sizeof(int) * n_k * n_chi, s))) return st;
   if ((st = upload(ctx, dsinv, sinv.data(), sizeof(int) * gs.nr, s))) return st;
-  // phase table exp(-i k.L) / N_k, k.L / 2 pi = sum_d k_d l_d / nk_d
-  {
-    std::vector<double> ph(2 * (size_t)n_k * n_k);
-    for (int k = 0; k < n_k; ++k)
-      for (int l = 0; l < n_k; ++l) {
-        const int kv[3] = {k / (nk[1] * nk[2]), (k / nk[2]) % nk[1], k % nk[2]};
-        const int lv[3] = {l / (nk[1] * nk[2]), (l / nk[2]) % nk[1], l % nk[2]};
-        long num = 0;   // sum_d k_d l_d / nk_d over a common denominator
-        const long den = (long)nk[0] * nk[1] * nk[2];
-        for (int d = 0; d < 3; ++d) num += (long)kv[d] * lv[d] * (den / nk[d]);
-        const double a = -2.0 * M_PI * (double)(num % den) / (double)den;
-        ph[2 * ((size_t)k * n_k + l)] = std::cos(a) / n_k;
-        ph[2 * ((size_t)k * n_k + l) + 1] = std::sin(a) / n_k;
-      }
-    if (is_fp64(prec)) {
-      if ((st = upload(ctx, dph, ph.data(), sizeof(double) * ph.size(), s))) return st;
-    } else {
-      std::vector<float> f(ph.begin(), ph.end());
-      if ((st = upload(ctx, dph, f.data(), sizeof(float) * f.size(), s))) return st;
-    }
-  }
+  if ((st = upload_phases(ctx, dph, kl_phases(nk), prec, s))) return st;
   const double fac = g.dv * g.dv / g.volume;   // Eq. FFTX2 normalisation
   std::vector<float> cw32;
   if (is_fp64(prec)) {
@@ -227,7 +307,6 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
     cw32 = split_weights(C_h, n * n, fac);
     if ((st = upload(ctx, dcw, cw32.data(), sizeof(float) * 2 * n * n, s))) return st;
   }
-  const size_t smem = (size_t)(2 * n_k * 32 + n_k * n_k) * es;
   const long kstr = (long)rb * g.nr;
   for (int j = 0; j < n; ++j) {
     std::vector<GreenScales> scales(n_k);
@@ -247,33 +326,13 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
                              uk, s);
         if (st) return st;
       }
-      const dim3 grd((g.nr + 31) / 32, rows);
-      if (is_fp64(prec)) {
-        auto kern = stripe_chi_kernel<double>;
-        if (smem > 48 * 1024 && (st = cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                                          (int)smem), "cudaFuncSetAttribute")))
-          return st;
-        kern<<<grd, 256, smem, s>>>((const double2*)gok, (const double2*)guk, kstr, g.nr, (const double2*)dph, n_k,
-                                    g.n1, g.n2, g.n3, nk[0], nk[1], nk[2], (double2*)rows_s, gs.nr);
-      } else {
-        auto kern = stripe_chi_kernel<float>;
-        if (smem > 48 * 1024 && (st = cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                                          (int)smem), "cudaFuncSetAttribute")))
-          return st;
-        kern<<<grd, 256, smem, s>>>((const float2*)gok, (const float2*)guk, kstr, g.nr, (const float2*)dph, n_k,
-                                    g.n1, g.n2, g.n3, nk[0], nk[1], nk[2], (float2*)rows_s, gs.nr);
-      }
-      if ((st = launch_check(ctx, "stripe_chi_kernel"))) return st;
+      if ((st = launch_stripe<true>(ctx, prec, g, nk, gok, guk, kstr, dph, rows, rows_s, nullptr, gs.nr, s)))
+        return st;
       if ((st = launch_row_fft(ctx, gs, prec, 1, rows_s, nullptr, gs.nr, slab_j + (size_t)r0 * ld * es, ld, dsmap,
                                n_k * n_chi, rows, 1.0, s, dsinv, tmp_s)))
         return st;
     }
-    const dim3 gq(g.nr, std::min(n_k, 8));
-    if (is_fp64(prec))
-      q_phase_kernel<double><<<gq, 256, 0, s>>>((double2*)slab_j, ld, n_chi, g.n1, g.n2, g.n3, nk[0], nk[1], nk[2]);
-    else
-      q_phase_kernel<float><<<gq, 256, 0, s>>>((float2*)slab_j, ld, n_chi, g.n1, g.n2, g.n3, nk[0], nk[1], nk[2]);
-    if ((st = launch_check(ctx, "q_phase_kernel"))) return st;
+    if ((st = launch_q_phase(ctx, prec, g, nk, slab_j, ld, n_chi, -1.0, s))) return st;
     if ((st = launch_col_plane(ctx, g, prec, -1, slab_j, ld, (int)ld, 1.0, s))) return st;
   }
   for (int q = 0; q < n_k; ++q) {
@@ -283,4 +342,158 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
       return st;
   }
   return tc ? tc_check(ctx, tcs, s) : GW_OK;
+}
+
+// Diagonal self-energy of Bloch states on a k mesh: the space-time route of
+// gw_sigma_diag on the supercell stripe.  For tau_j:
+//   W~(r, q+g') = exp(+i q.r) sum_g exp(+i g.r) W~_q(g, g', tau_j) for every q
+//       (the column passes of Eq. FFTW on each q block, then the factor),
+//   per block of cell rows: G_occ / G_unocc on the stripe (k -> L transform of
+//       the G_k rows), W~(r, R') by the row transform over the supercell grid
+//       from the G set {q + g'}, and the contraction
+//   Sigma_unocc_nk(tau) = +dV^2 sum_{r in C} sum_{R' in S} psi*_nk(r) G_unocc(r,R') W~(r,R') psi_nk(R')
+//       with psi_nk(r' + L) = exp(i k.L) psi_nk(r') and the 1/Omega_S of Eq. FFTW,
+//       likewise occupied with a minus sign.
+// Then the same even/odd split, CT + ST and Thiele continuation as at Gamma.
+extern "C" gw_status gw_sigma_diag_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_b, int n_occ,
+                                         const void* psi_k, const double* eps_k_h, double mu, const int32_t* bk_h,
+                                         int n_n, int n, const double* tau_h, const double* omega_h,
+                                         const double* C_h, const double* S_h, const void* w_tau, int n_chi,
+                                         const int32_t* gvec_h, gw_prec prec, double* sigma_tau_h, double* sigma_iw_h,
+                                         const double* w_real_h, int n_real, double* sigma_real_h, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  if (!psi_k || !eps_k_h || !bk_h || !tau_h || !omega_h || !C_h || !S_h || !w_tau || !sigma_iw_h)
+    return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  if (reinterpret_cast<uintptr_t>(psi_k) % 16) return fail(ctx, GW_ERR_ARG, "psi_k must be 16-byte aligned");
+  GridInfo g, gs;
+  std::vector<int> map, inv, smap, sinv;
+  gw_status st = kmesh_grids(ctx, grid, nk, n_chi, gvec_h, &g, &gs, map, inv, smap, sinv);
+  if (st) return st;
+  const int n_k = nk[0] * nk[1] * nk[2];
+  if (n_b < 2 || n_b > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 2 <= n_b <= N_r");
+  for (int k = 0; k < n_k; ++k)
+    if ((st = check_energies(ctx, eps_k_h + (size_t)k * n_b, n_b, n_occ, mu))) return st;
+  if (n < 1 || n > 32) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
+  if (n_n < 1 || n_n > 1024) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_n <= 1024");
+  if (n_real < 0 || (n_real > 0 && (!w_real_h || !sigma_real_h))) return fail(ctx, GW_ERR_ARG, "bad real-axis request");
+  for (int i = 0; i < n_n; ++i)
+    if (bk_h[2 * i] < 0 || bk_h[2 * i] >= n_b || bk_h[2 * i + 1] < 0 || bk_h[2 * i + 1] >= n_k)
+      return fail(ctx, GW_ERR_ARG, "(band, k) pair out of range");
+  for (int j = 0; j < n; ++j)
+    if (!(tau_h[j] > 0)) return fail(ctx, GW_ERR_ARG, "tau must be > 0");
+  cudaStream_t s = as_stream(stream);
+  const size_t es = csize(prec);
+  const int rb = std::min(g.nr, 1024);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  const long ld = (long)n_k * n_chi;
+  const int nreal1 = std::max(n_real, 1);
+  Carver probe(nullptr);
+  probe.take<int>(n_chi);
+  probe.take<int>(g.nr);
+  probe.take<int>((size_t)n_k * n_chi);
+  probe.take<int>(gs.nr);
+  probe.take<int>(3 * (size_t)n_n);
+  probe.take<double>((size_t)n_k * n_b);
+  probe.take<double2>((size_t)n_k * n_k);
+  probe.take<double>(2 * (size_t)n * n + n + nreal1);
+  probe.take<double>(2 * (size_t)n_n * n);
+  probe.take<double2>((size_t)n_n * (n + nreal1));
+  probe.take<int>(n_n);
+  probe.take<char>((size_t)g.nr * ld * es);
+  probe.take<char>((size_t)n_k * rb * g.nr * es);
+  probe.take<char>((size_t)n_k * rb * g.nr * es);
+  probe.take<char>(3 * (size_t)rb * gs.nr * es);
+  probe.take<char>((size_t)n_n * (gs.nr + g.nr) * es);
+  if (tc) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
+  if ((st = reserve(ctx, probe.off))) return st;
+  Carver cv(ctx->arena);
+  int* dmap = cv.take<int>(n_chi);
+  int* dinv = cv.take<int>(g.nr);
+  int* dsmap = cv.take<int>((size_t)n_k * n_chi);
+  int* dsinv = cv.take<int>(gs.nr);
+  int* dbk = cv.take<int>(3 * (size_t)n_n);           // (band, k) pairs, then 0 .. n_n-1
+  int* dbid = dbk + 2 * n_n;
+  char* dscale = cv.take<char>((size_t)n_k * n_b * 8);
+  char* dph = cv.take<char>((size_t)n_k * n_k * 16);
+  double* tab = cv.take<double>(2 * (size_t)n * n + n + nreal1);
+  double* acc = cv.take<double>(2 * (size_t)n_n * n);
+  double2* out = cv.take<double2>((size_t)n_n * (n + nreal1));
+  int* dstat = cv.take<int>(n_n);
+  char* wrg = cv.take<char>((size_t)g.nr * ld * es);
+  char* gok = cv.take<char>((size_t)n_k * rb * g.nr * es);
+  char* guk = cv.take<char>((size_t)n_k * rb * g.nr * es);
+  char* go_s = cv.take<char>(3 * (size_t)rb * gs.nr * es);   // G_occ, G_unocc and W~ stripes of a block
+  char* gu_s = go_s + (size_t)rb * gs.nr * es;
+  char* w_s = gu_s + (size_t)rb * gs.nr * es;
+  char* ext = cv.take<char>((size_t)n_n * (gs.nr + g.nr) * es);
+  char* prow = ext + (size_t)n_n * gs.nr * es;
+  void* tcs = tc ? cv.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false)) : nullptr;
+  if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
+  if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
+  if ((st = upload(ctx, dsmap, smap.data(), sizeof(int) * n_k * n_chi, s))) return st;
+  if ((st = upload(ctx, dsinv, sinv.data(), sizeof(int) * gs.nr, s))) return st;
+  std::vector<int> bk(3 * (size_t)n_n);
+  for (int i = 0; i < 2 * n_n; ++i) bk[i] = bk_h[i];
+  for (int i = 0; i < n_n; ++i) bk[2 * n_n + i] = i;
+  if ((st = upload(ctx, dbk, bk.data(), sizeof(int) * 3 * n_n, s))) return st;
+  if ((st = upload_phases(ctx, dph, kl_phases(nk), prec, s))) return st;
+  if ((st = upload(ctx, tab, C_h, sizeof(double) * n * n, s))) return st;
+  if ((st = upload(ctx, tab + (size_t)n * n, S_h, sizeof(double) * n * n, s))) return st;
+  if ((st = upload(ctx, tab + 2 * (size_t)n * n, omega_h, sizeof(double) * n, s))) return st;
+  if (n_real > 0 && (st = upload(ctx, tab + 2 * (size_t)n * n + n, w_real_h, sizeof(double) * n_real, s))) return st;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * 2 * n_n * n, s), "memset"))) return st;
+  // the requested orbitals over the supercell (Bloch phase) and on the cell
+  {
+    const dim3 grd((g.nr + 255) / 256, n_k, n_n);
+    if (is_fp64(prec))
+      bloch_extend_kernel<double><<<grd, 256, 0, s>>>((const double2*)psi_k, (long)n_b * g.nr, g.nr, dbk, g.n1, g.n2,
+                                                      g.n3, nk[0], nk[1], nk[2], (double2*)ext, (double2*)prow);
+    else
+      bloch_extend_kernel<float><<<grd, 256, 0, s>>>((const float2*)psi_k, (long)n_b * g.nr, g.nr, dbk, g.n1, g.n2,
+                                                     g.n3, nk[0], nk[1], nk[2], (float2*)ext, (float2*)prow);
+    if ((st = launch_check(ctx, "bloch_extend_kernel"))) return st;
+  }
+  double* acc_u = acc;
+  double* acc_o = acc + (size_t)n_n * n;
+  const double coef = g.dv * g.dv / (g.volume * n_k);   // dV^2 and the 1/Omega_S of Eq. FFTW
+  const long kstr = (long)rb * g.nr;
+  for (int j = 0; j < n; ++j) {
+    std::vector<GreenScales> scales(n_k);
+    for (int k = 0; k < n_k; ++k) {
+      scales[k] = green_scales(eps_k_h + (size_t)k * n_b, n_b, n_occ, mu, tau_h[j]);
+      if (!tc && (st = upload_scales(ctx, dscale + (size_t)k * n_b * 8, scales[k], prec, s))) return st;
+    }
+    for (int q = 0; q < n_k; ++q) {
+      const char* wq = static_cast<const char*>(w_tau) + ((size_t)q * n + j) * n_chi * n_chi * es;
+      char* blk = wrg + (size_t)q * n_chi * es;
+      if ((st = launch_col_line(ctx, g, prec, +1, 1, wq, n_chi, blk, ld, n_chi, dinv, 1.0, s))) return st;
+      if ((st = launch_col_plane(ctx, g, prec, +1, blk, ld, n_chi, 1.0, s))) return st;
+    }
+    if ((st = launch_q_phase(ctx, prec, g, nk, wrg, ld, n_chi, +1.0, s))) return st;
+    for (int r0 = 0; r0 < g.nr; r0 += rb) {
+      const int rows = std::min(rb, g.nr - r0);
+      for (int k = 0; k < n_k; ++k) {
+        const char* pk = static_cast<const char*>(psi_k) + (size_t)k * n_b * g.nr * es;
+        char* ok = gok + (size_t)k * kstr * es;
+        char* uk = guk + (size_t)k * kstr * es;
+        if (tc) st = tc_green_rows(ctx, g, n_b, n_occ, pk, scales[k], r0, rows, prec, ok, uk, tcs, true, s);
+        else st = green_rows(ctx, g, n_b, n_occ, pk, dscale + (size_t)k * n_b * 8, scales[k], r0, rows, prec, ok,
+                             uk, s);
+        if (st) return st;
+      }
+      if ((st = launch_stripe<false>(ctx, prec, g, nk, gok, guk, kstr, dph, rows, go_s, gu_s, gs.nr, s))) return st;
+      if ((st = launch_row_fft(ctx, gs, prec, 2, wrg + (size_t)r0 * ld * es, nullptr, ld, w_s, gs.nr, dsmap,
+                               n_k * n_chi, rows, 1.0, s, dsinv)))
+        return st;
+      if ((st = launch_sigma_contract(ctx, prec, w_s, go_s, gu_s, gs.nr, gs.nr, rows, ext, dbid, n_n, r0, coef,
+                                      acc_u + j, acc_o + j, n, s, prow, g.nr)))
+        return st;
+    }
+  }
+  if (tc && (st = tc_check(ctx, tcs, s))) return st;
+  std::vector<int32_t> labels(n_n);
+  for (int i = 0; i < n_n; ++i) labels[i] = bk_h[2 * i];
+  return sigma_finish(ctx, acc, n_n, n, tab, n_real, out, dstat, labels.data(), sigma_tau_h, sigma_iw_h, sigma_real_h,
+                      s);
 }

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(kSigThreads) sigma_contract_kernel(
     const typename cpx<T>::t* __restrict__ wrr, const typename cpx<T>::t* __restrict__ go,
     const typename cpx<T>::t* __restrict__ gu, long ld, int nr, int rows,
     const typename cpx<T>::t* __restrict__ psi, const int* __restrict__ bands, int n_n, int r0, double coef,
-    double* __restrict__ acc_u, double* __restrict__ acc_o, int acc_stride) {
+    double* __restrict__ acc_u, double* __restrict__ acc_o, int acc_stride,
+    const typename cpx<T>::t* __restrict__ psi_row, long ld_row) {
   using C = typename cpx<T>::t;
   constexpr int CHUNK = sizeof(T) == 4 ? 512 : 256;          // R' per chunk: 32 KB of psi per buffer
   constexpr int PAIRS = CHUNK / 2;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kSigThreads) sigma_contract_kernel(
       if (lane == b) {
         double so = 0, su = 0;
         if (b < nb && active) {
-          const C pn = psi[(long)bands[b0 + b] * nr + r0 + r];
+          const C pn = psi_row[(long)bands[b0 + b] * ld_row + r0 + r];
           so = -coef * ((double)pn.x * vo[b][0] + (double)pn.y * vo[b][1]);
           su = coef * ((double)pn.x * vu[b][0] + (double)pn.y * vu[b][1]);
         }
@@ -217,10 +218,15 @@ __global__ void sigma_finish_kernel(const double* __restrict__ acc_u, const doub
   status[b] = bad;
 }
 
-static gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wrr, const void* go, const void* gu,
-                                       long ld, int nr, int rows, const void* psi, const int* bands, int n_n, int r0,
-                                       double coef, double* acc_u, double* acc_o, int acc_stride, cudaStream_t st) {
+gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wrr, const void* go, const void* gu, long ld,
+                                int nr, int rows, const void* psi, const int* bands, int n_n, int r0, double coef,
+                                double* acc_u, double* acc_o, int acc_stride, cudaStream_t st, const void* psi_row,
+                                long ld_row) {
   if (rows <= 0) return GW_OK;
+  if (!psi_row) {
+    psi_row = psi;
+    ld_row = nr;
+  }
   const dim3 grid((rows + kSigRows - 1) / kSigRows);
   auto go_ = [&](auto kernel, size_t esz, int chunk, auto* tag) -> gw_status {
     using C = std::remove_pointer_t<decltype(tag)>;
@@ -230,11 +236,45 @@ static gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wr
     if (rc) return rc;
     KTimer kt(ctx, KF_SIGMA, 3.0 * rows * (double)nr * esz, st);
     kernel<<<grid, kSigThreads, bytes, st>>>((const C*)wrr, (const C*)go, (const C*)gu, ld, nr, rows, (const C*)psi,
-                                             bands, n_n, r0, coef, acc_u, acc_o, acc_stride);
+                                             bands, n_n, r0, coef, acc_u, acc_o, acc_stride, (const C*)psi_row,
+                                             ld_row);
     return launch_check(ctx, "sigma_contract_kernel");
   };
   if (is_fp64(prec)) return go_(sigma_contract_kernel<double>, sizeof(double2), 2 * 256, (double2*)nullptr);
   return go_(sigma_contract_kernel<float>, sizeof(float2), 2 * 512, (float2*)nullptr);
+}
+
+// Even/odd split, CT + ST and Thiele continuation of the accumulated
+// Sigma(tau) (acc [2][n_n][n]: unoccupied, occupied), then the results to the
+// host.  tab: C [n][n], S [n][n], omega [n], real frequencies [n_real] in one
+// device block; out [n_n][n] + [n_n][n_real] complex; stat [n_n].
+gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* tab, int n_real, double2* out,
+                       int* stat, const int32_t* labels, double* sigma_tau_h, double* sigma_iw_h,
+                       double* sigma_real_h, cudaStream_t s) {
+  gw_status st;
+  const double* dC = tab;
+  const double* dS = dC + (size_t)n * n;
+  const double* dom = dS + (size_t)n * n;
+  const double* dwr = dom + n;
+  double2* out_re = out + (size_t)n_n * n;
+  sigma_finish_kernel<<<(n_n + 63) / 64, 64, 0, s>>>(acc, acc + (size_t)n_n * n, n_n, n, dC, dS, dom, dwr, n_real,
+                                                      out, n_real > 0 ? out_re : nullptr, stat);
+  if ((st = launch_check(ctx, "sigma_finish_kernel"))) return st;
+  std::vector<double2> h_iw((size_t)n_n * n), h_re((size_t)n_n * std::max(n_real, 1));
+  std::vector<int> h_stat(n_n);
+  std::vector<double> h_acc(2 * (size_t)n_n * n);
+  cudaMemcpyAsync(h_iw.data(), out, sizeof(double2) * n_n * n, cudaMemcpyDeviceToHost, s);
+  if (n_real > 0) cudaMemcpyAsync(h_re.data(), out_re, sizeof(double2) * n_n * n_real, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h_stat.data(), stat, sizeof(int) * n_n, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h_acc.data(), acc, sizeof(double) * 2 * n_n * n, cudaMemcpyDeviceToHost, s);
+  if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sigma sync"))) return st;
+  std::memcpy(sigma_iw_h, h_iw.data(), sizeof(double2) * n_n * n);
+  if (n_real > 0) std::memcpy(sigma_real_h, h_re.data(), sizeof(double2) * n_n * n_real);
+  if (sigma_tau_h) std::memcpy(sigma_tau_h, h_acc.data(), sizeof(double) * 2 * n_n * n);
+  for (int b = 0; b < n_n; ++b)
+    if (h_stat[b])
+      return fail(ctx, GW_ERR_NUMERIC, "Thiele continuation broke down for band " + std::to_string(labels[b]));
+  return GW_OK;
 }
 
 size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec) {
@@ -350,21 +390,5 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
     }
   }
   if (tc && (st = tc_check(ctx, tcs, s))) return st;
-  sigma_finish_kernel<<<(n_n + 63) / 64, 64, 0, s>>>(acc_u, acc_o, n_n, n, dC, dS, dom, dwr, n_real, out_iw,
-                                                      n_real > 0 ? out_re : nullptr, dstat);
-  if ((st = launch_check(ctx, "sigma_finish_kernel"))) return st;
-  std::vector<double2> h_iw((size_t)n_n * n), h_re((size_t)n_n * std::max(n_real, 1));
-  std::vector<int> h_stat(n_n);
-  std::vector<double> h_acc(2 * (size_t)n_n * n);
-  cudaMemcpyAsync(h_iw.data(), out_iw, sizeof(double2) * n_n * n, cudaMemcpyDeviceToHost, s);
-  if (n_real > 0) cudaMemcpyAsync(h_re.data(), out_re, sizeof(double2) * n_n * n_real, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(h_stat.data(), dstat, sizeof(int) * n_n, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(h_acc.data(), acc, sizeof(double) * 2 * n_n * n, cudaMemcpyDeviceToHost, s);
-  if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sigma sync"))) return st;
-  std::memcpy(sigma_iw_h, h_iw.data(), sizeof(double2) * n_n * n);
-  if (n_real > 0) std::memcpy(sigma_real_h, h_re.data(), sizeof(double2) * n_n * n_real);
-  if (sigma_tau_h) std::memcpy(sigma_tau_h, h_acc.data(), sizeof(double) * 2 * n_n * n);
-  for (int b = 0; b < n_n; ++b)
-    if (h_stat[b]) return fail(ctx, GW_ERR_NUMERIC, "Thiele continuation broke down for band " + std::to_string(bands_h[b]));
-  return GW_OK;
+  return sigma_finish(ctx, acc, n_n, n, dC, n_real, out_iw, dstat, bands_h, sigma_tau_h, sigma_iw_h, sigma_real_h, s);
 }

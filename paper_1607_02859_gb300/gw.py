@@ -26,7 +26,7 @@ STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "G
 EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches", "gw_ctx_scratch_bytes", "gw_ctx_reserve",
            "gw_ctx_set_timing", "gw_ctx_kernel_stats", "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
-           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh",
+           "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh", "gw_sigma_diag_kmesh",
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy"]
 
 
@@ -75,6 +75,8 @@ _SIGS = {
     "gw_chi0_plan_launch": (_I, [_P, _P, _P, _P]),
     "gw_chi0_plan_status": (_I, [_P, _P]),
     "gw_chi0_plan_destroy": (_I, [_P]),
+    "gw_sigma_diag_kmesh": (_I, [_P, _G, _IP, _I, _I, _P, _DP, ct.c_double, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I,
+                                 _IP, _I, _DP, _P, _DP, _I, _P, _P]),
     "gw_chi0_omega_kmesh": (_I, [_P, _G, _IP, _I, _I, _P, _DP, ct.c_double, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                            _DP, _DP, _DP, _I, _DP, _P]),
@@ -398,3 +400,29 @@ class Chi0Plan:
             self.close()
         except Exception:
             pass
+
+
+def sigma_diag_kmesh(ctx, grid, nk, psi_k, eps_k, n_occ, mu, bands_k, tau, omega, C, S, w_tau, gvec, prec,
+                     w_real=None):
+    """Sigma_nk for (band, k index) pairs on a k mesh (gw_sigma_diag_kmesh); w_tau [N_k][n][n_chi][n_chi]."""
+    p = prec_of(prec)
+    nkv = _i32(nk)
+    bk = _i32(np.asarray(bands_k).reshape(-1, 2))
+    tau = _f64(tau)
+    n = len(tau)
+    n_n = bk.shape[0]
+    s_tau = np.zeros((2, n_n, n))
+    s_iw = np.zeros((n_n, n), dtype=np.complex128)
+    wr = None if w_real is None else _f64(w_real)
+    n_real = 0 if wr is None else len(wr)
+    s_re = np.zeros((n_n, max(n_real, 1)), dtype=np.complex128)
+    gv = _i32(gvec)
+    _check(lib().gw_sigma_diag_kmesh(ctx.handle, ct.byref(grid), _ip(nkv), psi_k.shape[1], int(n_occ),
+                                     _dev(psi_k, "psi_k", p), _dp(_f64(eps_k)), float(mu), _ip(bk), n_n, n, _dp(tau),
+                                     _dp(_f64(omega)), _dp(_f64(C)), _dp(_f64(S)), _dev(w_tau, "w_tau", p), len(gv),
+                                     _ip(gv), p, _dp(s_tau), s_iw.ctypes.data_as(_DP), _dp(wr), n_real,
+                                     s_re.ctypes.data_as(_DP) if n_real else None, _stream()), ctx)
+    out = {"sigma_unocc": s_tau[0], "sigma_occ": s_tau[1], "sigma_iw": s_iw}
+    if n_real:
+        out["sigma_real"] = s_re
+    return out

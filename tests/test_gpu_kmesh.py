@@ -74,3 +74,37 @@ def test_kmesh_argument_checks(ctx, case):
         gw.chi0_omega_kmesh(ctx, grid, (1, 1, 5), psi, p.eps_k, p.n_occ, p.mu, p.tau, mats["C"], gv, "fp32", out)
     with pytest.raises(gw.GwError):       # mu outside a gap
         gw.chi0_omega_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, 5.0, p.tau, mats["C"], gv, "fp32", out)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3", "fp64"])
+def test_sigma_kmesh(ctx, prec):
+    from oracle import sigma as osg
+    p = inputs.kmesh_problem(n=(6, 6, 6), a=(6.0, 6.5, 7.0), nk=(2, 2, 2), n_occ=4, n_unocc=20, n_tau=4, seed=63)
+    gv = ogv.g_set(p.n, 60)
+    mats = ogrids.transform_matrices(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
+    rng = np.random.default_rng(64)
+    nc = len(gv)
+    w = np.zeros((p.n_k, len(p.tau), nc, nc), dtype=np.complex128)
+    for q in range(p.n_k):                     # Hermitian negative W~_q(tau) decaying with tau
+        a = rng.standard_normal((nc, nc)) + 1j * rng.standard_normal((nc, nc))
+        for j, t in enumerate(p.tau):
+            w[q, j] = -0.02 * p.volume * (a @ a.conj().T) / nc * np.exp(-0.7 * t)
+    bands = [(3, 0), (4, 1), (2, 5), (5, 7)]
+    su = np.zeros((len(bands), len(p.tau)))
+    so = np.zeros_like(su)
+    for j, t in enumerate(p.tau):
+        ws = okm.w_stripe(w[:, j], p.n, p.nk, p.lattice, gv)
+        su[:, j], so[:, j] = okm.sigma_k_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, t, ws, p.n, p.nk, p.lattice, bands)
+    ref = osg.sigma_iw(su, so, mats["C"], mats["S"])
+    dt = gw.cdtype(prec)
+    grid = gw.make_grid(p.n, p.lattice)
+    psi = torch.from_numpy(np.ascontiguousarray(p.psi_k)).to("cuda", dtype=dt)
+    w_d = torch.from_numpy(w).to("cuda", dtype=dt)
+    out = gw.sigma_diag_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, p.mu, bands, p.tau, p.omega, mats["C"],
+                              mats["S"], w_d, gv, prec)
+    err = np.max(np.abs(out["sigma_iw"] - ref))
+    scale = np.max(np.abs(ref))
+    print("sigma k mesh %s: max |dSigma| %.2e Ha (max |Sigma| %.2e)" % (prec, err, scale))
+    # the bars of the Gamma-point Sigma tests: FP64 to rounding, the others within 1 meV and 1e-4 relative
+    assert np.max(np.abs(out["sigma_unocc"] - su)) < (1e-11 if prec == "fp64" else 1e-4) * np.max(np.abs(su))
+    assert err < (1e-11 * scale if prec == "fp64" else min(1e-4 * scale, 3.674932e-5))
