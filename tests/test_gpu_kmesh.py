@@ -108,3 +108,47 @@ def test_sigma_kmesh(ctx, prec):
     # the bars of the Gamma-point Sigma tests: FP64 to rounding, the others within 1 meV and 1e-4 relative
     assert np.max(np.abs(out["sigma_unocc"] - su)) < (1e-11 if prec == "fp64" else 1e-4) * np.max(np.abs(su))
     assert err < (1e-11 * scale if prec == "fp64" else min(1e-4 * scale, 3.674932e-5))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_kmesh_chain_to_sigma(ctx, prec):
+    """chi0_q -> W~_q (gw_screen_W per q on the supercell G triples q + nk g) ->
+    W~_q(tau) -> Sigma_nk, against the same chain in the oracle; Sigma within 1 meV."""
+    from oracle import screen as osc
+    from oracle import sigma as osg
+    p = inputs.kmesh_problem(n=(6, 6, 6), a=(6.0, 6.5, 7.0), nk=(2, 2, 2), n_occ=4, n_unocc=20, n_tau=4, seed=65)
+    gv = ogv.g_set(p.n, 60)
+    nc = len(gv)
+    mats = ogrids.transform_matrices(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
+    ns = tuple(np.asarray(p.n) * np.asarray(p.nk))
+    lat_s = p.lattice * np.asarray(p.nk)[:, None]
+    gs_all = okm.supercell_gvecs(gv, p.nk)
+    bands = [(3, 0), (4, 6), (2, 3)]
+    # oracle chain
+    chi_w = reference(p, gv, mats["C"])                                   # [N_q][n][nc][nc]
+    w_tau = np.empty_like(chi_w)
+    for q in range(p.n_k):
+        vh = ogv.v_sqrt(gs_all[q * nc:(q + 1) * nc], lat_s)
+        w_tau[q] = osc.inverse_ct(osc.screen(chi_w[q], vh), mats["Cinv"])
+    su = np.zeros((len(bands), len(p.tau)))
+    so = np.zeros_like(su)
+    for j, t in enumerate(p.tau):
+        ws = okm.w_stripe(w_tau[:, j], p.n, p.nk, p.lattice, gv)
+        su[:, j], so[:, j] = okm.sigma_k_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, t, ws, p.n, p.nk, p.lattice, bands)
+    ref = osg.sigma_iw(su, so, mats["C"], mats["S"])
+    # GPU chain
+    dt = gw.cdtype(prec)
+    grid = gw.make_grid(p.n, p.lattice)
+    grid_s = gw.make_grid(ns, lat_s)
+    psi = torch.from_numpy(np.ascontiguousarray(p.psi_k)).to("cuda", dtype=dt)
+    chi = torch.empty((p.n_k, len(p.tau), nc, nc), dtype=dt, device="cuda")
+    gw.chi0_omega_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, p.mu, p.tau, mats["C"], gv, prec, chi)
+    wt = torch.empty_like(chi)
+    for q in range(p.n_k):
+        gw.screen_W(ctx, grid_s, gs_all[q * nc:(q + 1) * nc], prec, chi[q], chi[q], resid=False)
+        gw.tau_to_omega(ctx, gw.CT, mats["Cinv"], chi[q], wt[q], prec)
+    out = gw.sigma_diag_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, p.mu, bands, p.tau, p.omega, mats["C"],
+                              mats["S"], wt, gv, prec)
+    err = np.max(np.abs(out["sigma_iw"] - ref))
+    print("k-mesh chain %s: max |dSigma| %.2e Ha (max |Sigma| %.2e)" % (prec, err, np.max(np.abs(ref))))
+    assert err < 3.674932e-5
