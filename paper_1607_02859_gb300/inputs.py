@@ -279,3 +279,21 @@ def kmesh_problem(n=(6, 6, 6), a=(6.0, 6.5, 7.0), nk=(2, 2, 2), n_occ=4, n_unocc
                         tau=tau, omega=1.0 / tau[::-1], n_chi=int(np.prod(n)) if n_chi is None else int(n_chi),
                         x_min=float(np.min(np.abs(eps_k - mu))), x_max=float(width + np.max(np.abs(eps_k - mu))),
                         name="kmesh_%dx%dx%d_k%dx%dx%d" % (n + nk))
+
+
+def batch_mix(count=16, seed=4, n_chi_cap=2048):
+    """Uneven systems for one batched launch: grid n^3 with n in {12, 16, 20, 24}
+    (cell a = n * 10.26 / 12), 128-1024 complex bands in multiples of 8 (one
+    eighth occupied), 8-16 tau, the G set capped at n_chi_cap, the si8 energy
+    windows and gap."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([12, 16, 20, 24]))
+        n_b = int(rng.integers(16, 129)) * 8
+        n_occ = n_b // 8
+        n_tau = int(rng.integers(8, 17))
+        out.append(make_problem((n, n, n), n * 10.26 / 12, n_occ, n_b - n_occ, (-0.5, 0.0), (0.04, 4.0), 0.02, n_tau,
+                                seed + 100 + i, n_bands_sigma=4, n_chi=min(n ** 3, n_chi_cap), pin_edges=True,
+                                name="batch%d_%d^3_%db_%dt" % (i, n, n_b, n_tau)))
+    return out

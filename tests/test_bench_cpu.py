@@ -62,3 +62,14 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "gamma_toy", "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_batch_mix_and_flops():
+    from paper_1607_02859_gb300 import batch, inputs
+    ps = inputs.batch_mix(4, seed=9)
+    for p in ps:
+        assert p.n[0] in (12, 16, 20, 24) and 128 <= p.n_b <= 1024 and p.n_b % 8 == 0
+        assert p.n_occ == p.n_b // 8 and 8 <= len(p.tau) <= 16 and p.n_chi <= 2048
+    # G formation dominates: 8 N_r^2 N_b per tau
+    f = batch.chi0_flops(1728, 128, 8, 1728)
+    assert f > 8 * 8.0 * 1728 ** 2 * 128
