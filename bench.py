@@ -169,7 +169,7 @@ def measured_peaks():
 
 # ---------------------------------------------------------------------- reference arm (CPU oracle)
 
-SAMPLE_ROWS, SAMPLE_SOLVE = 768, 3072      # ~10 s of the FP64 oracle on 16 host cores at si8
+SAMPLE_ROWS, SAMPLE_SOLVE = 1536, 3072     # ~10 s of the FP64 oracle on 16 host cores at si8
 
 
 def oracle_sample(p, rows=SAMPLE_ROWS, n_solve=SAMPLE_SOLVE):
