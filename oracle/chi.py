@@ -23,7 +23,7 @@ from . import gvec as _gv
 
 
 def chi_rr(g_occ, g_unocc):
-    """Eq. chi_rr (spec index order, spin factor 2)."""
+    """Eq. chi_rr in the order chi(r,r') = -2 G_occ(r,r') G_unocc(r',r), spin factor 2."""
     return -2.0 * g_occ * g_unocc.T
 
 
