@@ -18,8 +18,11 @@ Modules (each function cites the passage it follows):
              W~(r,r') (Eq. FFTW)
   sigma   -- Sigma_nn(tau) (Eqs. Sigma_occ, Sigma_rr, Sigma_occ_reduce first
              term), even/odd split and CT+ST (Eqs. cos_sin_sigma*,
-             sigma_r_w), pair route
-  thiele  -- Thiele reciprocal differences (Eqs. pade1, pade2)
+             sigma_r_w), pair route; the full matrix Sigma_nm by both routes
+  thiele  -- Thiele reciprocal differences (Eqs. pade1, pade2) and the
+             derivative of the continued fraction
+  qp      -- linearised QP energies and spectral functions (Eqs. QP, GWQP,
+             Z, A)
   pipeline-- the chain chi0(i omega) -> W~ -> Sigma_nn(i omega) -> Sigma_nn(omega)
 
 Parity pins live in tests/test_oracle_*.py.  No function here is "parity

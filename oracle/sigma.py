@@ -1,4 +1,4 @@
-"""Diagonal correlation self-energy (Sec. II.D).  Oracle only.
+"""Correlation self-energy, diagonal and full matrix (Sec. II.D).  Oracle only.
 
 Space-time route (Eq. Sigma_rr, first term of Eq. Sigma_occ_reduce; the PAW
 one-centre terms are out of scope).  With G_occ/G_unocc as in green.py and
@@ -94,3 +94,55 @@ def sigma_pair_sparse(psi, eps, n_occ, mu, taus, entries, n, lattice, fft_index,
             su[b, t] = (np.exp(-(eps[n_occ:] - mu) * tau) * q[n_occ:]).sum()
             so[b, t] = -(np.exp((eps[:n_occ] - mu) * tau) * q[:n_occ]).sum()
     return su, so
+
+
+# ---------------------------------------------------------------- full matrix
+# Matrix elements Sigma_nm = <psi_n|Sigma|psi_m> of the same operators: the
+# paper's Eq. Sigma_occ_reduce written for a pair of bands (n, m) instead of
+# (n, n).  G o W~ is Hermitian in (r, r'), so the matrices are Hermitian and
+# their diagonals are the real values above.  The even/odd split and CT+ST
+# (Eqs. cos_sin_sigma, cos_sin_sigma1/2) act element by element on the
+# complex matrices.
+
+def sigma_matrix_tau(psi, eps, n_occ, mu, tau, w_rr, bands, dv):
+    """(Su, So) [N_n][N_n] complex at one tau:
+        Su_nm(tau)  = +dV^2 psi_n^H (G_unocc o W~) psi_m
+        So_nm(-tau) = -dV^2 psi_n^H (G_occ o W~) psi_m"""
+    gu = _gr.green_unocc(psi, eps, n_occ, mu, tau)
+    go = _gr.green_occ(psi, eps, n_occ, mu, tau)
+    p = psi[np.asarray(bands)]
+    su = dv * dv * (p.conj() @ (gu * w_rr) @ p.T)
+    so = -dv * dv * (p.conj() @ (go * w_rr) @ p.T)
+    return su, so
+
+
+def sigma_matrix_pair_tau(psi, eps, n_occ, mu, tau, w_gg, gvecs, n, lattice, bands):
+    """Conventional route for the matrix: with a_nl(G) = dV sum_r exp(-iG.r)
+    psi_l^*(r) psi_n(r),
+        Su_nm(tau) = (1/Omega) sum_{l unocc} exp(-(eps_l-mu) tau) a_nl^H W~ a_ml
+    and So_nm(-tau) likewise over occupied l with exp(+(eps_l-mu) tau) and a
+    minus sign."""
+    from . import gvec as _gv
+    vol = abs(np.linalg.det(lattice))
+    dv = vol / int(np.prod(n))
+    pm = _gv.phase_matrix(gvecs, n, -1.0)
+    a = [dv * (psi.conj() * psi[b][None, :]) @ pm.T for b in bands]     # each [N_b][N_chi]
+    fu = np.exp(-(eps[n_occ:] - mu) * tau)
+    fo = np.exp((eps[:n_occ] - mu) * tau)
+    nb = len(bands)
+    su = np.empty((nb, nb), dtype=np.complex128)
+    so = np.empty((nb, nb), dtype=np.complex128)
+    for i in range(nb):
+        for k in range(nb):
+            q = np.einsum("lg,gh,lh->l", a[i].conj(), w_gg, a[k]) / vol
+            su[i, k] = (fu * q[n_occ:]).sum()
+            so[i, k] = -(fo * q[:n_occ]).sum()
+    return su, so
+
+
+def sigma_matrix_iw(s_unocc, s_occ, C, S):
+    """Sigma_nm(i omega_k) [N_n][N_n][N] from complex [N_n][N_n][N_tau] arrays:
+    sum_j C_kj Sigma^c_nm(tau_j) + i sum_j S_kj Sigma^s_nm(tau_j)."""
+    sc = 0.5 * (s_unocc + s_occ)
+    ss = 0.5 * (s_unocc - s_occ)
+    return sc @ C.T + 1j * (ss @ S.T)

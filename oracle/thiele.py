@@ -44,3 +44,22 @@ def evaluate(a, z, x):
     if np.any(np.abs(t) < 1e-300):
         raise ThieleBreakdown("vanishing denominator")
     return a[0] / t
+
+
+def derivative(a, z, x):
+    """dP_N/dz at the points x.  P_N is analytic away from its poles, so on the
+    real axis this is also d/d omega.  Each backward step t <- 1 + a_p (x - z_{p-1}) / t
+    is differentiated with the quotient rule,
+        t' <- a_p / t - a_p (x - z_{p-1}) t' / t^2,
+    starting from t = 1, t' = 0; finally P_N' = -a_1 t' / t^2."""
+    x = np.asarray(x, dtype=np.complex128)
+    t = np.ones_like(x)
+    dt = np.zeros_like(x)
+    for p in range(len(a) - 1, 0, -1):
+        if np.any(np.abs(t) < 1e-300):
+            raise ThieleBreakdown("vanishing denominator")
+        dt = a[p] / t - a[p] * (x - z[p - 1]) * dt / (t * t)
+        t = 1.0 + a[p] * (x - z[p - 1]) / t
+    if np.any(np.abs(t) < 1e-300):
+        raise ThieleBreakdown("vanishing denominator")
+    return -a[0] * dt / (t * t)
