@@ -4,12 +4,16 @@
 One step = the whole hot path through the C ABI on one seeded system:
 chi0(i omega) (gw_chi0_omega: G formation, chi = -2 G_occ o conj(G_unocc), row
 and column FFTs, cosine transform), screening (gw_screen_W), inverse cosine
-transform (gw_tau_to_omega), and the diagonal self-energy with its Thiele
-continuation (gw_sigma_diag).  The metric is the effective TFLOP/s of the
+transform (gw_tau_to_omega), the diagonal self-energy with its Thiele
+continuation (gw_sigma_diag) and the linearised QP energies and spectral
+functions (gw_qp_energies).  The metric is the effective TFLOP/s of the
 method's algorithmic work (flop model below) divided by the device time.
+--sigma matrix replaces the last two calls by the full self-energy matrix over
+the same bands (gw_sigma_matrix).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gw|reference]
                   [--prec fp32|fp64|f16x3|bf16x3] [--workload si8|mid|gamma_toy|si64]
+                  [--sigma diag|matrix]
 
 N > 1 (under torchrun): independent replicas, one per GPU (the path is not
 sharded); value = the work of all ranks / the slowest rank's time.
@@ -242,6 +246,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-stage pass")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
+    ap.add_argument("--sigma", default="diag", choices=["diag", "matrix"],
+                    help="diag: Sigma_nn, continuation and QP energies; matrix: the full Sigma_nm(i omega)")
     args = ap.parse_args()
 
     from paper_1607_02859_gb300 import inputs
@@ -250,7 +256,8 @@ def main():
     workload = {"workload": "%s: %dx%dx%d grid (N_r=%d), %d+%d %s bands, %d tau/i omega, chi0 %dx%d, Sigma_nn for %d bands"
                 % (args.workload, *p.n, p.n_r, p.n_occ, p.n_b - p.n_occ, "real" if p.real else "complex", n_tau,
                    p.n_chi, p.n_chi, len(p.bands)),
-                "prec": args.prec, "l2": "per-step working set > 40 GB >> 129 MB L2; L2 also flushed between steps",
+                "prec": args.prec, "sigma": args.sigma,
+                "l2": "per-step working set > 40 GB >> 129 MB L2; L2 also flushed between steps",
                 "accuracy": ACCURACY.get(args.prec, "")}
     if args.impl == "reference":
         run_reference(args, p, workload)
@@ -279,6 +286,8 @@ def main():
     w_tau = torch.empty_like(chi_w)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     w_real = np.linspace(-1.0, 1.0, N_REAL)
+    eps_n = p.eps[p.bands]
+    vstat = eps_n.copy()          # synthetic static part: bare exchange - <V_xc> taken as 0
     stream = torch.cuda.current_stream()
 
     def step(psi_dev, events=None):
@@ -292,9 +301,17 @@ def main():
         mark(2)
         gw.tau_to_omega(ctx, gw.CT, mats["Cinv"], chi_w, w_tau, args.prec)
         mark(3)
+        if args.sigma == "matrix":
+            out = gw.sigma_matrix(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"],
+                                  mats["S"], w_tau, fidx, args.prec)
+            mark(4)
+            mark(5)
+            return out
         out = gw.sigma_diag(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"], mats["S"],
                             w_tau, fidx, args.prec, w_real=w_real)
         mark(4)
+        out["qp"] = gw.qp_energies(ctx, p.omega, out["sigma_iw"], eps_n, p.mu, vstat, w=w_real + p.mu)
+        mark(5)
         return out
 
     for _ in range(args.warmup):
@@ -325,7 +342,7 @@ def main():
     value = job_value(world, fl["total"], args.steps, t_dev)
 
     # per-stage breakdown and the dominant stage's roofline (same stream, CUDA events)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     flush.zero_()
     if args.no_breakdown:
         for e in ev:
@@ -334,7 +351,9 @@ def main():
         step(psi, ev)
     torch.cuda.synchronize()
     stage_ms = {name: ev[i].elapsed_time(ev[i + 1]) for i, name in
-                enumerate(["chi0_omega", "screen_W", "inverse_ct", "sigma_diag"])}
+                enumerate(["chi0_omega", "screen_W", "inverse_ct", "sigma_" + args.sigma, "qp_energies"])}
+    if args.sigma == "matrix":
+        del stage_ms["qp_energies"]
     # per-kernel device time and algorithmic work (library events on the launch stream)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -390,7 +409,8 @@ def main():
     t_e2e = max_over_ranks(float(np.sum(e_times)) if e_times else float("nan"), dist)
     e2e = {"value": job_value(world, fl["total"], args.steps, t_e2e), "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(psi_h.numel() * psi_h.element_size()),
-           "d2h_bytes_per_step": int(len(p.bands) * (3 * n_tau + N_REAL) * 16)}
+           "d2h_bytes_per_step": int(len(p.bands) * (3 * n_tau + N_REAL) * 16 + len(p.bands) * (48 + 8 * N_REAL)
+                                     if args.sigma == "diag" else len(p.bands) ** 2 * 3 * n_tau * 16)}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,

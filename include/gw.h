@@ -260,6 +260,52 @@ gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
                         double* sigma_iw_h, const double* w_real_h, int n_real,
                         double* sigma_real_h, void* stream);
 
+/* Full correlation self-energy matrix Sigma_nm = <psi_n|Sigma|psi_m> over the
+ * listed bands (Eq. Sigma_occ_reduce, first term, for a pair of bands; Eqs.
+ * cos_sin_sigma, sigma_r_w, cos_sin_sigma1/2 element by element):
+ *   Sigma_unocc_nm(tau) = +dV^2 sum_{r,R'} psi_n^*(r) G_unocc(r,R') W~(r,R') psi_m(R')
+ *   Sigma_occ_nm(-tau)  = -dV^2 sum_{r,R'} psi_n^*(r) G_occ(r,R')   W~(r,R') psi_m(R')
+ * (complex; Hermitian in (n, m); the diagonal is gw_sigma_diag's), then
+ *   Sigma_nm(i omega_k) = sum_j C_kj Sigma^c_nm(tau_j) + i sum_j S_kj Sigma^s_nm(tau_j)
+ * with Sigma^c = (Su+So)/2, Sigma^s = (Su-So)/2.  The contraction of
+ * gw_sigma_diag keeps V_m(r) = sum_R' G(r,R') W~(r,R') psi_m(R') per row and
+ * band; an FP64 kernel then adds conj(psi_n(r)) V_m(r) over the rows.
+ * Arguments as for gw_sigma_diag, 1 <= n_n <= 256.  Outputs (host, FP64
+ * complex): sigma_tau_h [2][n_n][n_n][n] = (Su, So) (may be NULL);
+ * sigma_iw_h [n_n][n_n][n].  No continuation (the QP equation needs the
+ * diagonal only).  Synchronous. */
+gw_status gw_sigma_matrix(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
+                          const void* psi, const double* eps_h, double mu, const int32_t* bands_h,
+                          int n_n, int n, const double* tau_h, const double* omega_h,
+                          const double* C_h, const double* S_h, const void* w_tau, int n_chi,
+                          const int32_t* fft_index_h, gw_prec prec, double* sigma_tau_h,
+                          double* sigma_iw_h, void* stream);
+
+/* Quasiparticle energies and spectral functions from the continued
+ * self-energy (Sec. II.E.2, Eqs. QP, GWQP, Z, A).  For every entry b (a band,
+ * or a band and k point) with Sigma_b(i omega_k) at the nodes omega_h [n]
+ * (sigma_iw_h [n_n][n] complex, as gw_sigma_diag returns it), the Thiele
+ * approximant of Eqs. pade1, pade2 is built again and, with real frequencies
+ * measured from mu as in gw_sigma_diag,
+ *   Z_b = 1 / (1 - d Re Sigma_b(w - mu) / dw at w = eps_b)
+ *   E_b = eps_b + Z_b Re(v_b + Sigma_b(eps_b - mu) - eps_b)
+ *   A_b(w) = |Im D| / pi / ((w - eps_b - Re D)^2 + (Im D)^2),  D = v_b + Sigma_b(w - mu) - eps_b.
+ * eps_h [n_n]: the entries' Kohn-Sham energies (Ha); vstat_h [n_n]: the
+ * frequency-independent rest of the paper's Sigma plus <T + V_ne + V_H>
+ * (e.g. bare exchange + core-valence exchange + eps_b - <V_xc>_b).  The
+ * derivative is the continued fraction's own (quotient rule on the backward
+ * recursion), not a finite difference.  w_h [n_w] absolute real energies.
+ * Outputs (host): e_qp_h [n_n]; z_h [n_n], sigma_eps_h [n_n] complex
+ * Sigma_b(eps_b - mu), dsigma_h [n_n] complex derivative (each may be NULL);
+ * spectral_h [n_n][n_w] (1/Ha; needed when n_w > 0).  1 <= n <= 32, distinct
+ * omega > 0.  Synchronous.  GW_ERR_NUMERIC (naming the entry) if a reciprocal
+ * difference or a denominator vanishes or Z is not finite; the other entries
+ * are still returned. */
+gw_status gw_qp_energies(gw_ctx* ctx, int n_n, int n, const double* omega_h, const double* sigma_iw_h,
+                         const double* eps_h, double mu, const double* vstat_h, int n_w,
+                         const double* w_h, double* e_qp_h, double* z_h, double* sigma_eps_h,
+                         double* dsigma_h, double* spectral_h, void* stream);
+
 /* The chi0 chain of Fig. 1 steps (1)-(3) in one call: for every tau_j and every
  * r-block of r_block rows, fused G formation + Hadamard + row transform into the
  * chi(r,G',tau_j) slab (Eqs. chi_rr, FFTX1; chi(r,R') is never stored whole, as

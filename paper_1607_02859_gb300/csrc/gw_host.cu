@@ -215,7 +215,7 @@ extern "C" gw_status gw_ctx_reserve(gw_ctx* ctx, size_t bytes) {
   if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
   return reserve(ctx, bytes);
 }
-extern "C" int gw_version(void) { return 100; }
+extern "C" int gw_version(void) { return 101; }
 
 // ---------------------------------------------------------------------- G set
 

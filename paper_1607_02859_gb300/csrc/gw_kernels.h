@@ -18,11 +18,14 @@ bool row_two_pass(const GridInfo& g, gw_prec prec);
 // gw_sigma.cu: the Sigma contraction over rows of G_occ, G_unocc, W~ (length
 // nr, leading dimension ld) against psi_n (rows of length nr; the row's own
 // value read from psi_row [.][ld_row] if given, else from psi), and the finish
-// (even/odd split, CT + ST, Thiele, results to the host).
+// (even/odd split, CT + ST, Thiele, results to the host).  With vout, the
+// contraction stores V_m(r) in vout [2][n_n][vstride] instead of reducing the
+// diagonal (the matrix Sigma_nm).
 gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wrr, const void* go, const void* gu, long ld,
                                 int nr, int rows, const void* psi, const int* bands, int n_n, int r0, double coef,
                                 double* acc_u, double* acc_o, int acc_stride, cudaStream_t st,
-                                const void* psi_row = nullptr, long ld_row = 0);
+                                const void* psi_row = nullptr, long ld_row = 0, double2* vout = nullptr,
+                                int vstride = 0);
 gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* tab, int n_real, double2* out,
                        int* stat, const int32_t* labels, double* sigma_tau_h, double* sigma_iw_h,
                        double* sigma_real_h, cudaStream_t s);
@@ -78,6 +81,7 @@ namespace gw {
 // scratch each composite call reserves in the context arena
 size_t chi0_omega_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, gw_prec prec, int rb);
 size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* nbatch_out, bool refine = false);
-size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec);
+size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec,
+                     bool full = false);
 gw_status upload_scales(gw_ctx* ctx, void* dst, const GreenScales& gs, gw_prec prec, cudaStream_t st);
 }  // namespace gw

@@ -43,13 +43,15 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-template <typename T>
+// FULL: instead of the diagonal reduction, V_m(r) itself goes to vout
+// [2][n_n][vstride] (occupied, then unoccupied) for the matrix Sigma_nm.
+template <typename T, bool FULL>
 __global__ void __launch_bounds__(kSigThreads) sigma_contract_kernel(
     const typename cpx<T>::t* __restrict__ wrr, const typename cpx<T>::t* __restrict__ go,
     const typename cpx<T>::t* __restrict__ gu, long ld, int nr, int rows,
     const typename cpx<T>::t* __restrict__ psi, const int* __restrict__ bands, int n_n, int r0, double coef,
     double* __restrict__ acc_u, double* __restrict__ acc_o, int acc_stride,
-    const typename cpx<T>::t* __restrict__ psi_row, long ld_row) {
+    const typename cpx<T>::t* __restrict__ psi_row, long ld_row, double2* __restrict__ vout, int vstride) {
   using C = typename cpx<T>::t;
   constexpr int CHUNK = sizeof(T) == 4 ? 512 : 256;          // R' per chunk: 32 KB of psi per buffer
   constexpr int PAIRS = CHUNK / 2;
@@ -127,7 +129,12 @@ __global__ void __launch_bounds__(kSigThreads) sigma_contract_kernel(
         vu[b][0] += __shfl_xor_sync(0xffffffffu, vu[b][0], o2);
         vu[b][1] += __shfl_xor_sync(0xffffffffu, vu[b][1], o2);
       }
-      if (lane == b) {
+      if constexpr (FULL) {
+        if (lane == b && b < nb && active) {
+          vout[(long)(b0 + b) * vstride + r] = make_double2(vo[b][0], vo[b][1]);
+          vout[(long)(n_n + b0 + b) * vstride + r] = make_double2(vu[b][0], vu[b][1]);
+        }
+      } else if (lane == b) {
         double so = 0, su = 0;
         if (b < nb && active) {
           const C pn = psi_row[(long)bands[b0 + b] * ld_row + r0 + r];
@@ -138,6 +145,7 @@ __global__ void __launch_bounds__(kSigThreads) sigma_contract_kernel(
         red[rl][b][1] = su;
       }
     }
+    if constexpr (FULL) continue;
     __syncthreads();
     if (threadIdx.x < 2 * nb) {
       const int b = threadIdx.x >> 1, which = threadIdx.x & 1;
@@ -162,6 +170,49 @@ __device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.
 
 constexpr int kMaxN = 32;
 
+__device__ __forceinline__ bool tiny(double2 a) { return !(sqrt(zabs2(a)) >= 1e-300); }
+
+// Thiele coefficients a_p = g_p(z_p) by reciprocal differences (Eq. pade2).
+// g holds f(z_k) on entry and is overwritten.  False if a difference vanishes.
+__device__ bool thiele_coeffs(double2* g, const double2* z, int n, double2* a) {
+  a[0] = g[0];
+  for (int p = 1; p < n; ++p) {
+    const double2 prev = g[p - 1];
+    for (int m = p; m < n; ++m) {
+      const double2 den = cmul(csub(z[m], z[p - 1]), g[m]);
+      if (tiny(den)) return false;
+      g[m] = zdiv(csub(prev, g[m]), den);
+    }
+    a[p] = g[p];
+  }
+  return true;
+}
+
+// The continued fraction of Eq. pade1 (tail set to zero) at x by backward
+// evaluation, t <- 1 + a_p (x - z_{p-1}) / t from t = 1, value a_1 / t; with
+// dval, also its derivative: each step differentiated by the quotient rule,
+// t' <- a_p / t - a_p (x - z_{p-1}) t' / t^2, and the value's -a_1 t' / t^2.
+// a and z are read through their index (registers or global memory).
+template <typename A, typename Z>
+__device__ bool thiele_eval(const A& a, const Z& z, int n, double2 x, double2* val, double2* dval) {
+  double2 t = make_double2(1.0, 0.0), dt = make_double2(0.0, 0.0);
+  for (int p = n - 1; p >= 1; --p) {
+    if (tiny(t)) return false;
+    const double2 ap = a(p);
+    const double2 u = cmul(ap, csub(x, z(p - 1)));
+    if (dval) dt = csub(zdiv(ap, t), zdiv(cmul(u, dt), cmul(t, t)));
+    const double2 q = zdiv(u, t);
+    t = make_double2(1.0 + q.x, q.y);
+  }
+  if (tiny(t)) return false;
+  *val = zdiv(a(0), t);
+  if (dval) {
+    const double2 d = zdiv(cmul(a(0), dt), cmul(t, t));
+    *dval = make_double2(-d.x, -d.y);
+  }
+  return true;
+}
+
 __global__ void sigma_finish_kernel(const double* __restrict__ acc_u, const double* __restrict__ acc_o, int n_n, int n,
                                     const double* __restrict__ Cm, const double* __restrict__ Sm,
                                     const double* __restrict__ omega, const double* __restrict__ wreal, int n_real,
@@ -169,7 +220,7 @@ __global__ void sigma_finish_kernel(const double* __restrict__ acc_u, const doub
                                     int* __restrict__ status) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_n) return;
-  double2 f[kMaxN], g[kMaxN], a[kMaxN], z[kMaxN];
+  double2 g[kMaxN], a[kMaxN], z[kMaxN];
   for (int k = 0; k < n; ++k) {
     double re = 0, im = 0;
     for (int j = 0; j < n; ++j) {
@@ -178,50 +229,156 @@ __global__ void sigma_finish_kernel(const double* __restrict__ acc_u, const doub
       re += Cm[k * n + j] * sc;
       im += Sm[k * n + j] * ss;
     }
-    f[k] = make_double2(re, im);
-    out_iw[b * n + k] = f[k];
+    g[k] = make_double2(re, im);
+    out_iw[b * n + k] = g[k];
     z[k] = make_double2(0.0, omega[k]);
-    g[k] = f[k];
   }
-  int bad = 0;
-  a[0] = g[0];
-  for (int p = 1; p < n && !bad; ++p) {
-    const double2 prev = g[p - 1];
-    for (int m = p; m < n; ++m) {
-      const double2 dz = make_double2(z[m].x - z[p - 1].x, z[m].y - z[p - 1].y);
-      const double2 den = make_double2(dz.x * g[m].x - dz.y * g[m].y, dz.x * g[m].y + dz.y * g[m].x);
-      if (!(sqrt(zabs2(den)) >= 1e-300)) {
-        bad = 1;
-        break;
-      }
-      g[m] = zdiv(make_double2(prev.x - g[m].x, prev.y - g[m].y), den);
-    }
-    a[p] = g[p];
-  }
+  bool ok = thiele_coeffs(g, z, n, a);
+  auto av = [&](int p) { return a[p]; };
+  auto zv = [&](int p) { return z[p]; };
   for (int q = 0; q < n_real; ++q) {
     double2 res = make_double2(NAN, NAN);
-    if (!bad) {
-      const double2 x = make_double2(wreal[q], 0.0);
-      double2 t = make_double2(1.0, 0.0);
-      for (int p = n - 1; p >= 1 && !bad; --p) {
-        if (!(sqrt(zabs2(t)) >= 1e-300)) { bad = 1; break; }
-        const double2 dx = make_double2(x.x - z[p - 1].x, x.y - z[p - 1].y);
-        const double2 num = make_double2(a[p].x * dx.x - a[p].y * dx.y, a[p].x * dx.y + a[p].y * dx.x);
-        const double2 qv = zdiv(num, t);
-        t = make_double2(1.0 + qv.x, qv.y);
-      }
-      if (!bad && sqrt(zabs2(t)) >= 1e-300) res = zdiv(a[0], t);
-      else bad = 1;
-    }
+    if (ok) ok = thiele_eval(av, zv, n, make_double2(wreal[q], 0.0), &res, nullptr);
+    if (!ok) res = make_double2(NAN, NAN);
     if (out_real) out_real[b * n_real + q] = res;
   }
-  status[b] = bad;
+  status[b] = ok ? 0 : 1;
+}
+
+// ---------------------------------------------------------------- full matrix
+// Sigma_nm(tau_j) += coef conj(psi_n(r0 + r)) V_m(r) summed over rows for the
+// unoccupied V (plus) and the occupied V (minus); one thread per (n, m) of a
+// 16 x 16 tile (blockIdx.x, blockIdx.y) and rows_per_cta rows per CTA
+// (blockIdx.z), staged 32 at a time in shared memory; the CTAs' partial sums
+// meet in FP64 atomics.  acc_u / acc_o are [n_n][n_n][acc_stride] complex,
+// already offset to tau_j.  Spreading the rows over CTAs matters: the sums are
+// FP64, whose per-SM rate is low.
+template <typename T>
+__global__ void __launch_bounds__(256) sigma_outer_kernel(const double2* __restrict__ vout, int vstride, int rows,
+                                                          int rows_per_cta,
+                                                          const typename cpx<T>::t* __restrict__ psi_row, long ld_row,
+                                                          const int* __restrict__ bands, int n_n, int r0, double coef,
+                                                          double2* __restrict__ acc_u, double2* __restrict__ acc_o,
+                                                          int acc_stride) {
+  __shared__ double2 sp[16][33], svo[16][33], svu[16][33];
+  const int n0 = blockIdx.y * 16, m0 = blockIdx.x * 16;
+  const int tn = threadIdx.x >> 4, tm = threadIdx.x & 15;
+  const int c0 = blockIdx.z * rows_per_cta, c1 = min(rows, c0 + rows_per_cta);
+  const double2* vo = vout;
+  const double2* vu = vout + (long)n_n * vstride;
+  double2 ao = make_double2(0.0, 0.0), au = make_double2(0.0, 0.0);
+  for (int c = c0; c < c1; c += 32) {
+    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+      const int i = e >> 5, r = e & 31;
+      const bool in = c + r < c1;
+      double2 pv = make_double2(0.0, 0.0), o = pv, u = pv;
+      if (in && n0 + i < n_n) {
+        const auto v = psi_row[(long)bands[n0 + i] * ld_row + r0 + c + r];
+        pv = make_double2((double)v.x, (double)v.y);
+      }
+      if (in && m0 + i < n_n) {
+        o = vo[(long)(m0 + i) * vstride + c + r];
+        u = vu[(long)(m0 + i) * vstride + c + r];
+      }
+      sp[i][r] = pv;
+      svo[i][r] = o;
+      svu[i][r] = u;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const double2 pv = sp[tn][r];
+      ao = cadd(ao, cmul(cconj(pv), svo[tm][r]));
+      au = cadd(au, cmul(cconj(pv), svu[tm][r]));
+    }
+    __syncthreads();
+  }
+  if (n0 + tn < n_n && m0 + tm < n_n) {
+    const long idx = ((long)(n0 + tn) * n_n + (m0 + tm)) * acc_stride;
+    double* po = reinterpret_cast<double*>(acc_o + idx);
+    double* pu = reinterpret_cast<double*>(acc_u + idx);
+    atomicAdd(po, -coef * ao.x);
+    atomicAdd(po + 1, -coef * ao.y);
+    atomicAdd(pu, coef * au.x);
+    atomicAdd(pu + 1, coef * au.y);
+  }
+}
+
+// Sigma_nm(i omega_k) = sum_j C_kj Sigma^c_nm(tau_j) + i sum_j S_kj Sigma^s_nm(tau_j)
+// on the complex matrices (Eqs. cos_sin_sigma, sigma_r_w, cos_sin_sigma1/2);
+// one thread per (n, m, k).
+__global__ void sigma_matrix_finish_kernel(const double2* __restrict__ acc_u, const double2* __restrict__ acc_o,
+                                           int nnm, int n, const double* __restrict__ Cm,
+                                           const double* __restrict__ Sm, double2* __restrict__ out_iw) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)nnm * n) return;
+  const long e = t / n;
+  const int k = (int)(t - e * n);
+  double2 c = make_double2(0.0, 0.0), sn = c;
+  for (int j = 0; j < n; ++j) {
+    const double2 u = acc_u[e * n + j], o = acc_o[e * n + j];
+    c = cadd(c, cscale(cscale(cadd(u, o), 0.5), Cm[k * n + j]));
+    sn = cadd(sn, cscale(cscale(csub(u, o), 0.5), Sm[k * n + j]));
+  }
+  out_iw[t] = cadd(c, cmuli(sn));
+}
+
+// ---------------------------------------------------------------- QP energies
+// Thiele coefficients of every band's Sigma_n through z_k = i omega_k.
+__global__ void qp_coeff_kernel(const double2* __restrict__ sig, const double* __restrict__ omega, int n_n, int n,
+                                double2* __restrict__ coef, int* __restrict__ status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_n) return;
+  double2 g[kMaxN], a[kMaxN], z[kMaxN];
+  for (int k = 0; k < n; ++k) {
+    g[k] = sig[(long)b * n + k];
+    z[k] = make_double2(0.0, omega[k]);
+  }
+  const bool ok = thiele_coeffs(g, z, n, a);
+  for (int k = 0; k < n; ++k) coef[(long)b * n + k] = ok ? a[k] : make_double2(NAN, NAN);
+  status[b] = ok ? 0 : 1;
+}
+
+// One thread per (band, point).  Point 0: the linearised QP equation at eps_n
+// (Eqs. QP, GWQP, Z) with Sigma_n(eps_n - mu) and its derivative; points
+// 1..n_w: the spectral function of Eq. A at w_q, with
+// DeltaSigma = v_n + Sigma_n(w - mu) - eps_n.
+__global__ void qp_eval_kernel(const double2* __restrict__ coef, const double* __restrict__ omega, int n_n, int n,
+                               const double* __restrict__ eps, const double* __restrict__ vstat, double mu,
+                               const double* __restrict__ w, int n_w, double* __restrict__ e_qp,
+                               double* __restrict__ zf, double2* __restrict__ s_eps, double2* __restrict__ ds,
+                               double* __restrict__ spec, int* __restrict__ status) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)n_n * (n_w + 1)) return;
+  const int b = (int)(t / (n_w + 1));
+  const int q = (int)(t - (long)b * (n_w + 1));
+  const double2* ab = coef + (long)b * n;
+  auto av = [&](int p) { return ab[p]; };
+  auto zv = [&](int p) { return make_double2(0.0, omega[p]); };
+  const double e = eps[b];
+  double2 val = make_double2(NAN, NAN), dval = val;
+  if (q == 0) {
+    const bool ok = (status[b] & 1) == 0 && thiele_eval(av, zv, n, make_double2(e - mu, 0.0), &val, &dval);
+    const double z = ok ? 1.0 / (1.0 - dval.x) : NAN;
+    s_eps[b] = ok ? val : make_double2(NAN, NAN);
+    ds[b] = ok ? dval : make_double2(NAN, NAN);
+    zf[b] = z;
+    e_qp[b] = e + z * (vstat[b] + val.x - e);
+    if (!ok || !isfinite(z)) atomicOr(status + b, 2);
+  } else {
+    const double x = w[q - 1];
+    const bool ok = (status[b] & 1) == 0 && thiele_eval(av, zv, n, make_double2(x - mu, 0.0), &val, nullptr);
+    const double dre = vstat[b] + val.x - e, dim = val.y;
+    const double d = x - e - dre;
+    spec[(long)b * n_w + q - 1] = ok ? fabs(dim) / kPi / (d * d + dim * dim) : NAN;
+    if (!ok) atomicOr(status + b, 4);
+  }
 }
 
 gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wrr, const void* go, const void* gu, long ld,
                                 int nr, int rows, const void* psi, const int* bands, int n_n, int r0, double coef,
                                 double* acc_u, double* acc_o, int acc_stride, cudaStream_t st, const void* psi_row,
-                                long ld_row) {
+                                long ld_row, double2* vout, int vstride) {
   if (rows <= 0) return GW_OK;
   if (!psi_row) {
     psi_row = psi;
@@ -237,11 +394,34 @@ gw_status launch_sigma_contract(gw_ctx* ctx, gw_prec prec, const void* wrr, cons
     KTimer kt(ctx, KF_SIGMA, 3.0 * rows * (double)nr * esz, st);
     kernel<<<grid, kSigThreads, bytes, st>>>((const C*)wrr, (const C*)go, (const C*)gu, ld, nr, rows, (const C*)psi,
                                              bands, n_n, r0, coef, acc_u, acc_o, acc_stride, (const C*)psi_row,
-                                             ld_row);
+                                             ld_row, vout, vstride);
     return launch_check(ctx, "sigma_contract_kernel");
   };
-  if (is_fp64(prec)) return go_(sigma_contract_kernel<double>, sizeof(double2), 2 * 256, (double2*)nullptr);
-  return go_(sigma_contract_kernel<float>, sizeof(float2), 2 * 512, (float2*)nullptr);
+  if (vout) {
+    if (is_fp64(prec)) return go_(sigma_contract_kernel<double, true>, sizeof(double2), 2 * 256, (double2*)nullptr);
+    return go_(sigma_contract_kernel<float, true>, sizeof(float2), 2 * 512, (float2*)nullptr);
+  }
+  if (is_fp64(prec)) return go_(sigma_contract_kernel<double, false>, sizeof(double2), 2 * 256, (double2*)nullptr);
+  return go_(sigma_contract_kernel<float, false>, sizeof(float2), 2 * 512, (float2*)nullptr);
+}
+
+// The matrix update of one block of rows from the V_m(r) of the contraction.
+static gw_status launch_sigma_outer(gw_ctx* ctx, gw_prec prec, const double2* vout, int vstride, int rows,
+                                    const void* psi, long ld, const int* bands, int n_n, int r0, double coef,
+                                    double2* acc_u, double2* acc_o, int acc_stride, cudaStream_t st) {
+  if (rows <= 0) return GW_OK;
+  // about two CTAs per SM in all, rows split in multiples of 32
+  const long tiles = (long)((n_n + 15) / 16) * ((n_n + 15) / 16);
+  const long splits = std::max(1L, 2L * ctx->num_sms / tiles);
+  const int rpc = (int)std::max(32L, ((rows + splits - 1) / splits + 31) / 32 * 32);
+  const dim3 grid((n_n + 15) / 16, (n_n + 15) / 16, (rows + rpc - 1) / rpc);
+  if (is_fp64(prec))
+    sigma_outer_kernel<double><<<grid, 256, 0, st>>>(vout, vstride, rows, rpc, (const double2*)psi, ld, bands, n_n, r0,
+                                                     coef, acc_u, acc_o, acc_stride);
+  else
+    sigma_outer_kernel<float><<<grid, 256, 0, st>>>(vout, vstride, rows, rpc, (const float2*)psi, ld, bands, n_n, r0,
+                                                    coef, acc_u, acc_o, acc_stride);
+  return launch_check(ctx, "sigma_outer_kernel");
 }
 
 // Even/odd split, CT + ST and Thiele continuation of the accumulated
@@ -277,18 +457,21 @@ gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* t
   return GW_OK;
 }
 
-size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec) {
+size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec,
+                     bool full) {
   const size_t es = csize(prec);
   const int rb = std::min(g.nr, 2048);
+  const size_t nnm = full ? (size_t)n_n * n_n : (size_t)n_n;
   Carver probe(nullptr);
   probe.take<int>(n_chi);
   probe.take<int>(g.nr);
   probe.take<int>(n_n);
   probe.take<double>((size_t)n * n_b);
   probe.take<double>(4 * (size_t)n * n + 2 * n + std::max(n_real, 1));
-  probe.take<double>(2 * (size_t)n_n * n);
-  probe.take<double2>((size_t)n_n * n + (size_t)n_n * std::max(n_real, 1));
+  probe.take<double2>((full ? 2 : 1) * nnm * n);   // acc: [2][n_n][n] real, or [2][n_n][n_n][n] complex
+  probe.take<double2>(nnm * n + (size_t)n_n * std::max(n_real, 1));
   probe.take<int>(n_n);
+  if (full) probe.take<double2>(2 * (size_t)n_n * rb);
   probe.take<char>((size_t)g.nr * n_chi * es);
   probe.take<char>((size_t)rb * g.nr * es);
   probe.take<char>((size_t)rb * g.nr * es);
@@ -301,12 +484,14 @@ size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, in
 
 using namespace gw;
 
-extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
-                                   const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n,
-                                   const double* tau_h, const double* omega_h, const double* C_h, const double* S_h,
-                                   const void* w_tau, int n_chi, const int32_t* fft_index_h, gw_prec prec,
-                                   double* sigma_tau_h, double* sigma_iw_h, const double* w_real_h, int n_real,
-                                   double* sigma_real_h, void* stream) {
+// Shared body of gw_sigma_diag (full = false: acc real [2][n_n][n], Thiele
+// continuation) and gw_sigma_matrix (full = true: acc complex [2][n_n][n_n][n]).
+static gw_status sigma_impl(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
+                            const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n,
+                            const double* tau_h, const double* omega_h, const double* C_h, const double* S_h,
+                            const void* w_tau, int n_chi, const int32_t* fft_index_h, gw_prec prec, bool full,
+                            double* sigma_tau_h, double* sigma_iw_h, const double* w_real_h, int n_real,
+                            double* sigma_real_h, cudaStream_t s) {
   if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
   GridInfo g;
   gw_status st = grid_info(ctx, grid, &g);
@@ -319,7 +504,8 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   if (reinterpret_cast<uintptr_t>(psi) % 16) return fail(ctx, GW_ERR_ARG, "psi must be 16-byte aligned");
   if ((st = check_energies(ctx, eps_h, n_b, n_occ, mu))) return st;
   if (n < 1 || n > kMaxN) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
-  if (n_n < 1 || n_n > 1024) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_n <= 1024");
+  if (n_n < 1 || n_n > (full ? 256 : 1024))
+    return fail(ctx, GW_ERR_SHAPE, full ? "need 1 <= n_n <= 256" : "need 1 <= n_n <= 1024");
   if (n_real < 0 || (n_real > 0 && (!w_real_h || !sigma_real_h))) return fail(ctx, GW_ERR_ARG, "bad real-axis request");
   for (int b = 0; b < n_n; ++b)
     if (bands_h[b] < 0 || bands_h[b] >= n_b) return fail(ctx, GW_ERR_ARG, "band index out of range");
@@ -327,11 +513,11 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
     if (!(tau_h[j] > 0)) return fail(ctx, GW_ERR_ARG, "tau must be > 0");
   std::vector<int> map, inv;
   if ((st = index_maps(ctx, g, fft_index_h, n_chi, map, inv))) return st;
-  cudaStream_t s = as_stream(stream);
   const size_t es = csize(prec);
   const int rb = std::min(g.nr, 2048);
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
-  if ((st = reserve(ctx, sigma_scratch(g, n_b, n_occ, n, n_chi, n_n, n_real, prec)))) return st;
+  const size_t nnm = full ? (size_t)n_n * n_n : (size_t)n_n;
+  if ((st = reserve(ctx, sigma_scratch(g, n_b, n_occ, n, n_chi, n_n, n_real, prec, full)))) return st;
   Carver cv(ctx->arena);
   int* dmap = cv.take<int>(n_chi);
   int* dinv = cv.take<int>(g.nr);
@@ -341,10 +527,12 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   double* dS = dC + (size_t)n * n;
   double* dom = dS + (size_t)n * n;
   double* dwr = dom + n;
-  double* acc = cv.take<double>(2 * (size_t)n_n * n);
-  double2* out_iw = cv.take<double2>((size_t)n_n * n + (size_t)n_n * std::max(n_real, 1));
-  double2* out_re = out_iw + (size_t)n_n * n;
+  const size_t acc_elems = (full ? 2 : 1) * nnm * n;     // in double2: [2][n_n][n] real or [2][n_n][n_n][n] complex
+  double2* acc2 = cv.take<double2>(acc_elems);
+  double* acc = reinterpret_cast<double*>(acc2);
+  double2* out_iw = cv.take<double2>(nnm * n + (size_t)n_n * std::max(n_real, 1));
   int* dstat = cv.take<int>(n_n);
+  double2* vout = full ? cv.take<double2>(2 * (size_t)n_n * rb) : nullptr;
   char* wrg = cv.take<char>((size_t)g.nr * n_chi * es);
   char* gob = cv.take<char>((size_t)rb * g.nr * es);
   char* gub = cv.take<char>((size_t)rb * g.nr * es);
@@ -363,9 +551,11 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   if ((st = upload(ctx, dS, S_h, sizeof(double) * n * n, s))) return st;
   if ((st = upload(ctx, dom, omega_h, sizeof(double) * n, s))) return st;
   if (n_real > 0 && (st = upload(ctx, dwr, w_real_h, sizeof(double) * n_real, s))) return st;
-  if ((st = cuda_check(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * 2 * n_n * n, s), "memset"))) return st;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(acc2, 0, sizeof(double2) * acc_elems, s), "memset"))) return st;
   double* acc_u = acc;
   double* acc_o = acc + (size_t)n_n * n;
+  double2* accm_u = acc2;
+  double2* accm_o = acc2 + nnm * n;
   const double coef = g.dv * g.dv / g.volume;   // dV^2 and the 1/Omega of Eq. FFTW
   bool first = true;
   for (int j = 0; j < n; ++j) {
@@ -384,11 +574,134 @@ extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, in
       if ((st = launch_row_fft(ctx, g, prec, 2, wrg + (size_t)r0 * n_chi * es, nullptr, n_chi, wrr, g.nr, dmap, n_chi,
                                rows, 1.0, s, dinv)))
         return st;
-      if ((st = launch_sigma_contract(ctx, prec, wrr, gob, gub, g.nr, g.nr, rows, psi, dbands, n_n, r0, coef,
-                                      acc_u + j, acc_o + j, n, s)))
-        return st;
+      if (!full) {
+        if ((st = launch_sigma_contract(ctx, prec, wrr, gob, gub, g.nr, g.nr, rows, psi, dbands, n_n, r0, coef,
+                                        acc_u + j, acc_o + j, n, s)))
+          return st;
+      } else {
+        if ((st = launch_sigma_contract(ctx, prec, wrr, gob, gub, g.nr, g.nr, rows, psi, dbands, n_n, r0, coef,
+                                        nullptr, nullptr, n, s, nullptr, 0, vout, rb)))
+          return st;
+        if ((st = launch_sigma_outer(ctx, prec, vout, rb, rows, psi, g.nr, dbands, n_n, r0, coef, accm_u + j,
+                                     accm_o + j, n, s)))
+          return st;
+      }
     }
   }
   if (tc && (st = tc_check(ctx, tcs, s))) return st;
-  return sigma_finish(ctx, acc, n_n, n, dC, n_real, out_iw, dstat, bands_h, sigma_tau_h, sigma_iw_h, sigma_real_h, s);
+  if (!full)
+    return sigma_finish(ctx, acc, n_n, n, dC, n_real, out_iw, dstat, bands_h, sigma_tau_h, sigma_iw_h, sigma_real_h, s);
+  const long tot = (long)nnm * n;
+  sigma_matrix_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(accm_u, accm_o, (int)nnm, n, dC, dS, out_iw);
+  if ((st = launch_check(ctx, "sigma_matrix_finish_kernel"))) return st;
+  std::vector<double2> h_iw(nnm * n), h_acc(2 * nnm * n);
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(h_iw.data(), out_iw, sizeof(double2) * nnm * n, cudaMemcpyDeviceToHost, s),
+                       "copy sigma")))
+    return st;
+  if (sigma_tau_h && (st = cuda_check(ctx, cudaMemcpyAsync(h_acc.data(), acc2, sizeof(double2) * 2 * nnm * n,
+                                                           cudaMemcpyDeviceToHost, s), "copy sigma")))
+    return st;
+  if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sigma sync"))) return st;
+  std::memcpy(sigma_iw_h, h_iw.data(), sizeof(double2) * nnm * n);
+  if (sigma_tau_h) std::memcpy(sigma_tau_h, h_acc.data(), sizeof(double2) * 2 * nnm * n);
+  return GW_OK;
+}
+
+extern "C" gw_status gw_sigma_diag(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
+                                   const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n,
+                                   const double* tau_h, const double* omega_h, const double* C_h, const double* S_h,
+                                   const void* w_tau, int n_chi, const int32_t* fft_index_h, gw_prec prec,
+                                   double* sigma_tau_h, double* sigma_iw_h, const double* w_real_h, int n_real,
+                                   double* sigma_real_h, void* stream) {
+  return sigma_impl(ctx, grid, n_b, n_occ, psi, eps_h, mu, bands_h, n_n, n, tau_h, omega_h, C_h, S_h, w_tau, n_chi,
+                    fft_index_h, prec, false, sigma_tau_h, sigma_iw_h, w_real_h, n_real, sigma_real_h,
+                    as_stream(stream));
+}
+
+extern "C" gw_status gw_sigma_matrix(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
+                                     const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n,
+                                     const double* tau_h, const double* omega_h, const double* C_h, const double* S_h,
+                                     const void* w_tau, int n_chi, const int32_t* fft_index_h, gw_prec prec,
+                                     double* sigma_tau_h, double* sigma_iw_h, void* stream) {
+  return sigma_impl(ctx, grid, n_b, n_occ, psi, eps_h, mu, bands_h, n_n, n, tau_h, omega_h, C_h, S_h, w_tau, n_chi,
+                    fft_index_h, prec, true, sigma_tau_h, sigma_iw_h, nullptr, 0, nullptr, as_stream(stream));
+}
+
+extern "C" gw_status gw_qp_energies(gw_ctx* ctx, int n_n, int n, const double* omega_h, const double* sigma_iw_h,
+                                    const double* eps_h, double mu, const double* vstat_h, int n_w, const double* w_h,
+                                    double* e_qp_h, double* z_h, double* sigma_eps_h, double* dsigma_h,
+                                    double* spectral_h, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  if (n < 1 || n > kMaxN) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
+  if (n_n < 1 || n_n > (1 << 20)) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n_n <= 2^20");
+  if (n_w < 0 || n_w > (1 << 24)) return fail(ctx, GW_ERR_SHAPE, "need 0 <= n_w <= 2^24");
+  if (!omega_h || !sigma_iw_h || !eps_h || !vstat_h || !e_qp_h) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  if (n_w > 0 && (!w_h || !spectral_h)) return fail(ctx, GW_ERR_ARG, "n_w > 0 needs w_h and spectral_h");
+  for (int k = 0; k < n; ++k)
+    if (!(omega_h[k] > 0)) return fail(ctx, GW_ERR_ARG, "omega must be > 0");
+  for (int k = 1; k < n; ++k)
+    if (!(omega_h[k] != omega_h[k - 1])) return fail(ctx, GW_ERR_ARG, "omega nodes must be distinct");
+  cudaStream_t s = as_stream(stream);
+  const size_t nw1 = std::max(n_w, 1);
+  // layout: Sigma(i omega), coefficients, omega, eps, v, w, E, Z, Sigma(eps), dSigma, A, status
+  auto carve = [&](Carver& c, double2** sig, double2** cf, double** om, double** ep, double** vs, double** w,
+                   double** e, double** z, double2** se, double2** ds, double** sp, int** stat) {
+    *sig = c.take<double2>((size_t)n_n * n);
+    *cf = c.take<double2>((size_t)n_n * n);
+    *om = c.take<double>(n);
+    *ep = c.take<double>(n_n);
+    *vs = c.take<double>(n_n);
+    *w = c.take<double>(nw1);
+    *e = c.take<double>(n_n);
+    *z = c.take<double>(n_n);
+    *se = c.take<double2>(n_n);
+    *ds = c.take<double2>(n_n);
+    *sp = c.take<double>((size_t)n_n * nw1);
+    *stat = c.take<int>(n_n);
+  };
+  double2 *dsig, *dcf, *dse, *dds;
+  double *dom, *deps, *dvs, *dw, *de, *dz, *dsp;
+  int* dstat;
+  Carver probe(nullptr);
+  carve(probe, &dsig, &dcf, &dom, &deps, &dvs, &dw, &de, &dz, &dse, &dds, &dsp, &dstat);
+  gw_status st;
+  if ((st = reserve(ctx, probe.off))) return st;
+  Carver cv(ctx->arena);
+  carve(cv, &dsig, &dcf, &dom, &deps, &dvs, &dw, &de, &dz, &dse, &dds, &dsp, &dstat);
+  if ((st = upload(ctx, dsig, sigma_iw_h, sizeof(double2) * n_n * n, s))) return st;
+  if ((st = upload(ctx, dom, omega_h, sizeof(double) * n, s))) return st;
+  if ((st = upload(ctx, deps, eps_h, sizeof(double) * n_n, s))) return st;
+  if ((st = upload(ctx, dvs, vstat_h, sizeof(double) * n_n, s))) return st;
+  if (n_w > 0 && (st = upload(ctx, dw, w_h, sizeof(double) * n_w, s))) return st;
+  qp_coeff_kernel<<<(n_n + 63) / 64, 64, 0, s>>>(dsig, dom, n_n, n, dcf, dstat);
+  if ((st = launch_check(ctx, "qp_coeff_kernel"))) return st;
+  const long pts = (long)n_n * (n_w + 1);
+  qp_eval_kernel<<<(unsigned)((pts + 127) / 128), 128, 0, s>>>(dcf, dom, n_n, n, deps, dvs, mu, dw, n_w, de, dz, dse,
+                                                              dds, dsp, dstat);
+  if ((st = launch_check(ctx, "qp_eval_kernel"))) return st;
+  std::vector<double> h_e(n_n), h_z(n_n), h_sp(n_w > 0 ? (size_t)n_n * n_w : 0);
+  std::vector<double2> h_se(n_n), h_ds(n_n);
+  std::vector<int> h_stat(n_n);
+  auto d2h = [&](void* dst, const void* src, size_t bytes) {
+    return cuda_check(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s), "copy qp");
+  };
+  if ((st = d2h(h_e.data(), de, sizeof(double) * n_n))) return st;
+  if ((st = d2h(h_z.data(), dz, sizeof(double) * n_n))) return st;
+  if ((st = d2h(h_se.data(), dse, sizeof(double2) * n_n))) return st;
+  if ((st = d2h(h_ds.data(), dds, sizeof(double2) * n_n))) return st;
+  if (n_w > 0 && (st = d2h(h_sp.data(), dsp, sizeof(double) * n_n * n_w))) return st;
+  if ((st = d2h(h_stat.data(), dstat, sizeof(int) * n_n))) return st;
+  if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "qp sync"))) return st;
+  std::memcpy(e_qp_h, h_e.data(), sizeof(double) * n_n);
+  if (z_h) std::memcpy(z_h, h_z.data(), sizeof(double) * n_n);
+  if (sigma_eps_h) std::memcpy(sigma_eps_h, h_se.data(), sizeof(double2) * n_n);
+  if (dsigma_h) std::memcpy(dsigma_h, h_ds.data(), sizeof(double2) * n_n);
+  if (n_w > 0) std::memcpy(spectral_h, h_sp.data(), sizeof(double) * n_n * n_w);
+  for (int b = 0; b < n_n; ++b)
+    if (h_stat[b])
+      return fail(ctx, GW_ERR_NUMERIC, std::string(h_stat[b] & 1 ? "Thiele coefficients broke down" :
+                                                    h_stat[b] & 2 ? "QP equation not finite" :
+                                                                    "Thiele evaluation broke down") +
+                                            " for entry " + std::to_string(b));
+  return GW_OK;
 }

@@ -27,7 +27,8 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_ctx_set_timing", "gw_ctx_kernel_stats", "gw_version", "gw_g_set", "gw_coulomb_sqrt", "gw_fit_transform", "gw_green_tau", "gw_chi0_rtau",
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
            "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh", "gw_sigma_diag_kmesh",
-           "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy"]
+           "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
+           "gw_sigma_matrix", "gw_qp_energies"]
 
 
 class GwError(RuntimeError):
@@ -81,6 +82,9 @@ _SIGS = {
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                            _DP, _DP, _DP, _I, _DP, _P]),
     "gw_chi0_omega": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
+    "gw_sigma_matrix": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
+                             _DP, _DP, _P]),
+    "gw_qp_energies": (_I, [_P, _I, _I, _DP, _DP, _DP, _D, _DP, _I, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
 }
 
 _lib = None
@@ -337,6 +341,52 @@ def sigma_diag(ctx, grid, psi, eps, n_occ, mu, bands, tau, omega, C, S, w_tau, f
     out = {"sigma_unocc": s_tau[0], "sigma_occ": s_tau[1], "sigma_iw": s_iw}
     if n_real:
         out["sigma_real"] = s_re
+    return out
+
+
+def sigma_matrix(ctx, grid, psi, eps, n_occ, mu, bands, tau, omega, C, S, w_tau, fft_index, prec):
+    """Full self-energy matrix over the listed bands (gw_sigma_matrix): a dict with
+    sigma_unocc, sigma_occ [n_n][n_n][n] and sigma_iw [n_n][n_n][n], complex."""
+    p = prec_of(prec)
+    bands = _i32(bands)
+    tau = _f64(tau)
+    idx = _i32(fft_index)
+    n = len(tau)
+    n_n = len(bands)
+    s_tau = np.zeros((2, n_n, n_n, n), dtype=np.complex128)
+    s_iw = np.zeros((n_n, n_n, n), dtype=np.complex128)
+    st = lib().gw_sigma_matrix(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p),
+                               _dp(_f64(eps)), float(mu), _ip(bands), n_n, n, _dp(tau), _dp(_f64(omega)),
+                               _dp(_f64(C)), _dp(_f64(S)), _dev(w_tau, "w_tau", p), len(idx), _ip(idx), p,
+                               s_tau.ctypes.data_as(_DP), s_iw.ctypes.data_as(_DP), _stream())
+    _check(st, ctx)
+    return {"sigma_unocc": s_tau[0], "sigma_occ": s_tau[1], "sigma_iw": s_iw}
+
+
+def qp_energies(ctx, omega, sigma_iw, eps, mu, vstat, w=None):
+    """Linearised QP energies and spectral functions (gw_qp_energies): a dict with
+    e_qp, z [n_n], sigma_eps, dsigma [n_n] complex and, if w is given, spectral [n_n][len(w)]."""
+    omega = _f64(omega)
+    sig = np.ascontiguousarray(np.atleast_2d(sigma_iw), dtype=np.complex128)
+    n_n, n = sig.shape
+    eps = _f64(np.atleast_1d(eps))
+    vstat = _f64(np.atleast_1d(vstat))
+    if len(omega) != n or len(eps) != n_n or len(vstat) != n_n:
+        raise ValueError("sizes of omega, sigma_iw, eps and vstat disagree")
+    wv = None if w is None else _f64(w)
+    n_w = 0 if wv is None else len(wv)
+    e = np.zeros(n_n)
+    z = np.zeros(n_n)
+    se = np.zeros(n_n, dtype=np.complex128)
+    ds = np.zeros(n_n, dtype=np.complex128)
+    sp = np.zeros((n_n, max(n_w, 1)))
+    st = lib().gw_qp_energies(ctx.handle, n_n, n, _dp(omega), sig.ctypes.data_as(_DP), _dp(eps), float(mu),
+                              _dp(vstat), n_w, _dp(wv), _dp(e), _dp(z), se.ctypes.data_as(_DP),
+                              ds.ctypes.data_as(_DP), sp.ctypes.data_as(_DP) if n_w else None, _stream())
+    _check(st, ctx)
+    out = {"e_qp": e, "z": z, "sigma_eps": se, "dsigma": ds}
+    if n_w:
+        out["spectral"] = sp
     return out
 
 

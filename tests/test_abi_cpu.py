@@ -32,7 +32,7 @@ def test_exports_match_header(L):
 
 
 def test_version(L):
-    assert gw.lib().gw_version() == 100
+    assert gw.lib().gw_version() == 101
 
 
 @pytest.mark.parametrize("n,n_chi", [((6, 6, 6), 216), ((8, 6, 10), 120), ((12, 12, 12), 500), ((24, 24, 24), 13824)])
