@@ -62,6 +62,7 @@ def transform_matrices(tau, omega, x_min, x_max, n_x=4000, ridge=1e-6):
     C[k][j]    = gamma_kj cos(omega_k tau_j)           (Eq. CT_FFT)
     S[k][j]    = lambda_kj sin(omega_k tau_j)          (Eq. ST_FFT; times i)
     Cinv[j][k] = xi_jk cos(tau_j omega_k) = C^{-1}     (Eq. INV_CT_FFT)
+    Sinv[j][k] = zeta_jk sin(tau_j omega_k) = S^{-1}   (Eq. INV_ST_FFT; times -i)
     """
     tau = np.asarray(tau, dtype=np.float64)
     omega = np.asarray(omega, dtype=np.float64)
@@ -71,5 +72,6 @@ def transform_matrices(tau, omega, x_min, x_max, n_x=4000, ridge=1e-6):
     C = gamma * np.cos(wt)
     S = lam * np.sin(wt)
     Cinv = np.linalg.inv(C)
-    return {"C": C, "S": S, "Cinv": Cinv, "gamma": gamma, "lambda": lam,
+    Sinv = np.linalg.inv(S)
+    return {"C": C, "S": S, "Cinv": Cinv, "Sinv": Sinv, "gamma": gamma, "lambda": lam,
             "fit_err_cos": err_c, "fit_err_sin": err_s}

@@ -146,3 +146,28 @@ def sigma_matrix_iw(s_unocc, s_occ, C, S):
     sc = 0.5 * (s_unocc + s_occ)
     ss = 0.5 * (s_unocc - s_occ)
     return sc @ C.T + 1j * (ss @ S.T)
+
+
+def sigma_tau_from_iw(sig_iw, Cinv, Sinv):
+    """Back to imaginary time (Eqs. INV_CT_FFT, INV_ST_FFT): the inverse of
+    sigma_iw / sigma_matrix_iw.  Sigma(i omega) = C Sigma^c + i S Sigma^s with
+    Sigma^c(tau), Sigma^s(tau) Hermitian in the band indices (real on the
+    diagonal) and C, S real, so C Sigma^c is the Hermitian part of Sigma(i omega)
+    and i S Sigma^s its anti-Hermitian part; then
+        Sigma^c(tau_j) = sum_k Cinv_jk [Herm Sigma](i omega_k)
+        Sigma^s(tau_j) = -i sum_k Sinv_jk [AntiHerm Sigma](i omega_k)
+    and Sigma_unocc(tau) = Sigma^c + Sigma^s, Sigma_occ(-tau) = Sigma^c - Sigma^s.
+    sig_iw is [N_n][N] (diagonal elements: Hermitian part = real part) or
+    [N_n][N_n][N] (matrix).  Returns (Su, So) of the same shape."""
+    sig = np.asarray(sig_iw)
+    if sig.ndim == 2:
+        herm, anti = sig.real.astype(np.complex128), 1j * sig.imag
+    else:
+        sh = sig.conj().transpose(1, 0, 2)
+        herm, anti = 0.5 * (sig + sh), 0.5 * (sig - sh)
+    sc = herm @ Cinv.T
+    ss = -1j * (anti @ Sinv.T)
+    su, so = sc + ss, sc - ss
+    if sig.ndim == 2:
+        return su.real, so.real
+    return su, so

@@ -213,3 +213,31 @@ def test_matrix_single_pole_closed_form():
                 ls = 2 * p.omega / (x ** 2 + p.omega ** 2)
                 bound += abs(w_nl) * 0.5 * (s["fit_err_cos"] * lc + s["fit_err_sin"] * ls)
             assert np.all(np.abs(sig[i, k] - exact) <= 1.05 * bound + 1e-14)
+
+
+# ---------------------------------------------------------------- inverse transforms
+
+def test_inverse_sine_transform_and_sigma_round_trip():
+    """Eq. INV_ST_FFT: Sinv S = S Sinv = 1; Sigma(i omega) of random Hermitian
+    Sigma_unocc(tau), Sigma_occ(-tau) matrices (and of real diagonals) goes
+    back to them through the Hermitian / anti-Hermitian split."""
+    p = inputs.tiny(seed=9, n_tau=12)
+    s = opipe.setup(p)
+    n = len(p.tau)
+    eye = np.eye(n)
+    assert np.max(np.abs(s["Sinv"] @ s["S"] - eye)) < 1e-9
+    assert np.max(np.abs(s["S"] @ s["Sinv"] - eye)) < 1e-9
+    rng = np.random.default_rng(26)
+
+    def herm(k):
+        a = rng.standard_normal((k, k, n)) + 1j * rng.standard_normal((k, k, n))
+        return a + a.conj().transpose(1, 0, 2)
+
+    su, so = herm(5), herm(5)
+    back_u, back_o = osg.sigma_tau_from_iw(osg.sigma_matrix_iw(su, so, s["C"], s["S"]), s["Cinv"], s["Sinv"])
+    assert np.max(np.abs(back_u - su)) < 1e-9 * np.max(np.abs(su))
+    assert np.max(np.abs(back_o - so)) < 1e-9 * np.max(np.abs(so))
+    du, do = rng.standard_normal((4, n)), rng.standard_normal((4, n))
+    bu, bo = osg.sigma_tau_from_iw(osg.sigma_iw(du, do, s["C"], s["S"]), s["Cinv"], s["Sinv"])
+    assert np.max(np.abs(bu - du)) < 1e-9 * np.max(np.abs(du))
+    assert np.max(np.abs(bo - do)) < 1e-9 * np.max(np.abs(do))
