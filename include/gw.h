@@ -57,7 +57,8 @@ typedef enum gw_prec {
 
 typedef enum gw_transform {
   GW_CT = 0,     /* out[k] = sum_j M[k][j] in[j]        (Eqs. CT_FFT, CTX, CT_W) */
-  GW_ST = 1      /* out[k] = i * sum_j M[k][j] in[j]    (Eq. ST_FFT)             */
+  GW_ST = 1,     /* out[k] = i * sum_j M[k][j] in[j]    (Eq. ST_FFT)             */
+  GW_IST = 2     /* out[j] = -i * sum_k M[j][k] in[k]   (Eq. INV_ST_FFT)         */
 } gw_transform;
 
 typedef struct gw_grid {
@@ -126,6 +127,12 @@ gw_status gw_coulomb_sqrt(const gw_grid* grid, const int32_t* gvec_h, int n_chi,
 gw_status gw_fit_transform(int n, const double* tau_h, const double* omega_h,
                            double x_min, double x_max, int n_x, double ridge,
                            double* C_h, double* S_h, double* Cinv_h, double* fit_err_h);
+
+/* Inverse of an n x n transform matrix (Eqs. INV_CT_FFT, INV_ST_FFT: the
+ * matrices xi cos and zeta sin are the inverses of gamma cos and lambda sin) by
+ * Gauss-Jordan elimination with partial pivoting in FP64.  Host only.
+ * GW_ERR_NUMERIC if M is singular. */
+gw_status gw_invert_transform(int n, const double* M_h, double* Minv_h);
 
 /* Device scratch in bytes that the context arena needs for gw_chi0_omega
  * (r_block <= 0: the default), gw_screen_W (n frequencies) and gw_sigma_diag
@@ -202,10 +209,13 @@ gw_status gw_rr_to_GG_fft_noalloc(const gw_grid* grid, int direction, int stage,
                                   const void* in, void* out, void* stream);
 
 /* Nonuniform time <-> frequency transform of `elems` complex elements per slice
- * (Eqs. CTX, CT_W, ST_FFT):  out[k][e] = (i if kind==GW_ST) sum_j M_h[k][j] in[j][e]
- * for k, j < n.  M_h is FP64 on the host; the sums are accumulated in FP64.
- * Use C for chi(tau)->chi(i omega), Cinv for W~(i omega)->W~(i tau).  in and
- * out must not overlap. */
+ * (Eqs. CTX, CT_W, ST_FFT, INV_ST_FFT):
+ *   out[k][e] = f sum_j M_h[k][j] in[j][e],  f = 1 (GW_CT), i (GW_ST), -i (GW_IST)
+ * for k, j < n.  M_h is FP64 on the host; the FP64 path sums in FP64, the
+ * others in FP32 with M split into two FP32 parts.  Use C for chi(tau)->chi(i
+ * omega), Cinv for W~(i omega)->W~(i tau), S for the odd part of Sigma, and Sinv
+ * (gw_invert_transform of S) with GW_IST to take it back to imaginary time.
+ * in and out must not overlap. */
 gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double* M_h, size_t elems,
                           gw_prec prec, const void* in, void* out, void* stream);
 
@@ -280,6 +290,24 @@ gw_status gw_sigma_matrix(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
                           const double* C_h, const double* S_h, const void* w_tau, int n_chi,
                           const int32_t* fft_index_h, gw_prec prec, double* sigma_tau_h,
                           double* sigma_iw_h, void* stream);
+
+/* The self-energy back on the imaginary time axis (Eqs. INV_CT_FFT,
+ * INV_ST_FFT), the inverse of the CT + ST of gw_sigma_diag / gw_sigma_matrix:
+ * Sigma(i omega) = C Sigma^c(tau) + i S Sigma^s(tau) with Sigma^c, Sigma^s
+ * Hermitian in the band indices, so the Hermitian part of Sigma(i omega)
+ * (the real part for diagonal elements) is the cosine part and the
+ * anti-Hermitian part the sine part; then
+ *   Sigma^c(tau_j) = sum_k Cinv_jk Herm(i omega_k),  Sigma^s(tau_j) = -i sum_k Sinv_jk Anti(i omega_k)
+ *   Sigma_unocc(tau_j) = Sigma^c + Sigma^s,  Sigma_occ(-tau_j) = Sigma^c - Sigma^s.
+ * matrix = 0: sigma_iw_h [n_n][n] complex -> sigma_tau_h [2][n_n][n] real
+ * (gw_sigma_diag's layout); matrix = 1: sigma_iw_h [n_n][n_n][n] complex ->
+ * sigma_tau_h [2][n_n][n_n][n] complex (gw_sigma_matrix's).  Cinv_h, Sinv_h
+ * [n][n] (gw_fit_transform, gw_invert_transform).  FP64 throughout: the sine
+ * matrix of the fitted grids is ill-conditioned (cond(S) ~ 2e6 at 16 points),
+ * so the inverse amplifies input errors by up to that factor.  Synchronous. */
+gw_status gw_sigma_to_tau(gw_ctx* ctx, int n_n, int n, int matrix, const double* Cinv_h,
+                          const double* Sinv_h, const double* sigma_iw_h, double* sigma_tau_h,
+                          void* stream);
 
 /* Quasiparticle energies and spectral functions from the continued
  * self-energy (Sec. II.E.2, Eqs. QP, GWQP, Z, A).  For every entry b (a band,

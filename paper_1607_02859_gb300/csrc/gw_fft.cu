@@ -710,8 +710,8 @@ gw_status launch_hadamard(gw_ctx* ctx, gw_prec prec, size_t count, const void* a
   return launch_check(ctx, "hadamard_kernel");
 }
 
-// Upload a host array into arena memory (pageable copy; the host buffer may be
-// released on return).
+// Transform weights w * fac as FP32 pairs: hi = fl(w fac), lo = fl(w fac - hi);
+// returns [hi_0 .. hi_{count-1}, lo_0 .. lo_{count-1}].
 std::vector<float> split_weights(const double* w, int count, double fac) {
   std::vector<float> out(2 * (size_t)count);
   for (int e = 0; e < count; ++e) {
@@ -722,6 +722,8 @@ std::vector<float> split_weights(const double* w, int count, double fac) {
   return out;
 }
 
+// Upload a host array into arena memory (pageable copy; the host buffer may be
+// released on return).
 gw_status upload(gw_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return GW_OK;
   return cuda_check(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload");
@@ -805,13 +807,19 @@ extern "C" gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double*
                                      const void* in, void* out, void* stream) {
   if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
   if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
-  if (kind != GW_CT && kind != GW_ST) return fail(ctx, GW_ERR_ARG, "kind must be GW_CT or GW_ST");
+  if (kind != GW_CT && kind != GW_ST && kind != GW_IST) return fail(ctx, GW_ERR_ARG, "kind must be GW_CT, GW_ST or GW_IST");
   if (n < 1 || n > 32) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
   if (!M_h || !in || !out) return fail(ctx, GW_ERR_ARG, "NULL pointer");
   if (in == out) return fail(ctx, GW_ERR_ARG, "in and out must not overlap");
   cudaStream_t s = as_stream(stream);
   gw_status st = reserve(ctx, 8 * 32 * 32);
   if (st) return st;
+  std::vector<double> neg;
+  if (kind == GW_IST) {             // -i sum M x = i sum (-M) x: the sine kernel with M negated
+    neg.assign(M_h, M_h + (size_t)n * n);
+    for (double& v : neg) v = -v;
+    M_h = neg.data();
+  }
   std::vector<float> m32;
   if (is_fp64(prec)) {
     if ((st = upload(ctx, ctx->arena, M_h, sizeof(double) * n * n, s))) return st;
@@ -819,7 +827,7 @@ extern "C" gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double*
     m32 = split_weights(M_h, n * n, 1.0);
     if ((st = upload(ctx, ctx->arena, m32.data(), sizeof(float) * 2 * n * n, s))) return st;
   }
-  return launch_ct(ctx, prec, kind == GW_ST, n, ctx->arena, elems, in, out, s, m32.empty() ? nullptr : m32.data());
+  return launch_ct(ctx, prec, kind != GW_CT, n, ctx->arena, elems, in, out, s, m32.empty() ? nullptr : m32.data());
 }
 
 // ---------------------------------------------------------------------- no-allocation variant

@@ -380,6 +380,13 @@ bool invert(int n, const double* M, double* out) {
 
 }  // namespace
 
+extern "C" gw_status gw_invert_transform(int n, const double* M_h, double* Minv_h) {
+  if (n < 1 || n > 64) return fail(nullptr, GW_ERR_SHAPE, "need 1 <= n <= 64");
+  if (!M_h || !Minv_h) return fail(nullptr, GW_ERR_ARG, "NULL pointer");
+  if (!invert(n, M_h, Minv_h)) return fail(nullptr, GW_ERR_NUMERIC, "matrix is singular");
+  return GW_OK;
+}
+
 extern "C" gw_status gw_fit_transform(int n, const double* tau_h, const double* omega_h, double x_min,
                                       double x_max, int n_x, double ridge, double* C_h, double* S_h,
                                       double* Cinv_h, double* fit_err_h) {

@@ -323,6 +323,56 @@ __global__ void sigma_matrix_finish_kernel(const double2* __restrict__ acc_u, co
   out_iw[t] = cadd(c, cmuli(sn));
 }
 
+// ---------------------------------------------------------------- back to imaginary time
+// Sigma(i omega) = C Sigma^c(tau) + i S Sigma^s(tau), with Sigma^c, Sigma^s
+// Hermitian in the band indices and C, S real: the Hermitian part of Sigma(i
+// omega) is the cosine part, the anti-Hermitian part the sine part.  One thread
+// per element e of [n_n][n_n] (matrix) or [n_n] (diagonal: real and imaginary
+// parts), writing both parts frequency-major, [n][E], for the transform.
+__global__ void sigma_split_kernel(const double2* __restrict__ sig, int n_n, int n, int matrix,
+                                   double2* __restrict__ herm, double2* __restrict__ anti) {
+  const long E = matrix ? (long)n_n * n_n : n_n;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  long et = e;                                     // the transposed element
+  if (matrix) {
+    const long a = e / n_n, b = e - a * n_n;
+    et = b * n_n + a;
+  }
+  for (int k = 0; k < n; ++k) {
+    const double2 v = sig[e * n + k];
+    if (matrix) {
+      const double2 t = cconj(sig[et * n + k]);
+      herm[(long)k * E + e] = cscale(cadd(v, t), 0.5);
+      anti[(long)k * E + e] = cscale(csub(v, t), 0.5);
+    } else {
+      herm[(long)k * E + e] = make_double2(v.x, 0.0);
+      anti[(long)k * E + e] = make_double2(0.0, v.y);
+    }
+  }
+}
+
+// Sigma_unocc(tau_j) = Sigma^c + Sigma^s, Sigma_occ(-tau_j) = Sigma^c - Sigma^s
+// from the transformed parts [n][E], written [2][E][n] (real parts only for the
+// diagonal form, as gw_sigma_diag returns them).
+__global__ void sigma_combine_kernel(const double2* __restrict__ sc, const double2* __restrict__ ss, long E, int n,
+                                     int matrix, double* __restrict__ out) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * n) return;
+  const long e = t / n;
+  const int j = (int)(t - e * n);
+  const double2 c = sc[(long)j * E + e], d = ss[(long)j * E + e];
+  const double2 u = cadd(c, d), o = csub(c, d);
+  if (matrix) {
+    double2* o2 = reinterpret_cast<double2*>(out);
+    o2[e * n + j] = u;
+    o2[E * n + e * n + j] = o;
+  } else {
+    out[e * n + j] = u.x;
+    out[E * n + e * n + j] = o.x;
+  }
+}
+
 // ---------------------------------------------------------------- QP energies
 // Thiele coefficients of every band's Sigma_n through z_k = i omega_k.
 __global__ void qp_coeff_kernel(const double2* __restrict__ sig, const double* __restrict__ omega, int n_n, int n,
@@ -703,5 +753,58 @@ extern "C" gw_status gw_qp_energies(gw_ctx* ctx, int n_n, int n, const double* o
                                                     h_stat[b] & 2 ? "QP equation not finite" :
                                                                     "Thiele evaluation broke down") +
                                             " for entry " + std::to_string(b));
+  return GW_OK;
+}
+
+extern "C" gw_status gw_sigma_to_tau(gw_ctx* ctx, int n_n, int n, int matrix, const double* Cinv_h,
+                                     const double* Sinv_h, const double* sigma_iw_h, double* sigma_tau_h,
+                                     void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  if (n < 1 || n > kMaxN) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
+  if (n_n < 1 || n_n > (matrix ? 4096 : (1 << 22))) return fail(ctx, GW_ERR_SHAPE, "n_n out of range");
+  if (matrix != 0 && matrix != 1) return fail(ctx, GW_ERR_ARG, "matrix must be 0 or 1");
+  if (!Cinv_h || !Sinv_h || !sigma_iw_h || !sigma_tau_h) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  cudaStream_t s = as_stream(stream);
+  const long E = matrix ? (long)n_n * n_n : n_n;
+  const size_t cplx = (size_t)E * n;
+  auto carve = [&](Carver& c, double** M, double2** sig, double2** herm, double2** anti, double2** sc, double2** ss,
+                   double2** out) {
+    *M = c.take<double>(2 * (size_t)n * n);      // Cinv, then -Sinv (the sine kernel multiplies by +i)
+    *sig = c.take<double2>(cplx);
+    *herm = c.take<double2>(cplx);
+    *anti = c.take<double2>(cplx);
+    *sc = c.take<double2>(cplx);
+    *ss = c.take<double2>(cplx);
+    *out = c.take<double2>(2 * cplx);           // [2][E][n], complex or (diagonal) real
+  };
+  double* dM;
+  double2 *dsig, *herm, *anti, *sc, *ss, *dout;
+  Carver probe(nullptr);
+  carve(probe, &dM, &dsig, &herm, &anti, &sc, &ss, &dout);
+  gw_status st;
+  if ((st = reserve(ctx, probe.off))) return st;
+  Carver cv(ctx->arena);
+  carve(cv, &dM, &dsig, &herm, &anti, &sc, &ss, &dout);
+  std::vector<double> m(2 * (size_t)n * n);
+  for (size_t i = 0; i < (size_t)n * n; ++i) {
+    m[i] = Cinv_h[i];
+    m[(size_t)n * n + i] = -Sinv_h[i];
+  }
+  if ((st = upload(ctx, dM, m.data(), sizeof(double) * m.size(), s))) return st;
+  if ((st = upload(ctx, dsig, sigma_iw_h, sizeof(double2) * cplx, s))) return st;
+  sigma_split_kernel<<<(unsigned)((E + 127) / 128), 128, 0, s>>>(dsig, n_n, n, matrix, herm, anti);
+  if ((st = launch_check(ctx, "sigma_split_kernel"))) return st;
+  // Eq. INV_CT_FFT on the cosine part, Eq. INV_ST_FFT (-i zeta sin) on the sine part, in FP64
+  if ((st = launch_ct(ctx, GW_FP64, false, n, dM, (size_t)E, herm, sc, s, nullptr))) return st;
+  if ((st = launch_ct(ctx, GW_FP64, true, n, dM + (size_t)n * n, (size_t)E, anti, ss, s, nullptr))) return st;
+  sigma_combine_kernel<<<(unsigned)((cplx + 255) / 256), 256, 0, s>>>(sc, ss, E, n, matrix,
+                                                                      reinterpret_cast<double*>(dout));
+  if ((st = launch_check(ctx, "sigma_combine_kernel"))) return st;
+  const size_t out_bytes = 2 * cplx * (matrix ? sizeof(double2) : sizeof(double));
+  std::vector<char> h(out_bytes);
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(h.data(), dout, out_bytes, cudaMemcpyDeviceToHost, s), "copy sigma")))
+    return st;
+  if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sigma sync"))) return st;
+  std::memcpy(sigma_tau_h, h.data(), out_bytes);
   return GW_OK;
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libgw.so")
 
 FP64, FP32, F16X3, BF16X3 = 0, 1, 2, 3
 PREC = {"fp64": FP64, "fp32": FP32, "f16x3": F16X3, "bf16x3": BF16X3}
-CT, ST = 0, 1
+CT, ST, IST = 0, 1, 2
 STATUS = {0: "GW_OK", 1: "GW_ERR_ARG", 2: "GW_ERR_SHAPE", 3: "GW_ERR_OOM", 4: "GW_ERR_CUDA",
           5: "GW_ERR_NUMERIC", 6: "GW_ERR_TIMEOUT", 7: "GW_ERR_UNSUPPORTED"}
 
@@ -28,7 +28,7 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
            "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh", "gw_sigma_diag_kmesh",
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
-           "gw_sigma_matrix", "gw_qp_energies"]
+           "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau"]
 
 
 class GwError(RuntimeError):
@@ -85,6 +85,8 @@ _SIGS = {
     "gw_sigma_matrix": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                              _DP, _DP, _P]),
     "gw_qp_energies": (_I, [_P, _I, _I, _DP, _DP, _DP, _D, _DP, _I, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
+    "gw_invert_transform": (_I, [_I, _DP, _DP]),
+    "gw_sigma_to_tau": (_I, [_P, _I, _I, _I, _DP, _DP, _DP, _DP, _P]),
 }
 
 _lib = None
@@ -222,7 +224,16 @@ def fit_transform(tau, omega, x_min, x_max, n_x=4000, ridge=1e-6):
     err = np.zeros(2)
     _check(lib().gw_fit_transform(n, _dp(tau), _dp(omega), float(x_min), float(x_max), int(n_x), float(ridge),
                                   _dp(C), _dp(S), _dp(Ci), _dp(err)))
-    return {"C": C, "S": S, "Cinv": Ci, "fit_err_cos": err[0], "fit_err_sin": err[1]}
+    return {"C": C, "S": S, "Cinv": Ci, "Sinv": invert_transform(S), "fit_err_cos": err[0], "fit_err_sin": err[1]}
+
+
+def invert_transform(M):
+    """Inverse of a transform matrix (Eqs. INV_CT_FFT, INV_ST_FFT), FP64 on the host."""
+    M = _f64(M)
+    n = M.shape[0]
+    out = np.zeros((n, n))
+    _check(lib().gw_invert_transform(n, _dp(M), _dp(out)))
+    return out
 
 
 def workspace_size(grid, n_b, n_occ, n, n_chi, n_n, prec, r_block=0):
@@ -361,6 +372,20 @@ def sigma_matrix(ctx, grid, psi, eps, n_occ, mu, bands, tau, omega, C, S, w_tau,
                                s_tau.ctypes.data_as(_DP), s_iw.ctypes.data_as(_DP), _stream())
     _check(st, ctx)
     return {"sigma_unocc": s_tau[0], "sigma_occ": s_tau[1], "sigma_iw": s_iw}
+
+
+def sigma_to_tau(ctx, sigma_iw, Cinv, Sinv):
+    """(Sigma_unocc(tau), Sigma_occ(-tau)) from Sigma(i omega) (gw_sigma_to_tau):
+    [n_n][n] -> two real [n_n][n] arrays, or [n_n][n_n][n] -> two complex [n_n][n_n][n]."""
+    sig = np.ascontiguousarray(sigma_iw, dtype=np.complex128)
+    matrix = sig.ndim == 3
+    n_n, n = sig.shape[0], sig.shape[-1]
+    if matrix and sig.shape[1] != n_n:
+        raise ValueError("a matrix Sigma must be [n_n][n_n][n]")
+    out = np.zeros((2,) + sig.shape, dtype=np.complex128 if matrix else np.float64)
+    _check(lib().gw_sigma_to_tau(ctx.handle, n_n, n, int(matrix), _dp(_f64(Cinv)), _dp(_f64(Sinv)),
+                                 sig.ctypes.data_as(_DP), out.ctypes.data_as(_DP), _stream()), ctx)
+    return out[0], out[1]
 
 
 def qp_energies(ctx, omega, sigma_iw, eps, mu, vstat, w=None):

@@ -62,6 +62,10 @@ def test_fit_transform_matches_oracle(L, maker):
     for key in ("C", "S"):
         assert np.allclose(lib_m[key], ref[key], rtol=1e-7, atol=1e-9 * np.abs(ref[key]).max()), key
     assert np.allclose(lib_m["Cinv"] @ lib_m["C"], np.eye(len(p.tau)), atol=1e-9)
+    assert np.allclose(lib_m["Sinv"] @ lib_m["S"], np.eye(len(p.tau)), atol=1e-9)
+    # S is ill-conditioned (cond ~2e6 at 16 points): its 1e-12 difference between the two fits grows by cond(S)
+    err = np.linalg.norm(lib_m["Sinv"] - ref["Sinv"]) / np.linalg.norm(ref["Sinv"])
+    assert err < 1e-11 * np.linalg.cond(ref["S"])
     assert abs(lib_m["fit_err_cos"] - ref["fit_err_cos"]) < 1e-6
     assert abs(lib_m["fit_err_sin"] - ref["fit_err_sin"]) < 1e-6
 
@@ -74,6 +78,21 @@ def test_host_argument_errors(L):
     with pytest.raises(gw.GwError) as e:
         gw.fit_transform([1.0, -1.0], [1.0, 2.0], 0.1, 1.0)
     assert e.value.status == 1            # GW_ERR_ARG: tau <= 0
+
+
+def test_invert_transform(L):
+    """gw_invert_transform (Eqs. INV_CT_FFT, INV_ST_FFT) on a well-conditioned
+    matrix and its errors."""
+    rng = np.random.default_rng(7)
+    m = np.eye(12) + 0.1 * rng.standard_normal((12, 12))
+    inv = gw.invert_transform(m)
+    assert np.max(np.abs(inv @ m - np.eye(12))) < 1e-13
+    with pytest.raises(gw.GwError) as e:
+        gw.invert_transform(np.zeros((3, 3)))
+    assert e.value.status == 5            # GW_ERR_NUMERIC: singular
+    with pytest.raises(gw.GwError) as e:
+        gw.invert_transform(np.eye(65))
+    assert e.value.status == 2
 
 
 def test_device_calls_reject_null_context(L):

@@ -97,6 +97,23 @@ def test_sigma_matrix(ctx, case, prec):
     assert np.max(np.abs(diag - d["sigma_iw"])) < tol * np.max(np.abs(d["sigma_iw"])) + 1e-15
 
 
+@pytest.mark.parametrize("which", ["matrix", "diag"])
+def test_sigma_back_to_tau(ctx, case, which):
+    """gw_sigma_to_tau inverts the CT + ST (Eqs. INV_CT_FFT, INV_ST_FFT): from the
+    oracle's Sigma(i omega) it returns the oracle's Sigma_unocc(tau) and
+    Sigma_occ(-tau), and the GPU's own round trip returns gw_sigma_matrix's."""
+    name, p, s, wt, su, so, sig_ref = case
+    if which == "diag":
+        sig_ref = np.einsum("nnk->nk", sig_ref)
+        su, so = np.einsum("nnk->nk", su).real, np.einsum("nnk->nk", so).real
+    bu, bo = gw.sigma_to_tau(ctx, sig_ref, s["Cinv"], s["Sinv"])
+    ou, oo = osg.sigma_tau_from_iw(sig_ref, s["Cinv"], s["Sinv"])
+    scale = max(np.max(np.abs(su)), np.max(np.abs(so)))
+    tol = 1e-13 * np.linalg.cond(s["S"]) * scale
+    assert np.max(np.abs(bu - ou)) < tol and np.max(np.abs(bo - oo)) < tol
+    assert np.max(np.abs(bu - su)) < 10 * tol and np.max(np.abs(bo - so)) < 10 * tol
+
+
 def test_sigma_matrix_argument_errors(ctx):
     p = inputs.tiny(seed=61)
     s = opipe.setup(p)
@@ -198,3 +215,18 @@ def test_qp_breakdown_and_argument_errors(ctx):
     with pytest.raises(gw.GwError) as e:
         gw.qp_energies(ctx, np.geomspace(0.1, 10, 33), np.ones((1, 33)), [0.0], 0.0, [0.0])
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [6, 8, 11])
+def test_inverse_sine_kind(ctx, prec, n):
+    """gw_tau_to_omega with GW_IST: out[j] = -i sum_k M[j][k] in[k] (Eq. INV_ST_FFT),
+    on the register-resident sizes (6, 8) and the generic kernel (11)."""
+    rng = np.random.default_rng(n)
+    m = rng.standard_normal((n, n))
+    x = rng.standard_normal((n, 1000)) + 1j * rng.standard_normal((n, 1000))
+    out = torch.zeros((n, 1000), dtype=gw.cdtype(prec), device="cuda")
+    gw.tau_to_omega(ctx, gw.IST, m, to_dev(x, prec), out, prec)
+    ref = -1j * (m @ x)
+    err = np.max(np.abs(out.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < (1e-14 if prec == "fp64" else 1e-6)
