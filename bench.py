@@ -5,8 +5,9 @@ One step = the whole hot path through the C ABI on one seeded system:
 chi0(i omega) (gw_chi0_omega: G formation, chi = -2 G_occ o conj(G_unocc), row
 and column FFTs, cosine transform), screening (gw_screen_W), inverse cosine
 transform (gw_tau_to_omega), the diagonal self-energy with its Thiele
-continuation (gw_sigma_diag) and the linearised QP energies and spectral
-functions (gw_qp_energies).  The metric is the effective TFLOP/s of the
+continuation (gw_sigma_diag), the linearised QP energies and spectral
+functions (gw_qp_energies) and Sigma back on the imaginary time axis
+(gw_sigma_to_tau).  The metric is the effective TFLOP/s of the
 method's algorithmic work (flop model below) divided by the device time.
 --sigma matrix replaces the last two calls by the full self-energy matrix over
 the same bands (gw_sigma_matrix).
@@ -306,12 +307,15 @@ def main():
                                   mats["S"], w_tau, fidx, args.prec)
             mark(4)
             mark(5)
+            mark(6)
             return out
         out = gw.sigma_diag(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"], mats["S"],
                             w_tau, fidx, args.prec, w_real=w_real)
         mark(4)
         out["qp"] = gw.qp_energies(ctx, p.omega, out["sigma_iw"], eps_n, p.mu, vstat, w=w_real + p.mu)
         mark(5)
+        out["back_to_tau"] = gw.sigma_to_tau(ctx, out["sigma_iw"], mats["Cinv"], mats["Sinv"])
+        mark(6)
         return out
 
     for _ in range(args.warmup):
@@ -342,7 +346,7 @@ def main():
     value = job_value(world, fl["total"], args.steps, t_dev)
 
     # per-stage breakdown and the dominant stage's roofline (same stream, CUDA events)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
     flush.zero_()
     if args.no_breakdown:
         for e in ev:
@@ -351,9 +355,10 @@ def main():
         step(psi, ev)
     torch.cuda.synchronize()
     stage_ms = {name: ev[i].elapsed_time(ev[i + 1]) for i, name in
-                enumerate(["chi0_omega", "screen_W", "inverse_ct", "sigma_" + args.sigma, "qp_energies"])}
+                enumerate(["chi0_omega", "screen_W", "inverse_ct", "sigma_" + args.sigma, "qp_energies",
+                           "sigma_to_tau"])}
     if args.sigma == "matrix":
-        del stage_ms["qp_energies"]
+        del stage_ms["qp_energies"], stage_ms["sigma_to_tau"]
     # per-kernel device time and algorithmic work (library events on the launch stream)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -410,6 +415,7 @@ def main():
     e2e = {"value": job_value(world, fl["total"], args.steps, t_e2e), "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(psi_h.numel() * psi_h.element_size()),
            "d2h_bytes_per_step": int(len(p.bands) * (3 * n_tau + N_REAL) * 16 + len(p.bands) * (48 + 8 * N_REAL)
+                                     + 2 * len(p.bands) * n_tau * 8
                                      if args.sigma == "diag" else len(p.bands) ** 2 * 3 * n_tau * 16)}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
