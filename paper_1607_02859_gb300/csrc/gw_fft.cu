@@ -220,8 +220,10 @@ __global__ void __launch_bounds__(256) row_line_bwd_kernel(const typename cpx<T>
 constexpr int kPlaneW = 16;
 
 // In-place 2-D FFT over (i2, i3) of the rows of plane i1 = blockIdx.y, for 16
-// contiguous columns per CTA.
-template <typename T, int N2, int N3, int DIR>
+// contiguous columns per CTA.  PAIRS (FP32 only): rows move as 16-byte pairs
+// of columns; the host takes it when ld and ncols are even (every pair then
+// starts on a 16-byte boundary and lies wholly inside or outside the matrix).
+template <typename T, int N2, int N3, int DIR, bool PAIRS>
 __global__ void __launch_bounds__(256) col_plane_kernel(typename cpx<T>::t* __restrict__ buf, long ld, int ncols,
                                                         T scale) {
   using C = typename cpx<T>::t;
@@ -231,18 +233,35 @@ __global__ void __launch_bounds__(256) col_plane_kernel(typename cpx<T>::t* __re
   const long i1 = blockIdx.y;
   const int c0 = blockIdx.x * W;
   C* base = buf + i1 * (N2 * N3) * ld + c0;
-  for (int e = threadIdx.x; e < N2 * N3 * W; e += blockDim.x) {
-    const int rr = e / W, w = e - rr * W;
-    s[e] = (c0 + w < ncols) ? base[rr * ld + w] : mk(T(0), T(0));
+  if constexpr (PAIRS) {
+    for (int e = threadIdx.x; e < N2 * N3 * W / 2; e += blockDim.x) {
+      const int rr = e / (W / 2), w = 2 * (e - rr * (W / 2));
+      C a = mk(T(0), T(0)), b = a;
+      if (c0 + w < ncols) ld_pair(base + rr * ld + w, a, b);
+      s[rr * W + w] = a;
+      s[rr * W + w + 1] = b;
+    }
+  } else {
+    for (int e = threadIdx.x; e < N2 * N3 * W; e += blockDim.x) {
+      const int rr = e / W, w = e - rr * W;
+      s[e] = (c0 + w < ncols) ? base[rr * ld + w] : mk(T(0), T(0));
+    }
   }
   __syncthreads();
   pencil_pass<N3, DIR>(s, N2 * W, W, [](int p) { return (p / W) * (N3 * W) + (p % W); });
   __syncthreads();
   pencil_pass<N2, DIR>(s, N3 * W, N3 * W, [](int p) { return (p / W) * W + (p % W); });
   __syncthreads();
-  for (int e = threadIdx.x; e < N2 * N3 * W; e += blockDim.x) {
-    const int rr = e / W, w = e - rr * W;
-    if (c0 + w < ncols) base[rr * ld + w] = cscale(s[e], scale);
+  if constexpr (PAIRS) {
+    for (int e = threadIdx.x; e < N2 * N3 * W / 2; e += blockDim.x) {
+      const int rr = e / (W / 2), w = 2 * (e - rr * (W / 2));
+      if (c0 + w < ncols) st_pair(base + rr * ld + w, cscale(s[rr * W + w], scale), cscale(s[rr * W + w + 1], scale));
+    }
+  } else {
+    for (int e = threadIdx.x; e < N2 * N3 * W; e += blockDim.x) {
+      const int rr = e / W, w = e - rr * W;
+      if (c0 + w < ncols) base[rr * ld + w] = cscale(s[e], scale);
+    }
   }
 }
 
@@ -552,7 +571,9 @@ struct GridOps {
       kernel<<<grid, 256, bytes, st>>>((C*)buf, ld, ncols, (T)scale);
       return launch_check(ctx, "col_plane_kernel");
     };
-    return dir > 0 ? go(col_plane_kernel<T, N2, N3, +1>) : go(col_plane_kernel<T, N2, N3, -1>);
+    const bool pairs = sizeof(T) == 4 && ld % 2 == 0 && ncols % 2 == 0 && reinterpret_cast<uintptr_t>(buf) % 16 == 0;
+    if (pairs) return dir > 0 ? go(col_plane_kernel<T, N2, N3, +1, true>) : go(col_plane_kernel<T, N2, N3, -1, true>);
+    return dir > 0 ? go(col_plane_kernel<T, N2, N3, +1, false>) : go(col_plane_kernel<T, N2, N3, -1, false>);
   }
   static gw_status line(gw_ctx* ctx, int dir, int variant, const void* in, long ldi, void* out, long ldo, int ncols,
                         const int* inv, double scale, cudaStream_t st) {
