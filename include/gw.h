@@ -138,6 +138,9 @@ gw_status gw_invert_transform(int n, const double* M_h, double* Minv_h);
  * (r_block <= 0: the default), gw_screen_W (n frequencies) and gw_sigma_diag
  * (n_n bands, up to 64 real frequencies) on this problem.  The arena is shared
  * by the calls of one context, so a context needs the largest of the three.
+ * gw_sigma_matrix needs at most 16 n (3 n_n^2 - 2 n_n) + 32 n_n min(N_r, 2048) bytes
+ * more than the gw_sigma_diag figure, within 256-byte rounding;
+ * gw_qp_energies and gw_sigma_to_tau need only a few arrays of n_n x n.
  * Host only; any output may be NULL.  Used for admission by memory footprint. */
 gw_status gw_workspace_size(const gw_grid* grid, int n_b, int n_occ, int n, int n_chi, int n_n, gw_prec prec,
                             int r_block, size_t* chi0_bytes, size_t* screen_bytes, size_t* sigma_bytes);
