@@ -49,6 +49,9 @@ class System:
     prec: str
     r_block: int = 0
     w_real: np.ndarray = field(default_factory=lambda: np.linspace(-1.0, 1.0, 16))
+    # frequency-independent part of the QP equation per band of `bands`
+    # (<T + V_ne + V_H> + bare exchange); None: the Kohn-Sham energies
+    vstat: np.ndarray = None
 
     @property
     def n_b(self) -> int:
@@ -101,7 +104,8 @@ class Request:
 def run_request(ctx, req: Request, stream, keep_chi=False):
     """Run one request on `stream` through the C ABI; returns its result
     (chi0 tensor on the device for "chi0" when keep_chi, else its Frobenius norm;
-    the sigma_diag dict for "sigma")."""
+    for "sigma", the sigma_diag dict with the QP energies, Z and spectral
+    functions on w_real + mu under "qp")."""
     import torch
     s = req.system
     n = len(s.tau)
@@ -119,6 +123,9 @@ def run_request(ctx, req: Request, stream, keep_chi=False):
         del chi
         out = gw.sigma_diag(ctx, s.grid, s.psi, s.eps, s.n_occ, s.mu, s.bands, s.tau, s.omega, s.mats["C"],
                             s.mats["S"], w_tau, s.fidx, s.prec, w_real=s.w_real)
+        eps_n = s.eps[s.bands]
+        out["qp"] = gw.qp_energies(ctx, s.omega, out["sigma_iw"], eps_n, s.mu,
+                                   eps_n if s.vstat is None else s.vstat, w=s.w_real + s.mu)
         stream.synchronize()
         return out
 

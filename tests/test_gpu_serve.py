@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import pipeline as opl
+from oracle import qp as oqp
 from paper_1607_02859_gb300 import gw, inputs, serve
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +56,8 @@ def test_mix_matches_alone(built, prec):
             else:
                 d = np.max(np.abs(r.result["sigma_iw"] - ref["sigma_iw"]))
                 assert d < 1e-3 * MEV, d
+                d = np.max(np.abs(r.result["qp"]["e_qp"] - ref["qp"]["e_qp"]))
+                assert d < 1e-3 * MEV, d
         st = srv.stats()
         assert st["requests"] == 12 and st["p99_ms"] >= st["p50_ms"] > 0
     finally:
@@ -64,3 +67,6 @@ def test_mix_matches_alone(built, prec):
     ref = opl.run(p)
     got = alone[(0, "sigma")]["sigma_iw"]
     assert np.max(np.abs(got - ref["sigma_iw"])) < MEV
+    eps_n = p.eps[p.bands]
+    e_ref = oqp.linearized(ref["sigma_iw"], p.omega, eps_n, p.mu, eps_n)[0]
+    assert np.max(np.abs(alone[(0, "sigma")]["qp"]["e_qp"] - e_ref)) < MEV
