@@ -38,6 +38,9 @@ CASES = {
     "6^3_k2x2x2": dict(n=(6, 6, 6), a=(6.0, 6.5, 7.0), nk=(2, 2, 2), n_occ=4, n_unocc=20, n_tau=4, seed=61, n_chi=None),
     "4^3_k3x3x3_partial": dict(n=(4, 4, 4), a=(5.0, 5.5, 6.0), nk=(3, 3, 3), n_occ=3, n_unocc=13, n_tau=4, seed=62,
                                n_chi=40),
+    # the largest mesh the library takes: 64 k points (16^3 supercell)
+    "4^3_k4x4x4_max": dict(n=(4, 4, 4), a=(5.0, 5.5, 6.0), nk=(4, 4, 4), n_occ=2, n_unocc=10, n_tau=4, seed=66,
+                           n_chi=None),
 }
 
 
@@ -74,6 +77,9 @@ def test_kmesh_argument_checks(ctx, case):
         gw.chi0_omega_kmesh(ctx, grid, (1, 1, 5), psi, p.eps_k, p.n_occ, p.mu, p.tau, mats["C"], gv, "fp32", out)
     with pytest.raises(gw.GwError):       # mu outside a gap
         gw.chi0_omega_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, 5.0, p.tau, mats["C"], gv, "fp32", out)
+    with pytest.raises(gw.GwError) as e:  # more than 64 k points (checked before any array is read)
+        gw.chi0_omega_kmesh(ctx, grid, (5, 4, 4), psi, p.eps_k, p.n_occ, p.mu, p.tau, mats["C"], gv, "fp32", out)
+    assert e.value.status == 2
 
 
 @pytest.mark.parametrize("prec", ["fp32", "f16x3", "fp64"])
