@@ -108,3 +108,14 @@ def test_ctx_create_without_gpu_fails_cleanly(L):
     with pytest.raises(gw.GwError) as e:
         gw.Context(0)
     assert e.value.status == 4            # GW_ERR_CUDA, no abort
+
+
+def test_binding_checks_sizes_before_the_library():
+    """The QP and back-to-tau bindings reject inconsistent shapes on the host,
+    before any library or device call."""
+    with pytest.raises(ValueError):
+        gw.qp_energies(None, np.ones(4), np.ones((2, 4)), [0.0], 0.0, [0.0, 0.0])     # eps has 1 entry, not 2
+    with pytest.raises(ValueError):
+        gw.qp_energies(None, np.ones(3), np.ones((2, 4)), [0.0, 0.0], 0.0, [0.0, 0.0])  # 3 nodes, 4 values
+    with pytest.raises(ValueError):
+        gw.sigma_to_tau(None, np.ones((2, 3, 4)), np.eye(4), np.eye(4))               # not square in bands
