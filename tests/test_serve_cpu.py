@@ -227,4 +227,3 @@ def test_prepare_sizes_arenas_within_budget():
         assert r.error == "" and sorted(w.arena for w in srv.workers) == [0, 20 * GB, 20 * GB]
     finally:
         srv.close()
-
