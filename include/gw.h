@@ -200,12 +200,16 @@ gw_status gw_rr_to_GG_fft(gw_ctx* ctx, const gw_grid* grid, int direction, int s
  * two index maps the transform needs live in one fixed array inside the
  * library's device image (n_chi + N_r <= 27648 entries, i.e. up to the 24^3
  * grid); larger requests return GW_ERR_SHAPE.  That array exists on every GPU
- * that loads the library until the process exits.  It is looked up once per
- * device on the first call made with that device current; make that first call
- * before any stream capture.  Every call rewrites both maps in full, so nothing
- * carries over between calls, but all calls share the array: calls whose work
- * overlaps on the GPU (different streams, or different host threads) race on
- * it.  Calls on one stream are ordered and safe.  Errors are reported through
+ * that loads the library until the process exits.  Its device address is
+ * looked up once per device, on the first call made with that device current.
+ * Every call rewrites both maps in full, so nothing carries over between
+ * calls, but all calls share the array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race on it.  Calls on one
+ * stream are ordered and safe.  The maps are uploaded on every call by a copy
+ * from pageable host memory, which waits for the stream's earlier work before
+ * it starts.  Because that copy's host source lives only for the call, a call
+ * made while `stream` is being captured into a CUDA graph is refused with
+ * GW_ERR_UNSUPPORTED and does nothing.  Errors are reported through
  * gw_last_error(NULL). */
 gw_status gw_rr_to_GG_fft_noalloc(const gw_grid* grid, int direction, int stage, int n_chi,
                                   const int32_t* fft_index_h, gw_prec prec, int r0, int n_rows,

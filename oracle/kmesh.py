@@ -13,7 +13,8 @@ Bloch orbitals satisfy psi_nk(r + L) = exp(i k.L) psi_nk(r), so the Green's
 function on the stripe r in C, R' in S is
     G(r, r'+L, tau) = (1/N_k) sum_k exp(-i k.L) G_k(r, r', tau)
 (the 1/N_k is the normalisation of the orbitals over S), chi(r, R') follows
-the Gamma-point form (reading R2), and
+the Gamma-point form chi(r, R') = -2 G_occ(r, R') conj(G_unocc(r, R')) (the
+index order G_occ(r,r') G_unocc(r',r) of the spin-degenerate product), and
     chi_q(g, g') = (dV^2 / Omega) sum_{r in C} exp(-i(q+g).r)
                                   sum_{R' in S} chi(r, R') exp(+i(q+g').R'),
 which is the q-diagonal block of the Gamma-point chi of the supercell (the

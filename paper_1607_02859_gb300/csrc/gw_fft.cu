@@ -860,7 +860,10 @@ extern "C" gw_status gw_tau_to_omega(gw_ctx* ctx, int kind, int n, const double*
 // caller that may not allocate device memory at all can still run the
 // transform: for example a program whose memory pool has taken the whole GPU
 // and forbids any other cudaMalloc, or a serving loop that cannot afford the
-// device-wide synchronisation a cudaMalloc/cudaFree may bring.
+// device-wide synchronisation a cudaMalloc/cudaFree may bring.  The maps are
+// still uploaded on every call, by cudaMemcpyAsync from pageable host memory:
+// that copy waits for the stream's earlier work before it starts, so a call
+// is not free of host-side waiting, only of allocation.
 
 namespace {
 
@@ -911,6 +914,15 @@ extern "C" gw_status gw_rr_to_GG_fft_noalloc(const gw_grid* grid, int direction,
   if (direction != 1 && direction != -1) return done(fail(&local, GW_ERR_ARG, "direction must be +1 or -1"));
   if (stage != 1 && stage != 2) return done(fail(&local, GW_ERR_ARG, "stage must be 1 or 2"));
   if (!in || !out) return done(fail(&local, GW_ERR_ARG, "NULL pointer"));
+  cudaStream_t s = as_stream(stream);
+  // The maps are copied from host vectors that live only for this call: a
+  // captured copy would replay from freed host memory, so refuse capture.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess) return done(cuda_check(&local, ce, "cudaStreamIsCapturing"));
+  if (cap != cudaStreamCaptureStatusNone)
+    return done(fail(&local, GW_ERR_UNSUPPORTED,
+                     "gw_rr_to_GG_fft_noalloc cannot be called while its stream is being captured"));
   std::vector<int> map, inv;
   if ((st = index_maps(&local, g, fft_index_h, n_chi, map, inv))) return done(st);
   if ((long)n_chi + g.nr > kNoAllocMaxInts)
@@ -922,7 +934,6 @@ extern "C" gw_status gw_rr_to_GG_fft_noalloc(const gw_grid* grid, int direction,
   if ((st = noalloc_maps_ptr(&local, &maps))) return done(st);
   int* dmap = maps;
   int* dinv = maps + n_chi;
-  cudaStream_t s = as_stream(stream);
   // both maps are rewritten in full on every call, so nothing carries over
   if ((st = upload(&local, dmap, map.data(), sizeof(int) * n_chi, s))) return done(st);
   if ((st = upload(&local, dinv, inv.data(), sizeof(int) * g.nr, s))) return done(st);

@@ -6,7 +6,9 @@
 //   G(r, r'+L, tau) = (1/N_k) sum_k exp(-i k.L) G_k(r, r', tau),
 // where G_k is the Gamma-point band sum of Eqs. Green_occ/unocc over the
 // orbitals of k (the 1/N_k normalises them over S).  Then, as at Gamma,
-//   chi(r, R') = -2 G_occ(r, R') conj(G_unocc(r, R'))            (reading R2)
+//   chi(r, R') = -2 G_occ(r, R') conj(G_unocc(r, R'))
+// (spin-degenerate, index order G_occ(r,r') G_unocc(r',r), i.e. the conjugate
+// of the printed tau > 0 slice of Eq. chi_rr for complex orbitals)
 // and for every q of the mesh
 //   chi_q(g, g') = (dV^2/Omega) sum_{r in C} exp(-i(q+g).r)
 //                                sum_{R' in S} chi(r, R') exp(+i(q+g').R'),

@@ -121,7 +121,8 @@ WTOL = {"f16x3": 2e-5, "bf16x3": 3e-4}
 
 @pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
 def test_tc_screen_W(ctx, case, prec):
-    """256-column panels: cases with N_chi = 216 (one panel), 480 and 400 (two)."""
+    """512-column screening panels: N_chi = 216, 480 and 400, one panel each (a
+    ragged panel narrower than the panel width)."""
     from oracle import screen as osc
     name, p, s = case
     grid = gw.make_grid(p.n, p.lattice)
@@ -136,7 +137,8 @@ def test_tc_screen_W(ctx, case, prec):
 
 @pytest.mark.parametrize("prec", ["f16x3"])
 def test_tc_gamma_toy_end_to_end(ctx, prec):
-    """12^3 Gamma toy (N_chi = 1728: seven screening panels) through the whole
+    """12^3 Gamma toy (N_chi = 1728: four 512-column screening
+    panels, the last one ragged) through the whole
     chain with the tensor-core precision; Sigma within 1 meV of the oracle."""
     p = inputs.gamma_toy()
     ref = opipe.run(p)

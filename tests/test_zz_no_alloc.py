@@ -79,11 +79,47 @@ def test_noalloc_matches_regular_entry_point(ctx, prec):
 def test_noalloc_rejects_invalid_sizes():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    grid = gw.make_grid((24, 24, 24), np.eye(3) * 10.26)
-    _, idx = gw.g_set(grid, 13824)
+    grid24 = gw.make_grid((24, 24, 24), np.eye(3) * 10.26)
+    _, idx = gw.g_set(grid24, 13824)
     x = torch.zeros((1, 13824), dtype=torch.complex64, device="cuda")
-    gw.rr_to_GG_fft_noalloc(grid, +1, 1, idx, "fp32", 0, 1, x, x.clone())     # at the limit: fine
-    big = gw.make_grid((24, 24, 24), np.eye(3) * 10.26)
+    gw.rr_to_GG_fft_noalloc(grid24, +1, 1, idx, "fp32", 0, 1, x, x.clone())     # n_chi + N_r at the capacity
+    # the 36^3 grid is compiled, but its N_r alone is beyond the fixed map capacity
+    grid36 = gw.make_grid((36, 36, 36), np.eye(3) * 20.52)
+    _, idx36 = gw.g_set(grid36, 100)
+    y = torch.zeros((1, 100), dtype=torch.complex64, device="cuda")
+    z = torch.zeros((1, 46656), dtype=torch.complex64, device="cuda")
     with pytest.raises(gw.GwError) as e:
-        gw.rr_to_GG_fft_noalloc(big, +1, 1, np.concatenate([idx, idx[:1]]), "fp32", 0, 1, x, x.clone())
-    assert e.value.status in (1, 2)
+        gw.rr_to_GG_fft_noalloc(grid36, -1, 1, idx36, "fp32", 0, 1, y, z)
+    assert e.value.status == 2
+    assert "capacity" in str(e.value)
+
+
+def test_noalloc_refuses_stream_capture():
+    """The maps are copied from host memory that lives only for the call, so a
+    call on a stream that is being captured must be refused and do nothing."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    p = inputs.tiny(seed=32)
+    grid, idx, x = _case(p, 216, 3)
+    xd = torch.from_numpy(x).to("cuda", dtype=torch.complex64)
+    out = torch.zeros((p.n_r, 216), dtype=torch.complex64, device="cuda")
+    flag = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    refused = None
+    with torch.cuda.graph(g):
+        flag.add_(1.0)                            # keep the captured graph non-empty
+        try:
+            gw.rr_to_GG_fft_noalloc(grid, +1, 1, idx, "fp32", 0, p.n_r, xd, out)
+        except gw.GwError as err:
+            refused = err
+    assert refused is not None and refused.status == 7, refused
+    assert "captured" in str(refused)
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(flag.item()) == 1.0
+    assert float(out.abs().max().item()) == 0.0
+    # the same call outside a capture works
+    gw.rr_to_GG_fft_noalloc(grid, +1, 1, idx, "fp32", 0, p.n_r, xd, out)
+    torch.cuda.synchronize()
+    assert float(out.abs().max().item()) > 0.0
