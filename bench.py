@@ -47,6 +47,7 @@ ACCURACY = {
     "bf16x3": "3 bf16 split products on tcgen05; tested: chi0 within 2e-5 relative, Sigma_nn within 1 meV",
 }
 N_REAL = 64          # real frequencies of the continued Sigma_nn(omega)
+E2E_STEPS = 3        # steps of the end-to-end pass
 FLUSH_BYTES = 512 << 20
 
 
@@ -174,16 +175,24 @@ def measured_peaks():
 
 # ---------------------------------------------------------------------- reference arm (CPU oracle)
 
-SAMPLE_ROWS, SAMPLE_SOLVE = 1536, 3072     # ~10 s of the FP64 oracle on 16 host cores at si8
+SAMPLE_SOLVE = 3072
+SAMPLE_G_FLOPS = 2.8e12     # G-row work of one sample: ~10 s of the FP64 oracle on 16 host cores
 
 
-def oracle_sample(p, rows=SAMPLE_ROWS, n_solve=SAMPLE_SOLVE):
+def sample_rows(p):
+    """Rows of the bounded oracle sample: about SAMPLE_G_FLOPS of G formation (1536 rows at si8,
+    89 at si64)."""
+    return int(min(1536, max(16, SAMPLE_G_FLOPS // (8.0 * p.n_r * p.n_b * len(p.tau)))))
+
+
+def oracle_sample(p, rows=None, n_solve=SAMPLE_SOLVE):
     """Time the FP64 oracle on a bounded slice of the workload: G_occ/G_unocc rows and the
     real-space chi product for `rows` rows at every tau, plus one screening solve of size
     n_solve.  Returns (flops, seconds) under the same flop model."""
     from oracle import chi as ochi  # noqa: F401  (oracle only in this leg)
     from oracle import green as ogr
     from oracle import screen as osc
+    rows = sample_rows(p) if rows is None else rows
     rr = np.arange(rows)
     t0 = time.perf_counter()
     for tau in p.tau:
@@ -223,7 +232,7 @@ def run_reference(args, p, workload):
         tot_t += t
     val = tot_f / tot_t / 1e12
     sample = ("FP64 numpy oracle: G_occ/G_unocc rows + chi product for %d of %d rows at all %d tau, plus one %d^2 "
-              "screening solve" % (SAMPLE_ROWS, p.n_r, len(p.tau), SAMPLE_SOLVE))
+              "screening solve" % (sample_rows(p), p.n_r, len(p.tau), SAMPLE_SOLVE))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -243,7 +252,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--prec", default="f16x3", choices=["fp32", "fp64", "f16x3", "bf16x3"])
-    ap.add_argument("--workload", default="si8", choices=["si8", "mid", "gamma_toy", "si64"])
+    ap.add_argument("--workload", default="si64", choices=["si8", "mid", "gamma_toy", "si64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-stage pass")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
@@ -254,10 +263,19 @@ def main():
     from paper_1607_02859_gb300 import inputs
     p = getattr(inputs, args.workload)()
     n_tau = len(p.tau)
+    grids = "log-spaced tau in [0.05, 40], omega_k = 1/tau_(N-1-k), weight ridge 1e-6 (the workload's given grid)"
+    if args.workload != "gamma_toy" and args.impl == "gw":
+        # optimised (MP2 minimax) time and frequency grids from the library's host setup
+        from paper_1607_02859_gb300 import gw as _gw
+        g = _gw.mp2_grids(n_tau, p.x_min, p.x_max)
+        p = inputs.on_grids(p, g["tau"], g["omega"], 0.0)
+        grids = "MP2 minimax tau/omega grids (gw_mp2_grids), weights fitted without ridge"
+    elif args.workload != "gamma_toy":
+        grids = "MP2 minimax tau/omega grids"
     workload = {"workload": "%s: %dx%dx%d grid (N_r=%d), %d+%d %s bands, %d tau/i omega, chi0 %dx%d, Sigma_nn for %d bands"
                 % (args.workload, *p.n, p.n_r, p.n_occ, p.n_b - p.n_occ, "real" if p.real else "complex", n_tau,
                    p.n_chi, p.n_chi, len(p.bands)),
-                "prec": args.prec, "sigma": args.sigma,
+                "prec": args.prec, "sigma": args.sigma, "grids": grids,
                 "l2": "per-step working set > 40 GB >> 129 MB L2; L2 also flushed between steps",
                 "accuracy": ACCURACY.get(args.prec, "")}
     if args.impl == "reference":
@@ -400,9 +418,11 @@ def main():
                                       % MEASURED_TRAFFIC[(args.workload, args.prec, dom)]["profile"])
 
     # end to end through the public API: orbitals copied from pinned host memory every step,
-    # Sigma read back to the host inside the call
+    # Sigma read back to the host inside the call; at most E2E_STEPS steps (a step of the
+    # 36^3 workload takes ~10 s)
     e_times = []
-    for _ in range(0 if args.no_e2e else args.steps):
+    e_steps = 0 if args.no_e2e else min(args.steps, E2E_STEPS)
+    for _ in range(e_steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -412,7 +432,7 @@ def main():
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1) / 1e3)
     t_e2e = max_over_ranks(float(np.sum(e_times)) if e_times else float("nan"), dist)
-    e2e = {"value": job_value(world, fl["total"], args.steps, t_e2e), "unit": "TFLOP/s",
+    e2e = {"value": job_value(world, fl["total"], max(e_steps, 1), t_e2e), "unit": "TFLOP/s", "steps": e_steps,
            "h2d_bytes_per_step": int(psi_h.numel() * psi_h.element_size()),
            "d2h_bytes_per_step": int(len(p.bands) * (3 * n_tau + N_REAL) * 16 + len(p.bands) * (48 + 8 * N_REAL)
                                      + 2 * len(p.bands) * n_tau * 8
@@ -429,7 +449,7 @@ def main():
         f, t = oracle_sample(p)
         line["cpu_baseline"] = {"value": f / t / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                                 "sample": "FP64 numpy oracle: G rows + chi product for %d of %d rows at all %d tau, plus "
-                                          "one %d^2 screening solve (%.1f s)" % (SAMPLE_ROWS, p.n_r, n_tau, SAMPLE_SOLVE, t)}
+                                          "one %d^2 screening solve (%.1f s)" % (sample_rows(p), p.n_r, n_tau, SAMPLE_SOLVE, t)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

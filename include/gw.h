@@ -128,6 +128,22 @@ gw_status gw_fit_transform(int n, const double* tau_h, const double* omega_h,
                            double x_min, double x_max, int n_x, double ridge,
                            double* C_h, double* S_h, double* Cinv_h, double* fit_err_h);
 
+/* Optimised n-point imaginary-time and imaginary-frequency grids (Sec. II.A.2:
+ * the grids minimise the discretisation error of the direct MP2 energy in each
+ * domain) for transition energies x in [x_min, x_max] (Ha):
+ *   tau_j   minimise max_x |1 - x sum_j alpha_j exp(-2 x tau_j)|
+ *           (1/x = int dtau exp(-x|tau|)^2),
+ *   omega_k minimise max_x |1 - x sum_k sigma_k (2x/(x^2 + omega_k^2))^2|
+ *           (1/x = int dw/(2 pi) (2x/(x^2+w^2))^2),
+ * each a Chebyshev (minimax) approximation computed in FP64 by the Remez
+ * exchange with continuation in the number of terms.  Outputs ascending:
+ * tau_h [n] (1/Ha), omega_h [n] (Ha); alpha_h, sigma_h [n] (may be NULL);
+ * err_h [2] (may be NULL) receives the two largest relative errors.  Use the
+ * grids with gw_fit_transform (ridge 0).  1 <= n <= 40, 0 < x_min < x_max,
+ * x_max/x_min <= 1e7.  Host only, milliseconds. */
+gw_status gw_mp2_grids(int n, double x_min, double x_max, double* tau_h, double* omega_h,
+                       double* alpha_h, double* sigma_h, double* err_h);
+
 /* Inverse of an n x n transform matrix (Eqs. INV_CT_FFT, INV_ST_FFT: the
  * matrices xi cos and zeta sin are the inverses of gamma cos and lambda sin) by
  * Gauss-Jordan elimination with partial pivoting in FP64.  Host only.

@@ -74,25 +74,34 @@ def ct(f_tau, C):
     return np.tensordot(C, f_tau, axes=(1, 0))
 
 
-def pair_matrix_elements_fft(psi, i, a_bands, n, lattice, fft_index):
+def fftn_batch(x, workers=None):
+    """3-D DFT over the last three axes, sum_r x(r) exp(-2 pi i k.r / n): numpy's
+    FFT, or scipy's with `workers` threads (the same transform) when given."""
+    if workers:
+        import scipy.fft
+        return scipy.fft.fftn(x, axes=(1, 2, 3), workers=workers)
+    return np.fft.fftn(x, axes=(1, 2, 3))
+
+
+def pair_matrix_elements_fft(psi, i, a_bands, n, lattice, fft_index, workers=None):
     """M_ai(G) of Eq. CHI_g_it for one occupied band i and the bands a_bands, at
-    the G-set grid positions fft_index, with numpy's FFT as the transform step:
+    the G-set grid positions fft_index, with an FFT as the transform step:
     fftn(x)[k] = sum_r x(r) exp(-2 pi i k.r / n) = sum_r exp(-i G.r) x(r)."""
     vol = abs(np.linalg.det(lattice))
     dv = vol / int(np.prod(n))
     prod = psi[a_bands].conj() * psi[i][None, :]              # [Na][N_r]
-    f = np.fft.fftn(prod.reshape(len(a_bands), *n), axes=(1, 2, 3)).reshape(len(a_bands), -1)
+    f = fftn_batch(prod.reshape(len(a_bands), *n), workers).reshape(len(a_bands), -1)
     return dv * f[:, fft_index]
 
 
-def chi_rows_pair(psi, eps, n_occ, taus, rows, n, lattice, fft_index):
+def chi_rows_pair(psi, eps, n_occ, taus, rows, n, lattice, fft_index, workers=None):
     """Rows `rows` (G-set indices) of chi(G,G',tau) for every tau, by the pair
     sum of Eq. CHI_g_it: [N_tau][len(rows)][N_chi]."""
     vol = abs(np.linalg.det(lattice))
     un = np.arange(n_occ, psi.shape[0])
     out = np.zeros((len(taus), len(rows), len(fft_index)), dtype=np.complex128)
     for i in range(n_occ):
-        m = pair_matrix_elements_fft(psi, i, un, n, lattice, fft_index)   # [Nu][N_chi]
+        m = pair_matrix_elements_fft(psi, i, un, n, lattice, fft_index, workers)   # [Nu][N_chi]
         mr = m[:, rows]                                                    # [Nu][rows]
         for j, tau in enumerate(taus):
             w = np.exp(-(eps[n_occ:] - eps[i]) * tau)

@@ -19,6 +19,7 @@ cos_sin_sigma1/2):
 """
 import numpy as np
 
+from . import chi as _chi
 from . import green as _gr
 
 
@@ -65,7 +66,7 @@ def sigma_iw(s_unocc, s_occ, C, S):
     return sc @ C.T + 1j * (ss @ S.T)
 
 
-def sigma_pair_sparse(psi, eps, n_occ, mu, taus, entries, n, lattice, fft_index, bands):
+def sigma_pair_sparse(psi, eps, n_occ, mu, taus, entries, n, lattice, fft_index, bands, workers=None):
     """The conventional route of sigma_pair_tau for a W~(G,G',tau) with only a
     few nonzero entries, given as (j, j', values) with G-set indices j, j' and
     one value per tau:
@@ -83,7 +84,7 @@ def sigma_pair_sparse(psi, eps, n_occ, mu, taus, entries, n, lattice, fft_index,
     so = np.empty((len(bands), len(taus)))
     for b, n_ in enumerate(bands):
         prod = psi.conj() * psi[n_][None, :]
-        f = np.fft.fftn(prod.reshape(psi.shape[0], *n), axes=(1, 2, 3)).reshape(psi.shape[0], -1)
+        f = _chi.fftn_batch(prod.reshape(psi.shape[0], *n), workers).reshape(psi.shape[0], -1)
         a = dv * f[:, np.asarray(fft_index)[idx]]                  # [N_b][len(idx)]
         for t, tau in enumerate(taus):
             q = np.zeros(psi.shape[0])

@@ -28,7 +28,7 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
            "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh", "gw_sigma_diag_kmesh",
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
-           "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau"]
+           "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau", "gw_mp2_grids"]
 
 
 class GwError(RuntimeError):
@@ -86,6 +86,7 @@ _SIGS = {
                              _DP, _DP, _P]),
     "gw_qp_energies": (_I, [_P, _I, _I, _DP, _DP, _DP, _D, _DP, _I, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
     "gw_invert_transform": (_I, [_I, _DP, _DP]),
+    "gw_mp2_grids": (_I, [_I, _D, _D, _DP, _DP, _DP, _DP, _DP]),
     "gw_sigma_to_tau": (_I, [_P, _I, _I, _I, _DP, _DP, _DP, _DP, _P]),
 }
 
@@ -225,6 +226,18 @@ def fit_transform(tau, omega, x_min, x_max, n_x=4000, ridge=1e-6):
     _check(lib().gw_fit_transform(n, _dp(tau), _dp(omega), float(x_min), float(x_max), int(n_x), float(ridge),
                                   _dp(C), _dp(S), _dp(Ci), _dp(err)))
     return {"C": C, "S": S, "Cinv": Ci, "Sinv": invert_transform(S), "fit_err_cos": err[0], "fit_err_sin": err[1]}
+
+
+def mp2_grids(n, x_min, x_max):
+    """Optimised imaginary-time and frequency grids (gw_mp2_grids)."""
+    tau = np.zeros(int(n))
+    om = np.zeros(int(n))
+    al = np.zeros(int(n))
+    sg = np.zeros(int(n))
+    err = np.zeros(2)
+    _check(lib().gw_mp2_grids(int(n), float(x_min), float(x_max), _dp(tau), _dp(om), _dp(al), _dp(sg), _dp(err)))
+    return {"tau": tau, "omega": om, "alpha": al, "sigma": sg, "err_time": float(err[0]),
+            "err_frequency": float(err[1])}
 
 
 def invert_transform(M):

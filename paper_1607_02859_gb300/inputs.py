@@ -64,6 +64,15 @@ class Problem:
         return abs(float(np.linalg.det(self.lattice)))
 
 
+def on_grids(p, tau, omega, ridge=0.0):
+    """The same problem on other imaginary-time / frequency grids (for example
+    the optimised grids of the method's host setup), with the ridge of the
+    weight fit those grids want.  Pure data: no arithmetic on the grids."""
+    import dataclasses
+    return dataclasses.replace(p, tau=np.asarray(tau, dtype=np.float64).copy(),
+                               omega=np.asarray(omega, dtype=np.float64).copy(), ridge=float(ridge))
+
+
 def _sorted_lattice_points(n):
     """Integer triples g_d in [-n_d/2, n_d/2) ordered by (|g|^2, g1, g2, g3)."""
     ax = [np.arange(-(nd // 2), nd - nd // 2) for nd in n]
@@ -184,6 +193,23 @@ def tiny(seed=11, n=(6, 6, 6), a=(6.0, 6.5, 7.0), n_occ=4, n_unocc=20, n_tau=6, 
     return make_problem(n, a, n_occ, n_unocc, (-0.6, -0.05), (0.05, 2.0), 0.0, n_tau, seed,
                         n_bands_sigma=4, real=real, n_chi=n_chi, pin_edges=True,
                         name="tiny_%dx%dx%d" % n)
+
+
+def screening_chi(n_chi, n_w=2, rank=None, seed=60, decay=64.0):
+    """Seeded Hermitian negative semidefinite matrices shaped like chi0(G,G',i omega)
+    for screening tests at sizes where the oracle cannot form chi0 itself:
+    chi_w = -B_w B_w^H / rank with B_w [n_chi][rank] complex Gaussian rows damped
+    as (1 + j/decay)^-1 along the G-set index j (pair densities fall off with |G|).
+    Returns [n_w][n_chi][n_chi] complex128; the caller scales each matrix to the
+    screening strength it wants."""
+    rng = np.random.default_rng(seed)
+    rank = n_chi // 2 if rank is None else int(rank)
+    damp = 1.0 / (1.0 + np.arange(n_chi) / float(decay))
+    out = np.empty((n_w, n_chi, n_chi), dtype=np.complex128)
+    for w in range(n_w):
+        b = (rng.standard_normal((n_chi, rank)) + 1j * rng.standard_normal((n_chi, rank))) * damp[:, None]
+        out[w] = -(b @ b.conj().T) / rank
+    return out
 
 
 def serve_mix(count=6, seed=40, n_chi_cap=1536):

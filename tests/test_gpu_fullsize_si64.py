@@ -1,0 +1,97 @@
+"""Full-size checks at the 36^3 workload the benchmark times by default (64-atom
+cell: 128+4096 complex bands, 20 tau/omega on the optimised grids, chi0 on the
+lowest 8192 G): chi0(i tau) and chi0(i omega) on sampled G rows with every band
+against the pair sum (Eq. CHI_g_it), the screening at N_chi = 8192 against the
+FP64 dense solve, and Sigma_nn summed over all 4224 bands for a sparse W~.
+The oracle's FFTs run on all host cores (scipy.fft workers)."""
+import numpy as np
+import pytest
+
+from oracle import chi as ochi
+from oracle import grids as ogrids
+from oracle import gvec as ogv
+from oracle import screen as osc
+from oracle import sigma as osg
+from paper_1607_02859_gb300 import gw, inputs
+
+from test_gpu_fullsize import (CHI_TAU_TOL, CHI_TOL, MEV, W_TOL, WORKERS, chi_rows_check, ctx, optimised,  # noqa: F401
+                               scaled_screening_input, screen_check)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def si64():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    p = optimised(inputs.si64())
+    gv = ogv.g_set(p.n, p.n_chi)
+    idx = ogv.fft_index(gv, p.n)
+    mats = ogrids.transform_matrices(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
+    return p, gv, idx, mats
+
+
+@pytest.fixture(scope="module")
+def si64_rows(si64):
+    p, gv, idx, mats = si64
+    rows = sorted(np.random.default_rng(13).choice(p.n_chi, 12, replace=False).tolist())
+    return rows, ochi.chi_rows_pair(p.psi, p.eps, p.n_occ, p.tau, rows, p.n, p.lattice, idx, WORKERS)
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_si64_chi0_rows(ctx, si64, si64_rows, prec):
+    """K = 128 + 4096 bands through the tensor-core accumulation (f16x3, the bench's
+    precision) and the FP32 CUDA-core GEMM, rows of 46656 points (two-pass row transform)."""
+    p, gv, idx, mats = si64
+    rows, ref_tau = si64_rows
+    err_tau, err, herm = chi_rows_check(ctx, p, idx, mats, prec, rows, ref_tau)
+    assert err_tau < CHI_TAU_TOL[prec], err_tau
+    assert err < CHI_TOL, err
+    assert herm < CHI_TOL, herm
+
+
+@pytest.fixture(scope="module")
+def si64_screen(si64):
+    p, gv, idx, mats = si64
+    vh = ogv.v_sqrt(gv, p.lattice)
+    chi = scaled_screening_input(p.n_chi, vh, [8.0, 0.05], seed=62)
+    return chi, np.stack([osc.screen_one(c, vh) for c in chi])
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "fp32"])
+def test_si64_screen_vs_oracle(ctx, si64, si64_screen, prec):
+    p, gv, idx, mats = si64
+    chi, w_ref = si64_screen
+    errs, res = screen_check(ctx, gw.make_grid(p.n, p.lattice), gv, chi, w_ref, prec)
+    print("si64 screening %s: W~ relative error %s, residual probe %s" % (prec, errs, res))
+    assert max(errs) < W_TOL[prec], errs
+
+
+def test_si64_sigma_sparse_w(ctx, si64):
+    """Sigma_nn for four of the 32 bands (all 4224 bands in the sums over m), f16x3."""
+    p, gv, idx, mats = si64
+    prec = "f16x3"
+    grid = gw.make_grid(p.n, p.lattice)
+    psi = torch.from_numpy(p.psi).to("cuda", dtype=torch.complex64)
+    n = len(p.tau)
+    vol = p.volume
+    bands = p.bands[[0, 15, 16, 31]]
+    base = [(3, 3, -0.9, 0.25), (60, 60, -0.5, 0.6), (3, 60, 0.1 + 0.05j, 0.4), (60, 3, 0.1 - 0.05j, 0.4),
+            (2000, 2000, -0.3, 1.1)]
+    w = torch.zeros((n, p.n_chi, p.n_chi), dtype=torch.complex64, device="cuda")
+    entries = [(a, b, vol * c * np.exp(-om * p.tau)) for (a, b, c, om) in base]
+    for (a, b, v) in entries:
+        for j in range(n):
+            w[j, a, b] = complex(v[j])
+    su, so = osg.sigma_pair_sparse(p.psi, p.eps, p.n_occ, p.mu, p.tau, entries, p.n, p.lattice, idx, bands,
+                                   WORKERS)
+    ref = osg.sigma_iw(su, so, mats["C"], mats["S"])
+    out = gw.sigma_diag(ctx, grid, psi, p.eps, p.n_occ, p.mu, bands, p.tau, p.omega, mats["C"], mats["S"], w, idx,
+                        prec)
+    err = np.max(np.abs(out["sigma_iw"] - ref))
+    print("si64 Sigma_nn (sparse W~) max |dSigma(i omega)| %.2e Ha" % err)
+    assert err < MEV, err
+    assert err < 1e-4 * np.max(np.abs(ref))
+    del w, psi
+    torch.cuda.empty_cache()
