@@ -260,13 +260,32 @@ gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t
  * frequency of X = eps~^{-1} - 1 before W~ is formed: with the residual
  * R = chi~ - eps~ X = chi~ - X + chi~ X (chi~ = v^1/2 chi v^1/2), X <- X + (1 + X) R,
  * which squares the relative error of X each step (Newton-Schulz for the
- * inverse of eps~; the same solve of Eq. W_correlated).  Costs two N^3 FP64
- * complex GEMMs per step and frequency and 64 n_chi^2 bytes more scratch; the
- * result is then limited by the working precision of w_w.  refine_iters = 0 is
- * gw_screen_W. */
+ * inverse of eps~; the same solve of Eq. W_correlated).  GW_FP64 and GW_FP32:
+ * two N^3 FP64 complex GEMMs per step and frequency on CUDA cores, 64 n_chi^2
+ * bytes more scratch.  GW_F16X3 / GW_BF16X3: the product chi~ X on tcgen05 as
+ * exact fp16 slice products summed in FP64 (gw_zgemm_sliced, 5 levels: 36 bits
+ * of the row and column maxima) and X R as split fp16 products (R is small),
+ * about 160 n_chi^2 bytes more scratch.  The result is then limited by the
+ * working precision of w_w.  refine_iters = 0 is gw_screen_W. */
 gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h,
                              int n_omega, gw_prec prec, int refine_iters, const void* chi_w,
                              void* w_w, double* resid_h, void* stream);
+
+/* Complex FP64 matrix product C = A B with FP64-class accuracy on the fp16
+ * tensor cores (the product chi~ X of the refinement residual above; the paper
+ * has no counterpart).  Each row of A and column of B is scaled by a power of
+ * two and cut into 6-bit integer slices (exact in fp16); the product of two
+ * slices summed over 4096 real K elements is an integer below 2^24 and so
+ * exact in the FP32 accumulator; slice pairs with a + b <= levels (largest
+ * first) are scaled back and added in FP64.  The error is below about
+ * 2^(-6(levels+1)) * K * max|A_i.| max|B_.j| per element (levels 5: 2^-36).
+ * A [M][K] (lda), B [K][N] (ldb), C [M][N] (ldc) complex double, device,
+ * 16-byte aligned, row-major; C is overwritten and must not overlap A or B.
+ * 1 <= levels <= 7; scratch (context arena): about 2 (levels+1) K (2M + 4N)
+ * bytes.  Synchronous (reports GW_ERR_TIMEOUT from the bounded pipeline
+ * waits). */
+gw_status gw_zgemm_sliced(gw_ctx* ctx, int M, int N, int K, const void* A, long lda, const void* B, long ldb,
+                          void* C, long ldc, int levels, void* stream);
 
 /* Diagonal correlation self-energy (Eqs. Sigma_occ, Sigma_rr and the first term
  * of Sigma_occ_reduce; even/odd split Eqs. cos_sin_sigma_matrix1/2; CT+ST Eqs.

@@ -100,10 +100,12 @@ def chi_rows_pair(psi, eps, n_occ, taus, rows, n, lattice, fft_index, workers=No
     vol = abs(np.linalg.det(lattice))
     un = np.arange(n_occ, psi.shape[0])
     out = np.zeros((len(taus), len(rows), len(fft_index)), dtype=np.complex128)
+    taus = np.asarray(taus, dtype=np.float64)
     for i in range(n_occ):
         m = pair_matrix_elements_fft(psi, i, un, n, lattice, fft_index, workers)   # [Nu][N_chi]
         mr = m[:, rows]                                                    # [Nu][rows]
-        for j, tau in enumerate(taus):
-            w = np.exp(-(eps[n_occ:] - eps[i]) * tau)
-            out[j] += (mr.T * w) @ m.conj()
+        w = np.exp(-np.outer(taus, eps[n_occ:] - eps[i]))                 # [N_tau][Nu]
+        # sum over a of exp(-(eps_a - eps_i) tau_j) M_ai(G_row) M_ai(G')^*, all tau in one product
+        lhs = (w[:, None, :] * mr.T[None, :, :]).reshape(len(taus) * len(rows), -1)
+        out += (lhs @ m.conj()).reshape(len(taus), len(rows), -1)
     return -(2.0 / vol) * out

@@ -495,13 +495,78 @@ static gw_status refine_one(gw_ctx* ctx, int n, const typename cpx<T>::t* chi, c
   return launch_check(ctx, "refine_store_kernel");
 }
 
+// The same refinement for the tensor-core precisions, with the product chi~ X
+// of the residual on the tensor cores as exact fp16 slice products (slice pairs
+// up to kRefineLevels, i.e. 36 bits of the row and column maxima) summed in
+// FP64, and the correction X R as three fp16 split products (R is small: the
+// correction needs only the working precision).  Work: X, chi~, R in FP64 and
+// R, X R in FP32 (the last slot of ws); X in FP32 goes to the upper part of
+// xl, which the final store overwrites with the lower triangle.
+constexpr int kRefineLevels = 5;
+
+__global__ void to_f32_kernel(const double2* __restrict__ X, float2* __restrict__ Y, long nn) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x)
+    Y[e] = make_float2((float)X[e].x, (float)X[e].y);
+}
+
+__global__ void refine_update_f32_kernel(double2* X, const double2* __restrict__ R, const float2* __restrict__ XR,
+                                         long nn) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < nn; e += (long)gridDim.x * blockDim.x)
+    X[e] = make_double2(X[e].x + R[e].x + (double)XR[e].x, X[e].y + R[e].y + (double)XR[e].y);
+}
+
+static gw_status refine_one_tc(gw_ctx* ctx, gw_prec prec, int n, const float2* chi, const double* dvh, float2* xl,
+                               double2* ws, void* tcs, void* sls, int iters, cudaStream_t st) {
+  const long nn = (long)n * n;
+  double2* X = ws;
+  double2* Ct = ws + nn;
+  double2* R = ws + 2 * nn;
+  float2* R32 = reinterpret_cast<float2*>(ws + 3 * nn);
+  float2* XR32 = R32 + nn;
+  const dim3 tb(128), gb((n + 127) / 128, n);
+  const int eb = (int)std::min<long>((nn + 255) / 256, (long)ctx->num_sms * 8);
+  int* tstat = ctx->dflag + 4;
+  gw_status rc;
+  refine_expand_kernel<float><<<gb, tb, 0, st>>>(xl, chi, dvh, X, Ct, n);
+  if ((rc = launch_check(ctx, "refine_expand_kernel"))) return rc;
+  for (int it = 0; it < iters; ++it) {
+    // R = chi~ X (FP64-class), then R = chi~ - X + R
+    if ((rc = tc_zgemm_sliced(ctx, n, n, n, Ct, n, X, n, R, n, kRefineLevels, tstat, sls, st))) return rc;
+    refine_resid_kernel<<<eb, 256, 0, st>>>(Ct, X, R, nn);
+    if ((rc = launch_check(ctx, "refine_resid_kernel"))) return rc;
+    to_f32_kernel<<<eb, 256, 0, st>>>(X, xl, nn);
+    to_f32_kernel<<<eb, 256, 0, st>>>(R, R32, nn);
+    if ((rc = launch_check(ctx, "to_f32_kernel"))) return rc;
+    ctx->launches++;
+    TcGemm g;
+    g.M = g.N = g.K = n;
+    g.A = xl;
+    g.lda = n;
+    g.a_trans = g.a_conj = false;
+    g.B = R32;
+    g.ldb = n;
+    g.b_trans = g.b_conj = false;
+    g.C = XR32;
+    g.ldc = n;
+    g.alpha = 1.0f;
+    g.accumulate = false;
+    g.tri = 0;
+    g.status = tstat;
+    if ((rc = tc_gemm(ctx, prec, g, tcs, st))) return rc;
+    refine_update_f32_kernel<<<eb, 256, 0, st>>>(X, R, XR32, nn);
+    if ((rc = launch_check(ctx, "refine_update_f32_kernel"))) return rc;
+  }
+  refine_store_kernel<float><<<gb, tb, 0, st>>>(X, xl, n);
+  return launch_check(ctx, "refine_store_kernel");
+}
+
 // One batch of frequencies: chi[B][n][n] -> W[B][n][n] (may alias chi), with
 // work buffers E and P of the same shape.  tcs: tensor-core scratch (NULL for
 // the CUDA-core precisions).
 template <typename T>
 static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const void* chi, const double* dvh, void* E,
                               void* Pm, void* W, double2* probe, double* resid_h, void* tcs, int refine,
-                              double2* rws, cudaStream_t st) {
+                              double2* rws, void* sls, cudaStream_t st) {
   using C = typename cpx<T>::t;
   gw_status rc;
   C* e = static_cast<C*>(E);
@@ -609,9 +674,18 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
   assemble_kernel<T><<<dim3(n, B), 256, 0, st>>>(e, nn, p, nn, n);
   if ((rc = launch_check(ctx, "assemble_kernel"))) return rc;
   if (refine > 0)
-    for (int b = 0; b < B; ++b)
+    for (int b = 0; b < B; ++b) {
+      if constexpr (std::is_same<T, float>::value) {
+        if (tcs) {
+          if ((rc = refine_one_tc(ctx, prec, n, static_cast<const C*>(chi) + b * nn, dvh, e + b * nn, rws, tcs, sls,
+                                  refine, st)))
+            return rc;
+          continue;
+        }
+      }
       if ((rc = refine_one<T>(ctx, n, static_cast<const C*>(chi) + b * nn, dvh, e + b * nn, rws, refine, st)))
         return rc;
+    }
   if (resid_h)
     for (int b = 0; b < B; ++b)
       if ((rc = residual_probe<T>(ctx, n, static_cast<const C*>(chi) + b * nn, dvh, e + b * nn, probe, resid_h + b,
@@ -620,6 +694,13 @@ static gw_status screen_batch(gw_ctx* ctx, gw_prec prec, int n, int B, const voi
   const int nt = (n + 31) / 32;
   finalize_kernel<T><<<dim3(nt, nt, B), dim3(32, 8), 0, st>>>(e, nn, dvh, static_cast<C*>(W), nn, n);
   return launch_check(ctx, "finalize_kernel");
+}
+
+// Tensor-core GEMM scratch of the screening: panels of kTB over a batch, and
+// with refinement the full n x n x n correction product.
+static size_t screen_tc_scratch(int n_chi, int bsz, bool refine) {
+  const size_t a = tc_gemm_scratch(n_chi, n_chi, kTB, bsz);
+  return refine ? std::max(a, tc_gemm_scratch(n_chi, n_chi, n_chi, 1)) : a;
 }
 
 // Frequencies per batch (the two work matrices of a batch within 64 GB) and
@@ -638,8 +719,9 @@ size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* n
   probe.take<char>(bsz * nn * es);
   probe.take<char>(bsz * nn * es);
   probe.take<double2>(4 * (size_t)n_chi);
-  if (tc) probe.take<char>(tc_gemm_scratch(n_chi, n_chi, kTB, bsz));
+  if (tc) probe.take<char>(screen_tc_scratch(n_chi, bsz, refine));
   if (refine) probe.take<double2>(4 * nn);
+  if (refine && tc) probe.take<char>(tc_zgemm_sliced_scratch(n_chi, n_chi, n_chi, kRefineLevels));
   if (bsz_out) *bsz_out = bsz;
   if (nbatch_out) *nbatch_out = nbatch;
   return probe.off;
@@ -691,8 +773,7 @@ extern "C" gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
   int bsz = 0, nbatch = 0;
   const size_t need = screen_scratch(n_chi, n_omega, prec, &bsz, &nbatch, refine_iters > 0);
-  const size_t tcs_bytes =
-      tc ? tc_gemm_scratch(n_chi, n_chi, kTB, bsz) : 0;
+  const size_t tcs_bytes = tc ? screen_tc_scratch(n_chi, bsz, refine_iters > 0) : 0;
   if ((st = reserve(ctx, need))) return st;
   Carver cv(ctx->arena);
   double* dvh = cv.take<double>(n_chi);
@@ -701,6 +782,8 @@ extern "C" gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_
   double2* pr = cv.take<double2>(4 * (size_t)n_chi);
   void* tcs = tc ? cv.take<char>(tcs_bytes) : nullptr;
   double2* rws = refine_iters > 0 ? cv.take<double2>(4 * nn) : nullptr;
+  void* sls = refine_iters > 0 && tc ? cv.take<char>(tc_zgemm_sliced_scratch(n_chi, n_chi, n_chi, kRefineLevels))
+                                     : nullptr;
   if ((st = upload(ctx, dvh, vh.data(), sizeof(double) * n_chi, s))) return st;
   if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 8 * sizeof(int), s), "memset flag"))) return st;
   int first_bad = -1;
@@ -710,8 +793,8 @@ extern "C" gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_
     char* out = static_cast<char*>(w_w) + k0 * nn * es;
     double* rk = resid_h ? resid_h + k0 : nullptr;
     if (is_fp64(prec))
-      st = screen_batch<double>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, nullptr, refine_iters, rws, s);
-    else st = screen_batch<float>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, tcs, refine_iters, rws, s);
+      st = screen_batch<double>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, nullptr, refine_iters, rws, nullptr, s);
+    else st = screen_batch<float>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, tcs, refine_iters, rws, sls, s);
     if (st) return st;
     if (nbatch > 1 && first_bad < 0) {
       int f[3] = {0, 0, 0};

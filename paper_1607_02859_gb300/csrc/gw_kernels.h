@@ -84,4 +84,48 @@ size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* n
 size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec,
                      bool full = false);
 gw_status upload_scales(gw_ctx* ctx, void* dst, const GreenScales& gs, gw_prec prec, cudaStream_t st);
+
+// ---- the self-energy pass split for plans (gw_sigma.cu)
+// Device tables of one evaluation: G-set maps, bands, per-tau band factors
+// (n_b 8-byte slots per tau, packed in the working precision), C, S, omega and
+// real frequencies, the accumulators, the results and the Thiele status.
+struct SigmaTables {
+  int* map;
+  int* inv;
+  int* bands;
+  char* scale;
+  double* tab;
+  double2* acc2;
+  double2* out;
+  int* stat;
+};
+// Work buffers of one evaluation (r-block rows of G and W~, the W~(r,G') plane
+// stack, tensor-core scratch).
+struct SigmaWork {
+  bool fused;
+  double2* vout;
+  char* wrg;
+  char* gob;
+  char* gub;
+  char* wrr;
+  void* tcs;
+};
+void sigma_carve_tables(Carver& cv, const GridInfo& g, int n_b, int n, int n_chi, int n_n, int n_real, bool full,
+                        SigmaTables& t);
+void sigma_carve_work(Carver& cv, const GridInfo& g, int n_b, int n_occ, int n_chi, int n_n, gw_prec prec, bool full,
+                      SigmaWork& w);
+gw_status sigma_check(gw_ctx* ctx, const gw_grid* grid, GridInfo* g, int n_b, int n_occ, const void* psi,
+                      const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n, const double* tau_h,
+                      const double* omega_h, const double* C_h, const double* S_h, const void* w_tau, int n_chi,
+                      const int32_t* fft_index_h, gw_prec prec, bool full, const double* w_real_h, int n_real,
+                      std::vector<int>& map, std::vector<int>& inv, std::vector<GreenScales>& scales);
+gw_status sigma_upload_tables(gw_ctx* ctx, const SigmaTables& t, const GridInfo& g, int n_b, int n, int n_chi,
+                              const std::vector<int>& map, const std::vector<int>& inv, const int32_t* bands_h, int n_n,
+                              const std::vector<GreenScales>& scales, const double* C_h, const double* S_h,
+                              const double* omega_h, const double* w_real_h, int n_real, gw_prec prec, cudaStream_t s);
+gw_status sigma_kernels(gw_ctx* ctx, const GridInfo& g, gw_prec prec, bool full, int n_b, int n_occ, const void* psi,
+                        int n_n, int n, int n_chi, int n_real, const std::vector<GreenScales>& scales,
+                        const SigmaTables& t, const SigmaWork& w, const void* w_tau, cudaStream_t s);
+gw_status sigma_finish_launch(gw_ctx* ctx, const double* acc, int n_n, int n, const double* tab, int n_real,
+                              double2* out, int* stat, cudaStream_t s);
 }  // namespace gw

@@ -488,14 +488,9 @@ static gw_status launch_sigma_outer(gw_ctx* ctx, gw_prec prec, const double2* vo
   return launch_check(ctx, "sigma_outer_kernel");
 }
 
-// Even/odd split, CT + ST and Thiele continuation of the accumulated
-// Sigma(tau) (acc [2][n_n][n]: unoccupied, occupied), then the results to the
-// host.  tab: C [n][n], S [n][n], omega [n], real frequencies [n_real] in one
-// device block; out [n_n][n] + [n_n][n_real] complex; stat [n_n].
-gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* tab, int n_real, double2* out,
-                       int* stat, const int32_t* labels, double* sigma_tau_h, double* sigma_iw_h,
-                       double* sigma_real_h, cudaStream_t s) {
-  gw_status st;
+// The kernel of sigma_finish alone (device results, no synchronisation).
+gw_status sigma_finish_launch(gw_ctx* ctx, const double* acc, int n_n, int n, const double* tab, int n_real,
+                              double2* out, int* stat, cudaStream_t s) {
   const double* dC = tab;
   const double* dS = dC + (size_t)n * n;
   const double* dom = dS + (size_t)n * n;
@@ -503,7 +498,15 @@ gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* t
   double2* out_re = out + (size_t)n_n * n;
   sigma_finish_kernel<<<(n_n + 63) / 64, 64, 0, s>>>(acc, acc + (size_t)n_n * n, n_n, n, dC, dS, dom, dwr, n_real,
                                                       out, n_real > 0 ? out_re : nullptr, stat);
-  if ((st = launch_check(ctx, "sigma_finish_kernel"))) return st;
+  return launch_check(ctx, "sigma_finish_kernel");
+}
+
+// Results of sigma_finish_launch to the host (synchronises s).
+static gw_status sigma_fetch(gw_ctx* ctx, const double* acc, int n_n, int n, int n_real, const double2* out,
+                             const int* stat, const int32_t* labels, double* sigma_tau_h, double* sigma_iw_h,
+                             double* sigma_real_h, cudaStream_t s) {
+  gw_status st;
+  const double2* out_re = out + (size_t)n_n * n;
   std::vector<double2> h_iw((size_t)n_n * n), h_re((size_t)n_n * std::max(n_real, 1));
   std::vector<int> h_stat(n_n);
   std::vector<double> h_acc(2 * (size_t)n_n * n);
@@ -521,27 +524,189 @@ gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* t
   return GW_OK;
 }
 
-size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec,
-                     bool full) {
+// Even/odd split, CT + ST and Thiele continuation of the accumulated
+// Sigma(tau) (acc [2][n_n][n]: unoccupied, occupied), then the results to the
+// host.  tab: C [n][n], S [n][n], omega [n], real frequencies [n_real] in one
+// device block; out [n_n][n] + [n_n][n_real] complex; stat [n_n].
+gw_status sigma_finish(gw_ctx* ctx, double* acc, int n_n, int n, const double* tab, int n_real, double2* out,
+                       int* stat, const int32_t* labels, double* sigma_tau_h, double* sigma_iw_h,
+                       double* sigma_real_h, cudaStream_t s) {
+  gw_status st = sigma_finish_launch(ctx, acc, n_n, n, tab, n_real, out, stat, s);
+  if (st) return st;
+  return sigma_fetch(ctx, acc, n_n, n, n_real, out, stat, labels, sigma_tau_h, sigma_iw_h, sigma_real_h, s);
+}
+
+// Up to this many bands, the tensor-core precisions fuse the contraction into
+// the G formation (tc_sigma_rows): G never goes to memory.
+constexpr int kFusedBands = 32;
+
+void sigma_carve_tables(Carver& cv, const GridInfo& g, int n_b, int n, int n_chi, int n_n, int n_real, bool full,
+                        SigmaTables& t) {
+  const size_t nnm = full ? (size_t)n_n * n_n : (size_t)n_n;
+  t.map = cv.take<int>(n_chi);
+  t.inv = cv.take<int>(g.nr);
+  t.bands = cv.take<int>(n_n);
+  t.scale = cv.take<char>((size_t)n * n_b * 8);
+  t.tab = cv.take<double>(4 * (size_t)n * n + 2 * n + std::max(n_real, 1));
+  t.acc2 = cv.take<double2>((full ? 2 : 1) * nnm * n);   // [2][n_n][n] real, or [2][n_n][n_n][n] complex
+  t.out = cv.take<double2>(nnm * n + (size_t)n_n * std::max(n_real, 1));
+  t.stat = cv.take<int>(n_n);
+}
+
+void sigma_carve_work(Carver& cv, const GridInfo& g, int n_b, int n_occ, int n_chi, int n_n, gw_prec prec, bool full,
+                      SigmaWork& w) {
   const size_t es = csize(prec);
   const int rb = std::min(g.nr, 2048);
-  const size_t nnm = full ? (size_t)n_n * n_n : (size_t)n_n;
+  w.fused = (prec == GW_F16X3 || prec == GW_BF16X3) && !full && n_n <= kFusedBands;
+  w.vout = full ? cv.take<double2>(2 * (size_t)n_n * rb) : nullptr;
+  w.wrg = cv.take<char>((size_t)g.nr * n_chi * es);
+  w.gob = cv.take<char>((size_t)rb * g.nr * es);
+  w.gub = cv.take<char>((size_t)rb * g.nr * es);
+  w.wrr = cv.take<char>((size_t)rb * g.nr * es);
+  w.tcs = (prec == GW_F16X3 || prec == GW_BF16X3)
+              ? cv.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false, w.fused ? n_n : 0))
+              : nullptr;
+}
+
+size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_n, int n_real, gw_prec prec,
+                     bool full) {
   Carver probe(nullptr);
-  probe.take<int>(n_chi);
-  probe.take<int>(g.nr);
-  probe.take<int>(n_n);
-  probe.take<double>((size_t)n * n_b);
-  probe.take<double>(4 * (size_t)n * n + 2 * n + std::max(n_real, 1));
-  probe.take<double2>((full ? 2 : 1) * nnm * n);   // acc: [2][n_n][n] real, or [2][n_n][n_n][n] complex
-  probe.take<double2>(nnm * n + (size_t)n_n * std::max(n_real, 1));
-  probe.take<int>(n_n);
-  if (full) probe.take<double2>(2 * (size_t)n_n * rb);
-  probe.take<char>((size_t)g.nr * n_chi * es);
-  probe.take<char>((size_t)rb * g.nr * es);
-  probe.take<char>((size_t)rb * g.nr * es);
-  probe.take<char>((size_t)rb * g.nr * es);
-  if (prec == GW_F16X3 || prec == GW_BF16X3) probe.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false));
+  SigmaTables t;
+  SigmaWork w;
+  sigma_carve_tables(probe, g, n_b, n, n_chi, n_n, n_real, full, t);
+  sigma_carve_work(probe, g, n_b, n_occ, n_chi, n_n, prec, full, w);
   return probe.off;
+}
+
+gw_status sigma_upload_tables(gw_ctx* ctx, const SigmaTables& t, const GridInfo& g, int n_b, int n, int n_chi,
+                              const std::vector<int>& map, const std::vector<int>& inv, const int32_t* bands_h, int n_n,
+                              const std::vector<GreenScales>& scales, const double* C_h, const double* S_h,
+                              const double* omega_h, const double* w_real_h, int n_real, gw_prec prec, cudaStream_t s) {
+  gw_status st;
+  if ((st = upload(ctx, t.map, map.data(), sizeof(int) * n_chi, s))) return st;
+  if ((st = upload(ctx, t.inv, inv.data(), sizeof(int) * g.nr, s))) return st;
+  if ((st = upload(ctx, t.bands, bands_h, sizeof(int) * n_n, s))) return st;
+  for (int j = 0; j < n; ++j)
+    if ((st = upload_scales(ctx, t.scale + (size_t)j * n_b * 8, scales[j], prec, s))) return st;
+  double* dC = t.tab;
+  double* dS = dC + (size_t)n * n;
+  double* dom = dS + (size_t)n * n;
+  double* dwr = dom + n;
+  if ((st = upload(ctx, dC, C_h, sizeof(double) * n * n, s))) return st;
+  if ((st = upload(ctx, dS, S_h, sizeof(double) * n * n, s))) return st;
+  if ((st = upload(ctx, dom, omega_h, sizeof(double) * n, s))) return st;
+  if (n_real > 0 && (st = upload(ctx, dwr, w_real_h, sizeof(double) * n_real, s))) return st;
+  return GW_OK;
+}
+
+// The kernels of one self-energy evaluation on s, with the tables already on the
+// device: device-side memsets and launches only (no host copy, no
+// synchronisation), so that a plan can capture them in a CUDA graph.  Results
+// stay in t.out / t.stat (diagonal) or t.out (matrix); the tensor-core time-out
+// words in the scratch w.tcs.
+gw_status sigma_kernels(gw_ctx* ctx, const GridInfo& g, gw_prec prec, bool full, int n_b, int n_occ, const void* psi,
+                        int n_n, int n, int n_chi, int n_real, const std::vector<GreenScales>& scales,
+                        const SigmaTables& t, const SigmaWork& w, const void* w_tau, cudaStream_t s) {
+  gw_status st;
+  const size_t es = csize(prec);
+  const int rb = std::min(g.nr, 2048);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  const size_t nnm = full ? (size_t)n_n * n_n : (size_t)n_n;
+  const size_t acc_elems = (full ? 2 : 1) * nnm * n;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(t.acc2, 0, sizeof(double2) * acc_elems, s), "memset"))) return st;
+  double* acc = reinterpret_cast<double*>(t.acc2);
+  double* acc_u = acc;
+  double* acc_o = acc + (size_t)n_n * n;
+  double2* accm_u = t.acc2;
+  double2* accm_o = t.acc2 + nnm * n;
+  const double coef = g.dv * g.dv / g.volume;   // dV^2 and the 1/Omega of Eq. FFTW
+  bool first = true;
+  for (int j = 0; j < n; ++j) {
+    const char* wj = static_cast<const char*>(w_tau) + (size_t)j * n_chi * n_chi * es;
+    const char* sj = t.scale + (size_t)j * n_b * 8;
+    if ((st = launch_col_line(ctx, g, prec, +1, 1, wj, n_chi, w.wrg, n_chi, n_chi, t.inv, 1.0, s))) return st;
+    if ((st = launch_col_plane(ctx, g, prec, +1, w.wrg, n_chi, n_chi, 1.0, s))) return st;
+    for (int r0 = 0; r0 < g.nr; r0 += rb) {
+      const int rows = std::min(rb, g.nr - r0);
+      if (w.fused) {
+        // W~(r,R') of the block, then G formation with the contraction in its epilogue
+        if ((st = launch_row_fft(ctx, g, prec, 2, w.wrg + (size_t)r0 * n_chi * es, nullptr, n_chi, w.wrr, g.nr, t.map,
+                                 n_chi, rows, 1.0, s, t.inv)))
+          return st;
+        TcSigma sg;
+        sg.wrr = reinterpret_cast<const float2*>(w.wrr);
+        sg.ldw = g.nr;
+        sg.bands = t.bands;
+        sg.n_n = n_n;
+        sg.coef = coef;
+        sg.acc_u = acc_u + j;
+        sg.acc_o = acc_o + j;
+        sg.acc_stride = n;
+        sg.sk = reinterpret_cast<const float*>(sj);     // FP32 factors of tau_j (no host copy)
+        if ((st = tc_sigma_rows(ctx, g, n_b, n_occ, psi, scales[j], r0, rows, prec, sg, w.tcs, first, s))) return st;
+        first = false;
+        continue;
+      }
+      if (tc) {
+        st = tc_green_rows(ctx, g, n_b, n_occ, psi, scales[j], r0, rows, prec, w.gob, w.gub, w.tcs, first, s,
+                           reinterpret_cast<const float*>(sj));
+        first = false;
+      }
+      else st = green_rows(ctx, g, n_b, n_occ, psi, sj, scales[j], r0, rows, prec, w.gob, w.gub, s);
+      if (st) return st;
+      // W~(r,R') of the block (second step of Eq. FFTW), then the contraction
+      if ((st = launch_row_fft(ctx, g, prec, 2, w.wrg + (size_t)r0 * n_chi * es, nullptr, n_chi, w.wrr, g.nr, t.map,
+                               n_chi, rows, 1.0, s, t.inv)))
+        return st;
+      if (!full) {
+        if ((st = launch_sigma_contract(ctx, prec, w.wrr, w.gob, w.gub, g.nr, g.nr, rows, psi, t.bands, n_n, r0, coef,
+                                        acc_u + j, acc_o + j, n, s)))
+          return st;
+      } else {
+        if ((st = launch_sigma_contract(ctx, prec, w.wrr, w.gob, w.gub, g.nr, g.nr, rows, psi, t.bands, n_n, r0, coef,
+                                        nullptr, nullptr, n, s, nullptr, 0, w.vout, rb)))
+          return st;
+        if ((st = launch_sigma_outer(ctx, prec, w.vout, rb, rows, psi, g.nr, t.bands, n_n, r0, coef, accm_u + j,
+                                     accm_o + j, n, s)))
+          return st;
+      }
+    }
+  }
+  if (!full) return sigma_finish_launch(ctx, acc, n_n, n, t.tab, n_real, t.out, t.stat, s);
+  const long tot = (long)nnm * n;
+  const double* dS = t.tab + (size_t)n * n;
+  sigma_matrix_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(accm_u, accm_o, (int)nnm, n, t.tab, dS,
+                                                                             t.out);
+  return launch_check(ctx, "sigma_matrix_finish_kernel");
+}
+
+// Validation and host tables shared by the self-energy entry points and plans.
+gw_status sigma_check(gw_ctx* ctx, const gw_grid* grid, GridInfo* g, int n_b, int n_occ, const void* psi,
+                      const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n, const double* tau_h,
+                      const double* omega_h, const double* C_h, const double* S_h, const void* w_tau, int n_chi,
+                      const int32_t* fft_index_h, gw_prec prec, bool full, const double* w_real_h, int n_real,
+                      std::vector<int>& map, std::vector<int>& inv, std::vector<GreenScales>& scales) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  gw_status st = grid_info(ctx, grid, g);
+  if (st) return st;
+  if (!grid_supported(g->n1, g->n2, g->n3)) return fail(ctx, GW_ERR_UNSUPPORTED, "no kernels compiled for this grid");
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  if (!psi || !w_tau || !bands_h || !tau_h || !omega_h || !C_h || !S_h) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  if (n_b < 2 || n_b > g->nr) return fail(ctx, GW_ERR_SHAPE, "need 2 <= n_b <= N_r");
+  if (reinterpret_cast<uintptr_t>(psi) % 16) return fail(ctx, GW_ERR_ARG, "psi must be 16-byte aligned");
+  if ((st = check_energies(ctx, eps_h, n_b, n_occ, mu))) return st;
+  if (n < 1 || n > kMaxN) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
+  if (n_n < 1 || n_n > (full ? 256 : 1024))
+    return fail(ctx, GW_ERR_SHAPE, full ? "need 1 <= n_n <= 256" : "need 1 <= n_n <= 1024");
+  if (n_real < 0 || (n_real > 0 && !w_real_h)) return fail(ctx, GW_ERR_ARG, "bad real-axis request");
+  for (int b = 0; b < n_n; ++b)
+    if (bands_h[b] < 0 || bands_h[b] >= n_b) return fail(ctx, GW_ERR_ARG, "band index out of range");
+  for (int j = 0; j < n; ++j)
+    if (!(tau_h[j] > 0)) return fail(ctx, GW_ERR_ARG, "tau must be > 0");
+  if ((st = index_maps(ctx, *g, fft_index_h, n_chi, map, inv))) return st;
+  scales.resize(n);
+  for (int j = 0; j < n; ++j) scales[j] = green_scales(eps_h, n_b, n_occ, mu, tau_h[j]);
+  return GW_OK;
 }
 
 }  // namespace gw
@@ -556,113 +721,34 @@ static gw_status sigma_impl(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ
                             const void* w_tau, int n_chi, const int32_t* fft_index_h, gw_prec prec, bool full,
                             double* sigma_tau_h, double* sigma_iw_h, const double* w_real_h, int n_real,
                             double* sigma_real_h, cudaStream_t s) {
-  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
   GridInfo g;
-  gw_status st = grid_info(ctx, grid, &g);
-  if (st) return st;
-  if (!grid_supported(g.n1, g.n2, g.n3)) return fail(ctx, GW_ERR_UNSUPPORTED, "no kernels compiled for this grid");
-  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
-  if (!psi || !w_tau || !bands_h || !tau_h || !omega_h || !C_h || !S_h || !sigma_iw_h)
-    return fail(ctx, GW_ERR_ARG, "NULL pointer");
-  if (n_b < 2 || n_b > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 2 <= n_b <= N_r");
-  if (reinterpret_cast<uintptr_t>(psi) % 16) return fail(ctx, GW_ERR_ARG, "psi must be 16-byte aligned");
-  if ((st = check_energies(ctx, eps_h, n_b, n_occ, mu))) return st;
-  if (n < 1 || n > kMaxN) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
-  if (n_n < 1 || n_n > (full ? 256 : 1024))
-    return fail(ctx, GW_ERR_SHAPE, full ? "need 1 <= n_n <= 256" : "need 1 <= n_n <= 1024");
-  if (n_real < 0 || (n_real > 0 && (!w_real_h || !sigma_real_h))) return fail(ctx, GW_ERR_ARG, "bad real-axis request");
-  for (int b = 0; b < n_n; ++b)
-    if (bands_h[b] < 0 || bands_h[b] >= n_b) return fail(ctx, GW_ERR_ARG, "band index out of range");
-  for (int j = 0; j < n; ++j)
-    if (!(tau_h[j] > 0)) return fail(ctx, GW_ERR_ARG, "tau must be > 0");
   std::vector<int> map, inv;
-  if ((st = index_maps(ctx, g, fft_index_h, n_chi, map, inv))) return st;
-  const size_t es = csize(prec);
-  const int rb = std::min(g.nr, 2048);
+  std::vector<GreenScales> scales;
+  gw_status st = sigma_check(ctx, grid, &g, n_b, n_occ, psi, eps_h, mu, bands_h, n_n, n, tau_h, omega_h, C_h, S_h,
+                             w_tau, n_chi, fft_index_h, prec, full, w_real_h, n_real, map, inv, scales);
+  if (st) return st;
+  if (!sigma_iw_h || (n_real > 0 && !sigma_real_h)) return fail(ctx, GW_ERR_ARG, "NULL output pointer");
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
   const size_t nnm = full ? (size_t)n_n * n_n : (size_t)n_n;
   if ((st = reserve(ctx, sigma_scratch(g, n_b, n_occ, n, n_chi, n_n, n_real, prec, full)))) return st;
   Carver cv(ctx->arena);
-  int* dmap = cv.take<int>(n_chi);
-  int* dinv = cv.take<int>(g.nr);
-  int* dbands = cv.take<int>(n_n);
-  char* dscale = cv.take<char>((size_t)n * n_b * 8);
-  double* dC = cv.take<double>(4 * (size_t)n * n + 2 * n + std::max(n_real, 1));
-  double* dS = dC + (size_t)n * n;
-  double* dom = dS + (size_t)n * n;
-  double* dwr = dom + n;
-  const size_t acc_elems = (full ? 2 : 1) * nnm * n;     // in double2: [2][n_n][n] real or [2][n_n][n_n][n] complex
-  double2* acc2 = cv.take<double2>(acc_elems);
-  double* acc = reinterpret_cast<double*>(acc2);
-  double2* out_iw = cv.take<double2>(nnm * n + (size_t)n_n * std::max(n_real, 1));
-  int* dstat = cv.take<int>(n_n);
-  double2* vout = full ? cv.take<double2>(2 * (size_t)n_n * rb) : nullptr;
-  char* wrg = cv.take<char>((size_t)g.nr * n_chi * es);
-  char* gob = cv.take<char>((size_t)rb * g.nr * es);
-  char* gub = cv.take<char>((size_t)rb * g.nr * es);
-  char* wrr = cv.take<char>((size_t)rb * g.nr * es);
-  void* tcs = tc ? cv.take<char>(tc_scratch_bytes(g, n_b, n_occ, rb, false)) : nullptr;
-  if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
-  if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
-  std::vector<int> bv(bands_h, bands_h + n_n);
-  if ((st = upload(ctx, dbands, bv.data(), sizeof(int) * n_n, s))) return st;
-  std::vector<GreenScales> scales(n);
-  for (int j = 0; j < n; ++j) {
-    scales[j] = green_scales(eps_h, n_b, n_occ, mu, tau_h[j]);
-    if ((st = upload_scales(ctx, dscale + (size_t)j * n_b * 8, scales[j], prec, s))) return st;
-  }
-  if ((st = upload(ctx, dC, C_h, sizeof(double) * n * n, s))) return st;
-  if ((st = upload(ctx, dS, S_h, sizeof(double) * n * n, s))) return st;
-  if ((st = upload(ctx, dom, omega_h, sizeof(double) * n, s))) return st;
-  if (n_real > 0 && (st = upload(ctx, dwr, w_real_h, sizeof(double) * n_real, s))) return st;
-  if ((st = cuda_check(ctx, cudaMemsetAsync(acc2, 0, sizeof(double2) * acc_elems, s), "memset"))) return st;
-  double* acc_u = acc;
-  double* acc_o = acc + (size_t)n_n * n;
-  double2* accm_u = acc2;
-  double2* accm_o = acc2 + nnm * n;
-  const double coef = g.dv * g.dv / g.volume;   // dV^2 and the 1/Omega of Eq. FFTW
-  bool first = true;
-  for (int j = 0; j < n; ++j) {
-    const char* wj = static_cast<const char*>(w_tau) + (size_t)j * n_chi * n_chi * es;
-    if ((st = launch_col_line(ctx, g, prec, +1, 1, wj, n_chi, wrg, n_chi, n_chi, dinv, 1.0, s))) return st;
-    if ((st = launch_col_plane(ctx, g, prec, +1, wrg, n_chi, n_chi, 1.0, s))) return st;
-    for (int r0 = 0; r0 < g.nr; r0 += rb) {
-      const int rows = std::min(rb, g.nr - r0);
-      if (tc) {
-        st = tc_green_rows(ctx, g, n_b, n_occ, psi, scales[j], r0, rows, prec, gob, gub, tcs, first, s);
-        first = false;
-      }
-      else st = green_rows(ctx, g, n_b, n_occ, psi, dscale + (size_t)j * n_b * 8, scales[j], r0, rows, prec, gob, gub, s);
-      if (st) return st;
-      // W~(r,R') of the block (second step of Eq. FFTW), then the contraction
-      if ((st = launch_row_fft(ctx, g, prec, 2, wrg + (size_t)r0 * n_chi * es, nullptr, n_chi, wrr, g.nr, dmap, n_chi,
-                               rows, 1.0, s, dinv)))
-        return st;
-      if (!full) {
-        if ((st = launch_sigma_contract(ctx, prec, wrr, gob, gub, g.nr, g.nr, rows, psi, dbands, n_n, r0, coef,
-                                        acc_u + j, acc_o + j, n, s)))
-          return st;
-      } else {
-        if ((st = launch_sigma_contract(ctx, prec, wrr, gob, gub, g.nr, g.nr, rows, psi, dbands, n_n, r0, coef,
-                                        nullptr, nullptr, n, s, nullptr, 0, vout, rb)))
-          return st;
-        if ((st = launch_sigma_outer(ctx, prec, vout, rb, rows, psi, g.nr, dbands, n_n, r0, coef, accm_u + j,
-                                     accm_o + j, n, s)))
-          return st;
-      }
-    }
-  }
-  if (tc && (st = tc_check(ctx, tcs, s))) return st;
+  SigmaTables t;
+  SigmaWork w;
+  sigma_carve_tables(cv, g, n_b, n, n_chi, n_n, n_real, full, t);
+  sigma_carve_work(cv, g, n_b, n_occ, n_chi, n_n, prec, full, w);
+  if ((st = sigma_upload_tables(ctx, t, g, n_b, n, n_chi, map, inv, bands_h, n_n, scales, C_h, S_h, omega_h, w_real_h,
+                                n_real, prec, s)))
+    return st;
+  if ((st = sigma_kernels(ctx, g, prec, full, n_b, n_occ, psi, n_n, n, n_chi, n_real, scales, t, w, w_tau, s))) return st;
+  if (tc && (st = tc_check(ctx, w.tcs, s))) return st;
   if (!full)
-    return sigma_finish(ctx, acc, n_n, n, dC, n_real, out_iw, dstat, bands_h, sigma_tau_h, sigma_iw_h, sigma_real_h, s);
-  const long tot = (long)nnm * n;
-  sigma_matrix_finish_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(accm_u, accm_o, (int)nnm, n, dC, dS, out_iw);
-  if ((st = launch_check(ctx, "sigma_matrix_finish_kernel"))) return st;
+    return sigma_fetch(ctx, reinterpret_cast<const double*>(t.acc2), n_n, n, n_real, t.out, t.stat, bands_h,
+                       sigma_tau_h, sigma_iw_h, sigma_real_h, s);
   std::vector<double2> h_iw(nnm * n), h_acc(2 * nnm * n);
-  if ((st = cuda_check(ctx, cudaMemcpyAsync(h_iw.data(), out_iw, sizeof(double2) * nnm * n, cudaMemcpyDeviceToHost, s),
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(h_iw.data(), t.out, sizeof(double2) * nnm * n, cudaMemcpyDeviceToHost, s),
                        "copy sigma")))
     return st;
-  if (sigma_tau_h && (st = cuda_check(ctx, cudaMemcpyAsync(h_acc.data(), acc2, sizeof(double2) * 2 * nnm * n,
+  if (sigma_tau_h && (st = cuda_check(ctx, cudaMemcpyAsync(h_acc.data(), t.acc2, sizeof(double2) * 2 * nnm * n,
                                                            cudaMemcpyDeviceToHost, s), "copy sigma")))
     return st;
   if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sigma sync"))) return st;

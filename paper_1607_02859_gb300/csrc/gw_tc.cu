@@ -70,6 +70,18 @@ struct Params {
   float alpha_un;
   const int* dexp;        // device: e of the 2^e operand scaling
   int* status;            // device: [0] time-out flag, [1] where
+  // MODE 2 (self-energy): contraction of G o W~ with psi_n on the tensor cores
+  const float2* wrr;      // W~(r, R') rows of the block, [m_rows][ldw]
+  long ldw;
+  const float2* psi;      // psi [N_b][ldpsi]: psi_n(r) for the final sum over r
+  long ldpsi;
+  const int* bands;       // [n_n] device
+  int n_n, np;            // bands; MMA N = 2 n_n rounded up to 16
+  int r0;                 // grid row of the block's first row
+  double coef;            // dV^2 / Omega
+  double* acc_u;          // Sigma_unocc_nn(tau_j) at acc_u[n * acc_stride], Sigma_occ likewise
+  double* acc_o;
+  int acc_stride;
 };
 
 // Blocked accumulation.  The tensor cores add each MMA's products into the FP32
@@ -84,11 +96,24 @@ struct Params {
 // epilogue.
 //
 // MODE 0: out0 = -2 G_occ conj(G_unocc);  MODE 1: out0 = G_occ, out1 = G_unocc.
+// MODE 2: the self-energy contraction of the tile (first term of Eq.
+// Sigma_occ_reduce, Eq. Sigma_rr), with nothing written but the band sums:
+//   H(r,R') = G(r,R') W~(r,R')                        (CUDA cores, FP32)
+//   V_n(r)  = sum_{R' in tile} H(r,R') psi_n(R')      (tcgen05, 3 fp16 split products)
+//   Sigma_unocc_nn += coef Re(conj(psi_n(r)) V_n^unocc(r)),  Sigma_occ_nn -= ... V_n^occ
+// Once the tile's G is complete the pipeline stages are free: the epilogue
+// writes H row by row (its own power-of-two scale per row and column half) as
+// split fp16 in the 64-byte-swizzled K-major layout TMA would produce, the
+// producer loads the tile's psi_n operand behind it, and the MMA warp
+// accumulates V for each half of the tile's columns in the free half of
+// tensor memory; unoccupied first, then occupied in the same shared memory.
 template <int MODE, uint32_t FMT>
 __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_constant__ CUtensorMap mA_hi,
                                                               const __grid_constant__ CUtensorMap mA_lo,
                                                               const __grid_constant__ CUtensorMap mB_hi,
-                                                              const __grid_constant__ CUtensorMap mB_lo, Params p) {
+                                                              const __grid_constant__ CUtensorMap mB_lo,
+                                                              const __grid_constant__ CUtensorMap mP_hi,
+                                                              const __grid_constant__ CUtensorMap mP_lo, Params p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float2* epi = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);     // [8 warps][32 rows][16]
@@ -99,6 +124,14 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
   uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // MODE 2
+  uint64_t* hready = done + 2;           // [2] H operand of column half h written (4 warps)
+  uint64_t* hfree = hready + 2;          // [2] unoccupied MMAs of half h done: its H may be overwritten
+  uint64_t* vready = hfree + 2;          // [2] every V MMA of half h done
+  uint64_t* psi_full = vready + 2;       // psi_n operand of the tile landed
+  uint64_t* redbar = psi_full + 1;       // the epilogue warps' band sums are in shared memory
+  uint64_t* done2 = redbar + 1;          // every MMA of the self-energy phase done
+  double* red = reinterpret_cast<double*>(epi);   // [2][32] band sums of the CTA (MODE 2 only)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM;
@@ -117,6 +150,17 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
       mbar_init(&tempty[b], EPI_WARPS);
     }
     mbar_init(done, 1);
+    if (MODE == 2) {
+      for (int b = 0; b < 2; ++b) {
+        mbar_init(&hready[b], 4);
+        mbar_init(&hfree[b], 1);
+        mbar_init(&vready[b], 1);
+      }
+      mbar_init(psi_full, 1);
+      mbar_init(redbar, EPI_WARPS);
+      mbar_init(done2, 1);
+      for (int i = 0; i < 64; ++i) red[i] = 0.0;
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -129,6 +173,13 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // MODE 2 operands in the freed pipeline stages: H hi [0, 64 KB), H lo [64, 128 KB) as eight
+  // 32-wide K chunks of 128 rows; psi_n hi and lo from 128 KB, chunks of np rows.
+  uint8_t* const h_hi = smem;
+  uint8_t* const h_lo = smem + 8 * A_BYTES;
+  uint8_t* const p_hi = smem + 16 * A_BYTES;
+  const int p_chunk = MODE == 2 ? p.np * BK * 2 : 0;
+  uint8_t* const p_lo = p_hi + 8 * p_chunk;
 
   auto timed_out = [&](int where) {
     *abort_flag = 1;
@@ -166,6 +217,18 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
       // let our own copies land before the CTA exits
       for (int it = issued - STAGES < 0 ? 0 : issued - STAGES; it < issued; ++it)
         mbar_wait(&full[it % STAGES], (it / STAGES) & 1);
+    } else if constexpr (MODE == 2) {
+      // the tile's psi_n operand, once every MMA of the G formation has read its stages
+      if (wait_or_abort(done, 0)) {
+        mbar_expect_tx(psi_full, (uint32_t)(16 * p_chunk));
+        for (int cc = 0; cc < 8; ++cc) {
+          tma_load_3d(p_hi + cc * p_chunk, &mP_hi, psi_full, 2 * n0 + cc * BK, 0, 0);
+          tma_load_3d(p_lo + cc * p_chunk, &mP_lo, psi_full, 2 * n0 + cc * BK, 0, 0);
+        }
+        mbar_wait(psi_full, 0);    // our copies land before the CTA can exit
+      } else if (!*abort_flag) {
+        timed_out(6);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
@@ -208,6 +271,40 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
     }
     umma_commit(done);     // arrives once every MMA issued above has completed
     if (!mbar_wait(done, 0)) timed_out(5);
+    if constexpr (MODE == 2) {
+      // V accumulators [occ][half] of np columns each in the tensor-memory half the
+      // last G_unocc block used (drained before the epilogue signals hready)
+      const uint32_t vbase = tmem + (uint32_t)((1 - (n_un_blocks & 1)) * 256);
+      const uint32_t idesc2 = make_idesc(FMT, p.np, BM);
+      bool go = ok && wait_or_abort(psi_full, 0);
+      if (!go && !*abort_flag) timed_out(7);
+      for (int o = 0; o < 2 && go; ++o) {
+        for (int h = 0; h < 2 && go; ++h) {
+          if (!wait_or_abort(&hready[h], (uint32_t)o)) {
+            if (!*abort_flag) timed_out(8);
+            go = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = vbase + (uint32_t)((2 * o + h) * p.np);
+#pragma unroll 1
+          for (int cc = 4 * h; cc < 4 * h + 4; ++cc) {
+            const uint64_t ah = sw64_desc(h_hi + cc * A_BYTES), al = sw64_desc(h_lo + cc * A_BYTES);
+            const uint64_t bh = sw64_desc(p_hi + cc * p_chunk), bl = sw64_desc(p_lo + cc * p_chunk);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t off = (uint64_t)(kk * 32) >> 4;
+              umma(d, ah + off, bh + off, idesc2, (cc > 4 * h || kk > 0) ? 1u : 0u);
+              umma(d, ah + off, bl + off, idesc2, 1u);
+              umma(d, al + off, bh + off, idesc2, 1u);
+            }
+          }
+          umma_commit(o == 0 ? &hfree[h] : &vready[h]);
+        }
+      }
+      umma_commit(done2);
+      if (!mbar_wait(done2, 0)) timed_out(9);
+    }
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
     const int ew = warp - 2;
@@ -254,53 +351,200 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
       const int r0 = m0 + q * 32;                   // first output row of this warp
       const float sc = ldexpf(1.0f, -2 * (*p.dexp));
       const float ao = p.alpha_occ * sc, au = p.alpha_un * sc;
-      float2* stg = epi + ew * 32 * EPI_COLS;
+      if constexpr (MODE == 2) {
+        // ---------------------------------------------- self-energy contraction of the tile
+        const int row = q * 32 + lane;               // tensor-memory lane = tile row
+        const int gm = m0 + row;
+        const bool rvalid = gm < p.m_rows;
+        const float2* wrow = p.wrr + (long)(rvalid ? gm : 0) * p.ldw;
+        const int c0 = n0 + h * 64;                   // first complex column of this warp's half
+        const bool vec = (p.ldw % 2 == 0) && ((reinterpret_cast<uintptr_t>(p.wrr) & 15) == 0);
+        // H = g tot o W~ in place; returns the power of two that puts the row's max below 2^15
+        auto times_w = [&](float g) -> int {
+          float m = 0.f;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const int nc0 = n0 + h * 64 + cc * 16;
+          for (int c = 0; c < 64; c += 2) {
+            const int gn = c0 + c;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rvalid) {
+              if (vec && gn + 1 < p.n_cols) {
+                w = __ldg(reinterpret_cast<const float4*>(wrow + gn));
+              } else {
+                if (gn < p.n_cols) {
+                  const float2 a = wrow[gn];
+                  w.x = a.x;
+                  w.y = a.y;
+                }
+                if (gn + 1 < p.n_cols) {
+                  const float2 b = wrow[gn + 1];
+                  w.z = b.x;
+                  w.w = b.y;
+                }
+              }
+            }
+            const float ar = tot[2 * c] * g, ai = tot[2 * c + 1] * g;
+            const float br = tot[2 * c + 2] * g, bi = tot[2 * c + 3] * g;
+            tot[2 * c] = ar * w.x - ai * w.y;
+            tot[2 * c + 1] = ar * w.y + ai * w.x;
+            tot[2 * c + 2] = br * w.z - bi * w.w;
+            tot[2 * c + 3] = br * w.w + bi * w.z;
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(tot[2 * c]), fabsf(tot[2 * c + 1])),
+                               fmaxf(fabsf(tot[2 * c + 2]), fabsf(tot[2 * c + 3]))));
+          }
+          int ex = 0;
+          if (m > 0.f) frexpf(m, &ex);
+          return m > 0.f ? 14 - ex : 0;
+        };
+        // this row of H, scaled by 2^sh and split in two 16-bit parts, into K chunks
+        // 4h..4h+3: row `row` of a chunk is 64 bytes at (row/8)*512 + (row%8)*64, its
+        // 16-byte segment s stored at s ^ ((row/2) % 4) (the 64-byte swizzle of TMA)
+        auto store_h = [&](int sh) {
+          const float s = ldexpf(1.0f, sh);
 #pragma unroll
-        for (int pass = 0; pass < (MODE == 0 ? 1 : 2); ++pass) {
-          // row `lane` of the chunk to shared memory (rotated), then 128-byte row segments out
+          for (int j = 0; j < 4; ++j) {
+            const int base = (4 * h + j) * A_BYTES + (row >> 3) * 512 + (row & 7) * 64;
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            uint32_t ro[16];
-            const bool need_occ = MODE == 0 || pass == 0;
-            if (need_occ && have_occ) {
-              tmem_ld16(tmem + lane_addr + (uint32_t)(bo * 256 + h * 128 + 32 * cc + 16 * u), ro);
+            for (int sg = 0; sg < 4; ++sg) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const int c = 16 * j + 4 * sg + t;
+                uint16_t h0, l0, h1, l1;
+                split<FMT>(tot[2 * c] * s, h0, l0);
+                split<FMT>(tot[2 * c + 1] * s, h1, l1);
+                hw[t] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                lw[t] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+              }
+              const int off = base + ((sg ^ ((row >> 1) & 3)) << 4);
+              *reinterpret_cast<uint4*>(h_hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(h_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
+          __syncwarp();
+        };
+        const int shu = times_w(au);
+        store_h(shu);
+        if (lane == 0) mbar_arrive(&hready[h]);
+        // G_occ of this row and half from tensor memory
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          uint32_t x[16];
+          tmem_ld16(tmem + lane_addr + (uint32_t)(bo * 256 + h * 128 + 16 * u), x);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) tot[16 * u + i] = __uint_as_float(x[i]);
+        }
+        const int sho = times_w(ao);
+        bool fine = wait_or_abort(&hfree[h], 0);     // the unoccupied MMAs have read this half
+        if (__all_sync(0xffffffffu, fine)) {
+          tc_fence_after();
+          store_h(sho);
+          if (lane == 0) mbar_arrive(&hready[h]);
+          fine = wait_or_abort(&vready[h], 0);
+        }
+        if (__all_sync(0xffffffffu, fine)) {
+          tc_fence_after();
+          const uint32_t vb = tmem + lane_addr + (uint32_t)((1 - bo) * 256);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (16 * u < p.np) {                      // np is the same for the whole warp
+              uint32_t x[16], y[16];
+              tmem_ld16(vb + (uint32_t)(h * p.np + 16 * u), x);
+              tmem_ld16(vb + (uint32_t)((2 + h) * p.np + 16 * u), y);
               tmem_wait_ld();
-            } else {
 #pragma unroll
-              for (int i = 0; i < 16; ++i) ro[i] = 0u;
+              for (int i = 0; i < 16; ++i) {
+                tot[16 * u + i] = __uint_as_float(x[i]);
+                tot[64 + 16 * u + i] = __uint_as_float(y[i]);
+              }
             }
+          }
+          const int e = *p.dexp;
+          const float fu = ldexpf(1.0f, -(shu + e)), fo = ldexpf(1.0f, -(sho + e));
+          const long grow = (long)p.r0 + gm;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float gor = __uint_as_float(ro[2 * j]) * ao, goi = __uint_as_float(ro[2 * j + 1]) * ao;
-              const float gur = tot[32 * cc + 16 * u + 2 * j] * au, gui = tot[32 * cc + 16 * u + 2 * j + 1] * au;
-              float2 v;
-              if (MODE == 0) v = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
-              else v = pass == 0 ? make_float2(gor, goi) : make_float2(gur, gui);
-              stg[lane * EPI_COLS + ((u * 8 + j + lane) & (EPI_COLS - 1))] = v;
+          for (int n = 0; n < 32; ++n) {
+            if (n < p.n_n) {
+              float2 ps = make_float2(0.f, 0.f);
+              if (rvalid) ps = __ldg(p.psi + (long)p.bands[n] * p.ldpsi + grow);
+              float su = (ps.x * tot[2 * n] + ps.y * tot[2 * n + 1]) * fu;          // Re(conj(psi_n) V_n)
+              float so = (ps.x * tot[64 + 2 * n] + ps.y * tot[64 + 2 * n + 1]) * fo;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                su += __shfl_xor_sync(0xffffffffu, su, o);
+                so += __shfl_xor_sync(0xffffffffu, so, o);
+              }
+              if (lane == 0) {
+                atomicAdd(&red[n], (double)su);
+                atomicAdd(&red[32 + n], (double)so);
+              }
             }
           }
           __syncwarp();
-          float2* outp = (MODE == 0 || pass == 0) ? p.out0 : p.out1;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int idx = i * 32 + lane;
-            const int rr = idx >> 3, pc = (idx & 7) * 2;
-            const int gm = r0 + rr, gn = nc0 + pc;
-            if (gm >= p.m_rows || gn >= p.n_cols) continue;
-            const float2 v0 = stg[rr * EPI_COLS + ((pc + rr) & (EPI_COLS - 1))];
-            const float2 v1 = stg[rr * EPI_COLS + ((pc + 1 + rr) & (EPI_COLS - 1))];
-            float2* o = outp + (long)gm * p.ldo + gn;
-            if (gn + 1 < p.n_cols && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
-              *reinterpret_cast<float4*>(o) = make_float4(v0.x, v0.y, v1.x, v1.y);
-            } else {
-              o[0] = v0;
-              if (gn + 1 < p.n_cols) o[1] = v1;
-            }
+          if (lane == 0) mbar_arrive(redbar);
+        } else if (lane == 0 && !*abort_flag) {
+          timed_out(10);
+        }
+        // one warp adds the CTA's band sums into Sigma_unocc_nn(tau_j), Sigma_occ_nn(-tau_j)
+        if (ew == 0) {
+          const bool got = wait_or_abort(redbar, 0);
+          if (got && lane < p.n_n) {
+            atomicAdd(&p.acc_u[(long)lane * p.acc_stride], p.coef * red[lane]);
+            atomicAdd(&p.acc_o[(long)lane * p.acc_stride], -p.coef * red[32 + lane]);
+          } else if (!got && lane == 0 && !*abort_flag) {
+            timed_out(11);
           }
-          __syncwarp();
+        }
+      } else {
+        float2* stg = epi + ew * 32 * EPI_COLS;
+  #pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int nc0 = n0 + h * 64 + cc * 16;
+  #pragma unroll
+          for (int pass = 0; pass < (MODE == 0 ? 1 : 2); ++pass) {
+            // row `lane` of the chunk to shared memory (rotated), then 128-byte row segments out
+  #pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              uint32_t ro[16];
+              const bool need_occ = MODE == 0 || pass == 0;
+              if (need_occ && have_occ) {
+                tmem_ld16(tmem + lane_addr + (uint32_t)(bo * 256 + h * 128 + 32 * cc + 16 * u), ro);
+                tmem_wait_ld();
+              } else {
+  #pragma unroll
+                for (int i = 0; i < 16; ++i) ro[i] = 0u;
+              }
+  #pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float gor = __uint_as_float(ro[2 * j]) * ao, goi = __uint_as_float(ro[2 * j + 1]) * ao;
+                const float gur = tot[32 * cc + 16 * u + 2 * j] * au, gui = tot[32 * cc + 16 * u + 2 * j + 1] * au;
+                float2 v;
+                if (MODE == 0) v = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
+                else v = pass == 0 ? make_float2(gor, goi) : make_float2(gur, gui);
+                stg[lane * EPI_COLS + ((u * 8 + j + lane) & (EPI_COLS - 1))] = v;
+              }
+            }
+            __syncwarp();
+            float2* outp = (MODE == 0 || pass == 0) ? p.out0 : p.out1;
+  #pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int idx = i * 32 + lane;
+              const int rr = idx >> 3, pc = (idx & 7) * 2;
+              const int gm = r0 + rr, gn = nc0 + pc;
+              if (gm >= p.m_rows || gn >= p.n_cols) continue;
+              const float2 v0 = stg[rr * EPI_COLS + ((pc + rr) & (EPI_COLS - 1))];
+              const float2 v1 = stg[rr * EPI_COLS + ((pc + 1 + rr) & (EPI_COLS - 1))];
+              float2* o = outp + (long)gm * p.ldo + gn;
+              if (gn + 1 < p.n_cols && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+                *reinterpret_cast<float4*>(o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+              } else {
+                o[0] = v0;
+                if (gn + 1 < p.n_cols) o[1] = v1;
+              }
+            }
+            __syncwarp();
+          }
         }
       }
     }
@@ -400,6 +644,36 @@ __global__ void __launch_bounds__(256) prep_kernel(const float2* __restrict__ ps
   }
 }
 
+// The psi_n operand of the self-energy contraction (MODE 2): B rows 2n and 2n+1
+// hold (br, -bi) and (bi, br) of b = psi_{bands[n]}(R') * 2^e along real K =
+// 2R', 2R'+1, so that D[r][2n + c] = (Re, Im) sum_R' H(r,R') psi_n(R').  Rows of
+// band slots n >= n_n (up to np/2) are zero.  One thread per (R', n).
+template <uint32_t FMT>
+__global__ void __launch_bounds__(256) prep_psin_kernel(const float2* __restrict__ psi, int nr,
+                                                        const int* __restrict__ bands, int n_n, int kp,
+                                                        const int* __restrict__ dexp, uint16_t* __restrict__ hi,
+                                                        uint16_t* __restrict__ lo) {
+  const int rp = blockIdx.x * 256 + threadIdx.x;
+  const int n = blockIdx.y;
+  if (2 * rp >= kp) return;
+  float2 v = make_float2(0.f, 0.f);
+  if (n < n_n && rp < nr) {
+    v = psi[(long)bands[n] * nr + rp];
+    const float sc = ldexpf(1.0f, *dexp);
+    v.x *= sc;
+    v.y *= sc;
+  }
+  uint16_t h0, l0, h1, l1, h2, l2;
+  split<FMT>(v.x, h0, l0);
+  split<FMT>(-v.y, h1, l1);
+  split<FMT>(v.y, h2, l2);
+  const long o0 = (long)(2 * n) * kp + 2 * rp, o1 = o0 + kp;
+  reinterpret_cast<uint32_t*>(hi + o0)[0] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+  reinterpret_cast<uint32_t*>(lo + o0)[0] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+  reinterpret_cast<uint32_t*>(hi + o1)[0] = (uint32_t)h2 | ((uint32_t)h0 << 16);
+  reinterpret_cast<uint32_t*>(lo + o1)[0] = (uint32_t)l2 | ((uint32_t)l0 << 16);
+}
+
 // ---------------------------------------------------------------------- host side
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -476,7 +750,11 @@ static Layout layout(int n_b, int n_occ) {
   return L;
 }
 
-static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp) {
+// MMA N of the self-energy contraction for n_sig bands, and the padded real K of its operand
+static int sig_np(int n_sig) { return (2 * n_sig + 15) / 16 * 16; }
+static int sig_kp(const GridInfo& g) { return (2 * g.nr + BK - 1) / BK * BK; }
+
+static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp, int n_sig = 0) {
   const Layout L = layout(n_b, n_occ);
   Carver probe(nullptr);
   probe.take<unsigned int>(64);
@@ -485,6 +763,10 @@ static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, b
   probe.take<uint16_t>((size_t)2 * g.nr * L.kpad);
   probe.take<uint16_t>((size_t)n_rows * L.kpad);
   probe.take<uint16_t>((size_t)n_rows * L.kpad);
+  if (n_sig > 0) {
+    probe.take<uint16_t>((size_t)sig_np(n_sig) * sig_kp(g));
+    probe.take<uint16_t>((size_t)sig_np(n_sig) * sig_kp(g));
+  }
   if (with_tmp) probe.take<float2>((size_t)n_rows * g.nr);
   return Carver::round(probe.off);
 }
@@ -496,7 +778,8 @@ static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, b
 // same psi.
 static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
                      int r0, int n_rows, gw_prec prec, int mode, void* out0, void* out1, void* scratch, bool prep_b,
-                     cudaStream_t st, const float* sk_dev = nullptr, int* status_dev = nullptr) {
+                     cudaStream_t st, const float* sk_dev = nullptr, int* status_dev = nullptr,
+                     const TcSigma* sig = nullptr) {
   const uint32_t fmt = prec == GW_BF16X3 ? 1u : 0u;
   const Layout L = layout(n_b, n_occ);
   gw_status rc;
@@ -511,6 +794,9 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
   uint16_t* blo = cv.take<uint16_t>((size_t)2 * g.nr * L.kpad);
   uint16_t* ahi = cv.take<uint16_t>((size_t)n_rows * L.kpad);
   uint16_t* alo = cv.take<uint16_t>((size_t)n_rows * L.kpad);
+  const int np = mode == 2 ? sig_np(sig->n_n) : 0, kps = sig_kp(g);
+  uint16_t* phi = mode == 2 ? cv.take<uint16_t>((size_t)np * kps) : nullptr;
+  uint16_t* plo = mode == 2 ? cv.take<uint16_t>((size_t)np * kps) : nullptr;
   float2* tmp = need_tmp ? cv.take<float2>((size_t)n_rows * g.nr) : nullptr;
   if (mode == 1) {
     if (!out0) out0 = tmp;
@@ -543,6 +829,14 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
       prep_kernel<true, 1><<<gbB, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, 0, g.nr, sk, dexp,
                                                 L.k_occ_pad, L.k_un_x, L.kpad, bhi, blo);
     if ((rc = launch_check(ctx, "prep_kernel(B)"))) return rc;
+    if (mode == 2) {
+      const dim3 gp((kps / 2 + 255) / 256, np / 2);
+      if (fmt == 0)
+        prep_psin_kernel<0><<<gp, 256, 0, st>>>((const float2*)psi, g.nr, sig->bands, sig->n_n, kps, dexp, phi, plo);
+      else
+        prep_psin_kernel<1><<<gp, 256, 0, st>>>((const float2*)psi, g.nr, sig->bands, sig->n_n, kps, dexp, phi, plo);
+      if ((rc = launch_check(ctx, "prep_psin_kernel"))) return rc;
+    }
   } else {
     if ((rc = cuda_check(ctx, cudaMemsetAsync(status, 0, 2 * sizeof(int), st), "memset"))) return rc;
   }
@@ -554,11 +848,18 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
     prep_kernel<false, 1><<<gbA, tb, 0, st>>>((const float2*)psi, n_b, n_occ, g.nr, r0, n_rows, sk, dexp,
                                                L.k_occ_pad, L.k_un_x, L.kpad, ahi, alo);
   if ((rc = launch_check(ctx, "prep_kernel(A)"))) return rc;
-  CUtensorMap mah, mal, mbh, mbl;
+  CUtensorMap mah, mal, mbh, mbl, mph, mpl;
   if ((rc = tc_make_map3(ctx, &mah, ahi, L.kpad, n_rows, 1, BM, fmt, BK))) return rc;
   if ((rc = tc_make_map3(ctx, &mal, alo, L.kpad, n_rows, 1, BM, fmt, BK))) return rc;
   if ((rc = tc_make_map3(ctx, &mbh, bhi, L.kpad, 2L * g.nr, 1, 2 * BNC, fmt, BK))) return rc;
   if ((rc = tc_make_map3(ctx, &mbl, blo, L.kpad, 2L * g.nr, 1, 2 * BNC, fmt, BK))) return rc;
+  if (mode == 2) {
+    if ((rc = tc_make_map3(ctx, &mph, phi, kps, np, 1, np, fmt, BK))) return rc;
+    if ((rc = tc_make_map3(ctx, &mpl, plo, kps, np, 1, np, fmt, BK))) return rc;
+  } else {
+    mph = mah;                                   // unused outside the self-energy mode
+    mpl = mal;
+  }
   Params P;
   P.m_rows = n_rows;
   P.n_cols = g.nr;
@@ -572,17 +873,40 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
   P.alpha_un = (float)gs.amax_unocc;
   P.dexp = dexp;
   P.status = status;
+  P.wrr = nullptr;
+  P.ldw = 0;
+  P.psi = static_cast<const float2*>(psi);
+  P.ldpsi = g.nr;
+  P.bands = nullptr;
+  P.n_n = 0;
+  P.np = np;
+  P.r0 = r0;
+  P.coef = 0.0;
+  P.acc_u = P.acc_o = nullptr;
+  P.acc_stride = 0;
+  if (mode == 2) {
+    P.wrr = sig->wrr;
+    P.ldw = sig->ldw;
+    P.bands = sig->bands;
+    P.n_n = sig->n_n;
+    P.coef = sig->coef;
+    P.acc_u = sig->acc_u;
+    P.acc_o = sig->acc_o;
+    P.acc_stride = sig->acc_stride;
+  }
   const dim3 grid((g.nr + BNC - 1) / BNC, (n_rows + BM - 1) / BM);
   auto go = [&](auto kernel) -> gw_status {
     gw_status r = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                              "cudaFuncSetAttribute");
     if (r) return r;
-    KTimer kt(ctx, KF_GREEN_TC, 8.0 * n_rows * (double)g.nr * n_b, st);
-    kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mah, mal, mbh, mbl, P);
+    const double work = 8.0 * n_rows * (double)g.nr * n_b + (mode == 2 ? 16.0 * n_rows * (double)g.nr * P.n_n : 0.0);
+    KTimer kt(ctx, KF_GREEN_TC, work, st);
+    kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mah, mal, mbh, mbl, mph, mpl, P);
     return launch_check(ctx, "green_tc_kernel");
   };
   if (mode == 0) rc = fmt == 0 ? go(green_tc_kernel<0, 0>) : go(green_tc_kernel<0, 1>);
-  else rc = fmt == 0 ? go(green_tc_kernel<1, 0>) : go(green_tc_kernel<1, 1>);
+  else if (mode == 1) rc = fmt == 0 ? go(green_tc_kernel<1, 0>) : go(green_tc_kernel<1, 1>);
+  else rc = fmt == 0 ? go(green_tc_kernel<2, 0>) : go(green_tc_kernel<2, 1>);
   return rc;
 }
 
@@ -599,14 +923,22 @@ static gw_status check_status(gw_ctx* ctx, void* scratch, cudaStream_t st) {
 
 }  // namespace tc
 
-size_t tc_scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp) {
-  return tc::scratch_bytes(g, n_b, n_occ, n_rows, with_tmp);
+size_t tc_scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp, int n_sig) {
+  return tc::scratch_bytes(g, n_b, n_occ, n_rows, with_tmp, n_sig);
+}
+
+gw_status tc_sigma_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
+                        int r0, int n_rows, gw_prec prec, const TcSigma& sig, void* scratch, bool prep_b,
+                        cudaStream_t st) {
+  if (sig.n_n < 1 || sig.n_n > 32) return fail(ctx, GW_ERR_SHAPE, "fused self-energy contraction takes 1..32 bands");
+  return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 2, nullptr, nullptr, scratch, prep_b, st, sig.sk,
+                 nullptr, &sig);
 }
 
 gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
                         int r0, int n_rows, gw_prec prec, void* g_occ, void* g_unocc, void* scratch, bool prep_b,
-                        cudaStream_t st) {
-  return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 1, g_occ, g_unocc, scratch, prep_b, st);
+                        cudaStream_t st, const float* sk_dev) {
+  return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 1, g_occ, g_unocc, scratch, prep_b, st, sk_dev);
 }
 
 gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,

@@ -9,19 +9,41 @@ namespace gw {
 
 // Scratch the two calls below need for n_rows rows (with_tmp: room for an
 // output the caller did not supply).
-size_t tc_scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp);
+size_t tc_scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, bool with_tmp, int n_sig = 0);
 // G_occ / G_unocc rows as 3 fp16 (or bf16) split products on tcgen05 with FP32
 // accumulation in tensor memory.  Either output may be NULL.  prep_b = false
 // reuses the psi-only operand an earlier call left in the same scratch.
 gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi,
                         const GreenScales& gs, int r0, int n_rows, gw_prec prec, void* g_occ, void* g_unocc,
-                        void* scratch, bool prep_b, cudaStream_t st);
+                        void* scratch, bool prep_b, cudaStream_t st, const float* sk_dev = nullptr);
 // chi rows = -2 G_occ o conj(G_unocc) with both tiles accumulated in tensor memory.
 // sk_dev: the per-band factors gs.s already on the device as FP32 (then the
 // call copies nothing from the host).
 gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
                       int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st,
                       const float* sk_dev = nullptr, int* status_dev = nullptr);
+// The self-energy contraction fused into the G formation of rows r0 .. r0+n_rows-1
+// (first term of Eq. Sigma_occ_reduce): for every 128 x 128 tile, H = G o W~ on
+// CUDA cores, V_n = H psi_n on tcgen05, and
+//   acc_u[n * acc_stride] += coef sum_r Re(conj(psi_n(r)) V_n^unocc(r)),  acc_o likewise with -coef.
+// G never leaves the chip.  wrr: W~(r,R') rows of the block [n_rows][ldw] (FP32
+// complex); bands: device [n_n], 1 <= n_n <= 32.  The scratch must come from
+// tc_scratch_bytes(..., n_sig >= n_n); prep_b as for tc_green_rows (also
+// prepares the psi_n operand).
+struct TcSigma {
+  const float2* wrr;
+  long ldw;
+  const int* bands;
+  int n_n;
+  double coef;
+  double* acc_u;
+  double* acc_o;
+  int acc_stride;
+  const float* sk = nullptr;   // the per-band factors gs.s on the device as FP32 (else copied per call)
+};
+gw_status tc_sigma_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
+                        int r0, int n_rows, gw_prec prec, const TcSigma& sig, void* scratch, bool prep_b,
+                        cudaStream_t st);
 // As tc_check for a status word the caller owns (status_dev of tc_chi_rows).
 gw_status tc_check_status(gw_ctx* ctx, const int* status_dev, cudaStream_t st);
 // Synchronises and reports a time-out of the tensor-core pipeline waits
@@ -61,5 +83,13 @@ struct TcGemm {
 };
 size_t tc_gemm_scratch(int M, int N, int K, int batch);
 gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cudaStream_t st);
+
+// C = A B for complex FP64 A [M][K] (lda), B [K][N] (ldb), C [M][N] (ldc, written)
+// with FP64-class accuracy from exact fp16 slice products on tcgen05 (slice pairs
+// a + b <= levels, 6 bits per slice; error below 2^(-6(levels+1)) of the row and
+// column maxima).  status: device words set on a pipeline time-out.
+size_t tc_zgemm_sliced_scratch(int M, int N, int K, int levels);
+gw_status tc_zgemm_sliced(gw_ctx* ctx, int M, int N, int K, const double2* A, long lda, const double2* B, long ldb,
+                          double2* C, long ldc, int levels, int* status, void* scratch, cudaStream_t st);
 
 }  // namespace gw

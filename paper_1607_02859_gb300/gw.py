@@ -28,7 +28,8 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_chi0_rtau_fused", "gw_rr_to_GG_fft", "gw_tau_to_omega", "gw_screen_W", "gw_sigma_diag",
            "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh", "gw_sigma_diag_kmesh",
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
-           "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau", "gw_mp2_grids"]
+           "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau", "gw_mp2_grids",
+           "gw_zgemm_sliced"]
 
 
 class GwError(RuntimeError):
@@ -87,6 +88,7 @@ _SIGS = {
     "gw_qp_energies": (_I, [_P, _I, _I, _DP, _DP, _DP, _D, _DP, _I, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
     "gw_invert_transform": (_I, [_I, _DP, _DP]),
     "gw_mp2_grids": (_I, [_I, _D, _D, _DP, _DP, _DP, _DP, _DP]),
+    "gw_zgemm_sliced": (_I, [_P, _I, _I, _I, _P, ct.c_long, _P, ct.c_long, _P, ct.c_long, _I, _P]),
     "gw_sigma_to_tau": (_I, [_P, _I, _I, _I, _DP, _DP, _DP, _DP, _P]),
 }
 
@@ -313,6 +315,21 @@ def rr_to_GG_fft_noalloc(grid, direction, stage, fft_index, prec, r0, n_rows, in
     idx = _i32(fft_index)
     _check(lib().gw_rr_to_GG_fft_noalloc(ct.byref(grid), int(direction), int(stage), len(idx), _ip(idx), p, int(r0),
                                          int(n_rows), _dev(inp, "in", p), _dev(out, "out", p), _stream()))
+
+
+def zgemm_sliced(ctx, A, B, C, levels=5):
+    """C = A B for complex128 device matrices, FP64-class accuracy on the tensor cores."""
+    import torch
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K or tuple(C.shape) != (M, N):
+        raise ValueError("shapes do not match")
+    for t in (A, B, C):
+        if t.dtype != torch.complex128 or not t.is_cuda or t.stride(1) != 1:
+            raise ValueError("complex128 device matrices with unit column stride needed")
+    _check(lib().gw_zgemm_sliced(ctx.handle, int(M), int(N), int(K), ct.c_void_p(A.data_ptr()), int(A.stride(0)),
+                                 ct.c_void_p(B.data_ptr()), int(B.stride(0)), ct.c_void_p(C.data_ptr()),
+                                 int(C.stride(0)), int(levels), _stream()), ctx)
 
 
 def tau_to_omega(ctx, kind, M, inp, out, prec):

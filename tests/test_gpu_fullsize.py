@@ -26,8 +26,12 @@ from paper_1607_02859_gb300 import gw, inputs
 pytestmark = pytest.mark.gpu
 MEV = 3.674932e-5
 torch = pytest.importorskip("torch")
-CHI_TOL = 1e-6                                   # relative Frobenius, chi0(i omega) and chi0(i tau)
-CHI_TAU_TOL = {"fp32": 1e-6, "f16x3": 2e-6}
+# relative Frobenius error of chi0(i omega) and chi0(i tau): the FP32 path meets the 1e-6 bar; the
+# fp16 x 3 path adds the truncating FP32 accumulation of the tensor cores, about (3 products x 8 K16
+# steps per 128-wide accumulation block) x 2^-24 = 1.4e-6 relative, and 2^-22 from the dropped lo x lo
+# products: 3e-6 at any number of bands (blocks are summed in round-to-nearest FP32)
+CHI_TOL = {"fp32": 1e-6, "f16x3": 3e-6}
+CHI_TAU_TOL = {"fp32": 1e-6, "f16x3": 3e-6}
 W_TOL = {"fp32": 2e-5, "f16x3": 5e-5}            # relative Frobenius of W~ against the FP64 solve
 WORKERS = os.cpu_count()
 
@@ -134,8 +138,8 @@ def test_si8_chi0_rows(ctx, si8, si8_rows, prec):
     rows, ref_tau = si8_rows
     err_tau, err, herm = chi_rows_check(ctx, p, idx, mats, prec, rows, ref_tau)
     assert err_tau < CHI_TAU_TOL[prec], err_tau
-    assert err < CHI_TOL, err
-    assert herm < CHI_TOL, herm
+    assert err < CHI_TOL[prec], err
+    assert herm < CHI_TOL[prec], herm
 
 
 @pytest.fixture(scope="module")
@@ -155,6 +159,16 @@ def test_si8_screen_vs_oracle(ctx, si8, si8_screen, prec):
     errs, res = screen_check(ctx, gw.make_grid(p.n, p.lattice), gv, chi, w_ref, prec)
     print("si8 screening %s: W~ relative error %s, residual probe %s" % (prec, errs, res))
     assert max(errs) < W_TOL[prec], errs
+
+
+def test_si8_screen_refined(ctx, si8, si8_screen):
+    """One refinement step of the f16x3 solve at N_chi = 13824 (the residual
+    product as exact fp16 slice products on the tensor cores)."""
+    p, gv, idx, mats = si8
+    chi, w_ref = si8_screen
+    errs, res = screen_check(ctx, gw.make_grid(p.n, p.lattice), gv, chi, w_ref, "f16x3", refine=1)
+    print("si8 screening f16x3 + 1 refinement step: W~ relative error %s, residual probe %s" % (errs, res))
+    assert max(errs) < 1e-6, errs
 
 
 @pytest.mark.parametrize("prec", ["fp32", "f16x3"])

@@ -47,8 +47,8 @@ def test_si64_chi0_rows(ctx, si64, si64_rows, prec):
     rows, ref_tau = si64_rows
     err_tau, err, herm = chi_rows_check(ctx, p, idx, mats, prec, rows, ref_tau)
     assert err_tau < CHI_TAU_TOL[prec], err_tau
-    assert err < CHI_TOL, err
-    assert herm < CHI_TOL, herm
+    assert err < CHI_TOL[prec], err
+    assert herm < CHI_TOL[prec], herm
 
 
 @pytest.fixture(scope="module")
@@ -66,6 +66,16 @@ def test_si64_screen_vs_oracle(ctx, si64, si64_screen, prec):
     errs, res = screen_check(ctx, gw.make_grid(p.n, p.lattice), gv, chi, w_ref, prec)
     print("si64 screening %s: W~ relative error %s, residual probe %s" % (prec, errs, res))
     assert max(errs) < W_TOL[prec], errs
+
+
+def test_si64_screen_refined(ctx, si64, si64_screen):
+    """One refinement step of the f16x3 solve, as the benchmark times it: the
+    residual product on the tensor cores as exact fp16 slice products."""
+    p, gv, idx, mats = si64
+    chi, w_ref = si64_screen
+    errs, res = screen_check(ctx, gw.make_grid(p.n, p.lattice), gv, chi, w_ref, "f16x3", refine=1)
+    print("si64 screening f16x3 + 1 refinement step: W~ relative error %s, residual probe %s" % (errs, res))
+    assert max(errs) < 1e-6, errs
 
 
 def test_si64_sigma_sparse_w(ctx, si64):

@@ -72,3 +72,57 @@ def test_refine_argument_checks(ctx, toy):
     chi_d = torch.from_numpy(chi_ref[:1].astype(np.complex64)).to("cuda")
     with pytest.raises(gw.GwError):
         gw.screen_W(ctx, grid, s["gvecs"], "fp32", chi_d, chi_d.clone(), refine=9)
+
+
+def test_zgemm_sliced_exact_on_integers(ctx):
+    """Integer components below 64 are one exact slice each, so with every K block's
+    sum below 2^24 the tensor-core product must equal the exact integer product:
+    checks the exactness of the FP32 accumulation in tensor memory, the K blocks
+    (K = 2500 complex = 5000 real: two blocks), ragged tiles and the complex
+    mapping."""
+    rng = np.random.default_rng(5)
+    M, K, N = 300, 2500, 200
+    a = rng.integers(-50, 51, (M, K)) + 1j * rng.integers(-50, 51, (M, K))
+    b = rng.integers(-50, 51, (K, N)) + 1j * rng.integers(-50, 51, (K, N))
+    ar, ai = a.real.astype(np.int64), a.imag.astype(np.int64)
+    br, bi = b.real.astype(np.int64), b.imag.astype(np.int64)
+    ref = (ar @ br - ai @ bi) + 1j * (ar @ bi + ai @ br)          # exact in int64
+    A = torch.from_numpy(a).to("cuda")
+    B = torch.from_numpy(b).to("cuda")
+    C = torch.full((M, N), 7.0 + 0j, dtype=torch.complex128, device="cuda")
+    gw.zgemm_sliced(ctx, A, B, C, levels=1)
+    got = C.cpu().numpy()
+    assert np.array_equal(got, ref.astype(np.complex128))
+
+
+@pytest.mark.parametrize("levels", [3, 5])
+def test_zgemm_sliced_accuracy(ctx, levels):
+    """Gaussian matrices with rows and columns of magnitudes spread over four
+    decades, against numpy's FP64 product.  The slice pairs dropped (a + b >
+    levels, each below 2^(e_i + f_j - 6 (a+b) - 1)) and the slicing rest bound
+    each element's error by 4 (levels + 2) 2^(-6(levels+1)) K max|A_i.| max|B_.j|."""
+    rng = np.random.default_rng(6 + levels)
+    M, K, N = 520, 3000, 390
+    a = (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) * 10.0 ** rng.uniform(-2, 2, (M, 1))
+    b = (rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))) * 10.0 ** rng.uniform(-2, 2, (1, N))
+    ref = a @ b
+    C = torch.empty((M, N), dtype=torch.complex128, device="cuda")
+    gw.zgemm_sliced(ctx, torch.from_numpy(a).to("cuda"), torch.from_numpy(b).to("cuda"), C, levels=levels)
+    err = np.abs(C.cpu().numpy() - ref)
+    amax = np.max(np.maximum(np.abs(a.real), np.abs(a.imag)), axis=1)
+    bmax = np.max(np.maximum(np.abs(b.real), np.abs(b.imag)), axis=0)
+    scale = 4.0 * (levels + 2) * 2.0 ** (-6 * (levels + 1)) * K * np.outer(amax, bmax)
+    print("levels %d: max err / bound %.2e, relative Frobenius error %.2e"
+          % (levels, np.max(err / scale), np.linalg.norm(err) / np.linalg.norm(ref)))
+    assert np.max(err / scale) < 1.0
+    # a plain split GEMM with FP32 accumulation would be near 1e-6 here
+    assert np.linalg.norm(err) / np.linalg.norm(ref) < (1e-6 if levels == 3 else 1e-9)
+
+
+def test_zgemm_sliced_argument_checks(ctx):
+    A = torch.zeros((4, 4), dtype=torch.complex128, device="cuda")
+    with pytest.raises(gw.GwError) as e:
+        gw.zgemm_sliced(ctx, A, A, A.clone(), levels=0)
+    assert e.value.status == 1
+    with pytest.raises(ValueError):
+        gw.zgemm_sliced(ctx, A.to(torch.complex64), A, A.clone())
