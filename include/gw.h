@@ -456,6 +456,60 @@ gw_status gw_chi0_plan_status(gw_chi0_plan* plan, void* stream);
 /* Frees the plan's tables (synchronises the device). */
 gw_status gw_chi0_plan_destroy(gw_chi0_plan* plan);
 
+/* ---------------------------------------------------------------- batches
+ * Many uneven systems through the whole hot path in one CUDA-graph launch (the
+ * batched form of the serving layer; the paper has no counterpart).  Per
+ * system: chi0(i omega) (as gw_chi0_omega), W~(i omega) (gw_screen_W_refine
+ * with refine_iters), W~(i tau) (gw_tau_to_omega with Cinv) and the diagonal
+ * self-energy Sigma_nn(i omega) with its Thiele coefficients (gw_sigma_diag
+ * without real-axis points).  gw_batch_plan does all host work once
+ * (validation, tables, weights, uploads, the context arena grown to the
+ * largest need) and records the kernels of every system, in order, into one
+ * CUDA graph; gw_batch_launch replays it with no host work and no
+ * host-device copy; gw_batch_wait waits (bounded) and reads the results.
+ * The systems share the context's arena and run one after the other inside
+ * the graph.  A plan is invalidated if the context's arena is reallocated
+ * afterwards (a later call on the context that needs more scratch):
+ * gw_batch_launch then returns GW_ERR_ARG. */
+typedef struct gw_batch gw_batch;
+typedef struct gw_batch_system {
+  gw_grid grid;
+  int n_b, n_occ;
+  const double* eps_h;          /* host [n_b], ascending, mu in the gap          */
+  double mu;
+  int n;                        /* tau / omega points (<= 32)                   */
+  const double* tau_h;          /* host [n]                                     */
+  const double* omega_h;        /* host [n]                                     */
+  const double* C_h;            /* host [n][n] cosine transform (gw_fit_transform) */
+  const double* S_h;            /* host [n][n] sine transform                   */
+  const double* Cinv_h;         /* host [n][n] inverse cosine transform          */
+  int n_chi;
+  const int32_t* gvec_h;        /* host [n_chi][3] G set (gw_g_set)              */
+  const int32_t* fft_index_h;   /* host [n_chi]                                  */
+  int n_n;                      /* self-energy bands                            */
+  const int32_t* bands_h;       /* host [n_n]                                   */
+  int r_block;                  /* rows per r-block of the chi0 pass (e.g. from an autotuner); <= 0: default */
+  int refine_iters;             /* 0..8 refinement steps of the screening        */
+  const void* psi;              /* device [n_b][N_r], 16-byte aligned            */
+  void* chi_w;                  /* device [n][n_chi][n_chi] work: chi0(i omega), then W~(i omega) */
+  void* w_tau;                  /* device [n][n_chi][n_chi]: W~(i tau) (not overlapping chi_w) */
+} gw_batch_system;
+/* Host pointers are read during the call only; device pointers are recorded
+ * in the graph and must stay valid while the plan is used. */
+gw_status gw_batch_plan(gw_ctx* ctx, int n_sys, const gw_batch_system* systems, gw_prec prec, gw_batch** out);
+/* Replays the graph on `stream` (asynchronous). */
+gw_status gw_batch_launch(gw_batch* batch, void* stream);
+/* Waits at most timeout_ms (< 0: no limit) for the last launch; GW_ERR_TIMEOUT
+ * if it has not finished (the work continues; call again).  Then
+ * sigma_iw_h (host, may be NULL) receives every system's Sigma_nn(i omega)
+ * [n_n][n] complex, one system after the other, and status_h [n_sys] (may be
+ * NULL) each system's gw_status (GW_ERR_NUMERIC for a non-positive-definite
+ * eps~ or a vanishing Thiele denominator, GW_ERR_TIMEOUT for a tensor-core
+ * wait that gave up); the call returns the first failure. */
+gw_status gw_batch_wait(gw_batch* batch, int timeout_ms, double* sigma_iw_h, int* status_h);
+/* Frees the plan (synchronises its stream). */
+gw_status gw_batch_destroy(gw_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

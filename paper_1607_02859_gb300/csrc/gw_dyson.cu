@@ -727,6 +727,49 @@ size_t screen_scratch(int n_chi, int n_omega, gw_prec prec, int* bsz_out, int* n
   return probe.off;
 }
 
+// The screening of n_omega frequencies with v^1/2 already on the device (dvh)
+// and the arena carved by cv after it: device-side memsets and kernels only
+// when resid_h and first_bad are NULL (then a plan can capture it in a CUDA
+// graph).  Pivot and time-out flags are left in ctx->dflag (zeroed here first).
+// resid_h: the FP64 probe residuals (synchronous); first_bad: with several
+// batches of frequencies, the first frequency whose factorisation failed
+// (synchronises between batches).
+gw_status screen_launch(gw_ctx* ctx, int n_chi, int n_omega, gw_prec prec, int refine_iters, const double* dvh,
+                        const void* chi_w, void* w_w, Carver& cv, double* resid_h, int* first_bad, cudaStream_t s) {
+  gw_status st;
+  const size_t es = csize(prec);
+  const size_t nn = (size_t)n_chi * n_chi;
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  int bsz = 0, nbatch = 0;
+  screen_scratch(n_chi, n_omega, prec, &bsz, &nbatch, refine_iters > 0);
+  const size_t tcs_bytes = tc ? screen_tc_scratch(n_chi, bsz, refine_iters > 0) : 0;
+  void* E = cv.take<char>(bsz * nn * es);
+  void* M = cv.take<char>(bsz * nn * es);
+  double2* pr = cv.take<double2>(4 * (size_t)n_chi);
+  void* tcs = tc ? cv.take<char>(tcs_bytes) : nullptr;
+  double2* rws = refine_iters > 0 ? cv.take<double2>(4 * nn) : nullptr;
+  void* sls = refine_iters > 0 && tc ? cv.take<char>(tc_zgemm_sliced_scratch(n_chi, n_chi, n_chi, kRefineLevels))
+                                     : nullptr;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 8 * sizeof(int), s), "memset flag"))) return st;
+  for (int k0 = 0; k0 < n_omega; k0 += bsz) {
+    const int B = std::min(bsz, n_omega - k0);
+    const char* in = static_cast<const char*>(chi_w) + k0 * nn * es;
+    char* out = static_cast<char*>(w_w) + k0 * nn * es;
+    double* rk = resid_h ? resid_h + k0 : nullptr;
+    if (is_fp64(prec))
+      st = screen_batch<double>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, nullptr, refine_iters, rws, nullptr, s);
+    else st = screen_batch<float>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, tcs, refine_iters, rws, sls, s);
+    if (st) return st;
+    if (first_bad && nbatch > 1 && *first_bad < 0) {
+      int f[3] = {0, 0, 0};
+      cudaMemcpyAsync(f, ctx->dflag, sizeof(f), cudaMemcpyDeviceToHost, s);
+      if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
+      if (f[0]) *first_bad = k0 + f[2];
+    }
+  }
+  return GW_OK;
+}
+
 }  // namespace gw
 
 using namespace gw;
@@ -768,41 +811,13 @@ extern "C" gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_
   cudaStream_t s = as_stream(stream);
   std::vector<double> vh(n_chi);
   if ((st = gw_coulomb_sqrt(grid, gvec_h, n_chi, vh.data()))) return fail(ctx, st, gw_last_error(nullptr));
-  const size_t es = csize(prec);
-  const size_t nn = (size_t)n_chi * n_chi;
-  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
-  int bsz = 0, nbatch = 0;
-  const size_t need = screen_scratch(n_chi, n_omega, prec, &bsz, &nbatch, refine_iters > 0);
-  const size_t tcs_bytes = tc ? screen_tc_scratch(n_chi, bsz, refine_iters > 0) : 0;
-  if ((st = reserve(ctx, need))) return st;
+  if ((st = reserve(ctx, screen_scratch(n_chi, n_omega, prec, nullptr, nullptr, refine_iters > 0)))) return st;
   Carver cv(ctx->arena);
   double* dvh = cv.take<double>(n_chi);
-  void* E = cv.take<char>(bsz * nn * es);
-  void* M = cv.take<char>(bsz * nn * es);
-  double2* pr = cv.take<double2>(4 * (size_t)n_chi);
-  void* tcs = tc ? cv.take<char>(tcs_bytes) : nullptr;
-  double2* rws = refine_iters > 0 ? cv.take<double2>(4 * nn) : nullptr;
-  void* sls = refine_iters > 0 && tc ? cv.take<char>(tc_zgemm_sliced_scratch(n_chi, n_chi, n_chi, kRefineLevels))
-                                     : nullptr;
   if ((st = upload(ctx, dvh, vh.data(), sizeof(double) * n_chi, s))) return st;
-  if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->dflag, 0, 8 * sizeof(int), s), "memset flag"))) return st;
   int first_bad = -1;
-  for (int k0 = 0; k0 < n_omega; k0 += bsz) {
-    const int B = std::min(bsz, n_omega - k0);
-    const char* in = static_cast<const char*>(chi_w) + k0 * nn * es;
-    char* out = static_cast<char*>(w_w) + k0 * nn * es;
-    double* rk = resid_h ? resid_h + k0 : nullptr;
-    if (is_fp64(prec))
-      st = screen_batch<double>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, nullptr, refine_iters, rws, nullptr, s);
-    else st = screen_batch<float>(ctx, prec, n_chi, B, in, dvh, E, M, out, pr, rk, tcs, refine_iters, rws, sls, s);
-    if (st) return st;
-    if (nbatch > 1 && first_bad < 0) {
-      int f[3] = {0, 0, 0};
-      cudaMemcpyAsync(f, ctx->dflag, sizeof(f), cudaMemcpyDeviceToHost, s);
-      if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
-      if (f[0]) first_bad = k0 + f[2];
-    }
-  }
+  if ((st = screen_launch(ctx, n_chi, n_omega, prec, refine_iters, dvh, chi_w, w_w, cv, resid_h, &first_bad, s)))
+    return st;
   int flag[8] = {0};
   if ((st = cuda_check(ctx, cudaMemcpyAsync(flag, ctx->dflag, sizeof(flag), cudaMemcpyDeviceToHost, s), "flag")))
     return st;

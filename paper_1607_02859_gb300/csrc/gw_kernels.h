@@ -85,6 +85,14 @@ size_t sigma_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, in
                      bool full = false);
 gw_status upload_scales(gw_ctx* ctx, void* dst, const GreenScales& gs, gw_prec prec, cudaStream_t st);
 
+// ---- chi0 plans (gw_pipeline.cu), as used by the batch plans
+int* chi0_plan_status_words(gw_chi0_plan* p);
+size_t chi0_plan_work(const gw_chi0_plan* p);
+
+// ---- the screening without host work (gw_dyson.cu); see its definition
+gw_status screen_launch(gw_ctx* ctx, int n_chi, int n_omega, gw_prec prec, int refine_iters, const double* dvh,
+                        const void* chi_w, void* w_w, Carver& cv, double* resid_h, int* first_bad, cudaStream_t s);
+
 // ---- the self-energy pass split for plans (gw_sigma.cu)
 // Device tables of one evaluation: G-set maps, bands, per-tau band factors
 // (n_b 8-byte slots per tau, packed in the working precision), C, S, omega and

@@ -31,6 +31,33 @@ size_t chi0_omega_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_ch
   return probe.off;
 }
 
+// chi(G,G') = X(G,G') + conj(X(G',G)) in place, for every frequency.  The
+// tensor-core chi pass forms only the lower triangle T of chi(r,R') (R' <= r)
+// with its diagonal halved; chi(r,R') is Hermitian, so chi = T + T^H, and the
+// transforms of Eqs. FFTX1, FFTX2 and the cosine transform (Eq. CTX, real
+// weights) carry that over: chi(G,G',i omega) = X + X^H with X the result for T.
+// One CTA per pair of 32 x 32 tiles (I, J), I <= J, through shared memory.
+__global__ void __launch_bounds__(256) hermitize_kernel(float2* __restrict__ X, long sx, int n) {
+  __shared__ float2 a[32][33], b[32][33];
+  const int I = blockIdx.x, J = blockIdx.y;
+  if (I > J) return;
+  float2* x = X + blockIdx.z * sx;
+  const int tx = threadIdx.x;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int r = I * 32 + y, c = J * 32 + tx;
+    a[y][tx] = (r < n && c < n) ? x[(long)r * n + c] : make_float2(0.f, 0.f);
+    const int r2 = J * 32 + y, c2 = I * 32 + tx;
+    b[y][tx] = (r2 < n && c2 < n) ? x[(long)r2 * n + c2] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int r = I * 32 + y, c = J * 32 + tx;
+    if (r < n && c < n) x[(long)r * n + c] = make_float2(a[y][tx].x + b[tx][y].x, a[y][tx].y - b[tx][y].y);
+    const int r2 = J * 32 + y, c2 = I * 32 + tx;
+    if (I != J && r2 < n && c2 < n) x[(long)r2 * n + c2] = make_float2(b[y][tx].x + a[tx][y].x, b[y][tx].y - a[tx][y].y);
+  }
+}
+
 // Device tables of one chi0 evaluation.
 struct Chi0Dev {
   const int* map = nullptr;      // [n_chi] FFT positions of the G set
@@ -96,7 +123,7 @@ static gw_status chi0_launch(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ,
       const int rows = std::min(rb, g.nr - r0);
       if (tc) {
         if ((st = tc_chi_rows(ctx, g, n_b, n_occ, psi, gs, r0, rows, prec, ga, tcs, first, s,
-                              t.sk ? t.sk + (size_t)j * n_b : nullptr, t.status)))
+                              t.sk ? t.sk + (size_t)j * n_b : nullptr, t.status, true)))
           return st;
         first = false;
         st = launch_row_fft(ctx, g, prec, 1, ga, nullptr, g.nr, slab_j + (size_t)r0 * n_chi * es, n_chi, t.map, n_chi,
@@ -110,8 +137,13 @@ static gw_status chi0_launch(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ,
     }
     if ((st = launch_col_plane(ctx, g, prec, -1, slab_j, n_chi, n_chi, 1.0, s))) return st;
   }
-  return launch_col_line_ct(ctx, g, prec, slabs, (long)slab, n_chi, n, t.cw, n, chi_w, (long)n_chi * n_chi, n_chi,
-                            t.inv, n_chi, s, cw32.empty() ? nullptr : cw32.data());
+  if ((st = launch_col_line_ct(ctx, g, prec, slabs, (long)slab, n_chi, n, t.cw, n, chi_w, (long)n_chi * n_chi, n_chi,
+                               t.inv, n_chi, s, cw32.empty() ? nullptr : cw32.data())))
+    return st;
+  if (!tc) return GW_OK;
+  const int nt = (n_chi + 31) / 32;
+  hermitize_kernel<<<dim3(nt, nt, n), dim3(32, 8), 0, s>>>(static_cast<float2*>(chi_w), (long)n_chi * n_chi, n_chi);
+  return launch_check(ctx, "hermitize_kernel");
 }
 
 }  // namespace gw
@@ -273,6 +305,13 @@ extern "C" gw_status gw_chi0_plan_status(gw_chi0_plan* p, void* stream) {
   const bool tc = p->prec == GW_F16X3 || p->prec == GW_BF16X3;
   return tc ? tc_check_status(p->ctx, p->t.status, as_stream(stream)) : GW_OK;
 }
+
+namespace gw {
+// For the batch plans: the device time-out words of a chi0 plan (2 ints) and
+// the arena bytes a launch uses.
+int* chi0_plan_status_words(gw_chi0_plan* p) { return p->t.status; }
+size_t chi0_plan_work(const gw_chi0_plan* p) { return p->work; }
+}  // namespace gw
 
 extern "C" gw_status gw_chi0_plan_destroy(gw_chi0_plan* p) {
   if (!p) return GW_OK;

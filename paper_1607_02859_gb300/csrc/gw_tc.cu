@@ -82,6 +82,11 @@ struct Params {
   double* acc_u;          // Sigma_unocc_nn(tau_j) at acc_u[n * acc_stride], Sigma_occ likewise
   double* acc_o;
   int acc_stride;
+  // MODE 0 and 2: only tiles with R' <= r (the grid row of the tile's rows is r0 + local row).
+  // chi(r,R') and G(r,R') W~(r,R') are Hermitian in (r, R'): MODE 0 writes the lower triangle with
+  // the diagonal halved (T, so that the transform of chi is X + X^H with X that of T) and zeros
+  // above; MODE 2 weights the strictly lower part 2 and the diagonal 1 (the real quadratic form).
+  int lower;
 };
 
 // Blocked accumulation.  The tensor cores add each MMA's products into the FP32
@@ -136,6 +141,26 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM;
   const int n0 = blockIdx.x * BNC;
+  const long grow0 = (long)p.r0 + m0;                 // grid row of the tile's first row
+  if (MODE != 1 && p.lower && n0 >= grow0 + BM) {
+    // every R' of the tile is above every r: zeros (chi), or nothing (self-energy)
+    if (MODE == 0) {
+      for (int idx = threadIdx.x; idx < BM * (BNC / 2); idx += blockDim.x) {
+        const int row = idx / (BNC / 2), pc = 2 * (idx % (BNC / 2));
+        const int gm = m0 + row, gn = n0 + pc;
+        if (gm >= p.m_rows || gn >= p.n_cols) continue;
+        float2* o = p.out0 + (long)gm * p.ldo + gn;
+        if (gn + 1 < p.n_cols && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+          *reinterpret_cast<float4*>(o) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+          o[0] = make_float2(0.f, 0.f);
+          if (gn + 1 < p.n_cols) o[1] = make_float2(0.f, 0.f);
+        }
+      }
+    }
+    return;
+  }
+  const bool diag_tile = MODE != 1 && p.lower && n0 + BNC > grow0;   // the tile meets the diagonal
   const int total = p.k_occ_steps + p.k_un_steps;
   const int n_un_blocks = (p.k_un_steps + CH - 1) / CH;
   const bool have_occ = p.k_occ_steps > 0;
@@ -360,12 +385,19 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
         const int c0 = n0 + h * 64;                   // first complex column of this warp's half
         const bool vec = (p.ldw % 2 == 0) && ((reinterpret_cast<uintptr_t>(p.wrr) & 15) == 0);
         // H = g tot o W~ in place; returns the power of two that puts the row's max below 2^15
+        const long grow = grow0 + row;             // grid row r of this thread
         auto times_w = [&](float g) -> int {
           float m = 0.f;
 #pragma unroll
           for (int c = 0; c < 64; c += 2) {
             const int gn = c0 + c;
             float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            // weight of (r, R'): 2 below the diagonal, 1 on it, 0 above (lower-triangle mode)
+            float wa = 1.f, wb = 1.f;
+            if (p.lower) {
+              wa = gn < grow ? 2.f : (gn == grow ? 1.f : 0.f);
+              wb = gn + 1 < grow ? 2.f : (gn + 1 == grow ? 1.f : 0.f);
+            }
             if (rvalid) {
               if (vec && gn + 1 < p.n_cols) {
                 w = __ldg(reinterpret_cast<const float4*>(wrow + gn));
@@ -382,8 +414,8 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
                 }
               }
             }
-            const float ar = tot[2 * c] * g, ai = tot[2 * c + 1] * g;
-            const float br = tot[2 * c + 2] * g, bi = tot[2 * c + 3] * g;
+            const float ar = tot[2 * c] * g * wa, ai = tot[2 * c + 1] * g * wa;
+            const float br = tot[2 * c + 2] * g * wb, bi = tot[2 * c + 3] * g * wb;
             tot[2 * c] = ar * w.x - ai * w.y;
             tot[2 * c + 1] = ar * w.y + ai * w.x;
             tot[2 * c + 2] = br * w.z - bi * w.w;
@@ -462,7 +494,6 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
           }
           const int e = *p.dexp;
           const float fu = ldexpf(1.0f, -(shu + e)), fo = ldexpf(1.0f, -(sho + e));
-          const long grow = (long)p.r0 + gm;
 #pragma unroll
           for (int n = 0; n < 32; ++n) {
             if (n < p.n_n) {
@@ -498,13 +529,13 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
         }
       } else {
         float2* stg = epi + ew * 32 * EPI_COLS;
-  #pragma unroll
+#pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
           const int nc0 = n0 + h * 64 + cc * 16;
-  #pragma unroll
+#pragma unroll
           for (int pass = 0; pass < (MODE == 0 ? 1 : 2); ++pass) {
             // row `lane` of the chunk to shared memory (rotated), then 128-byte row segments out
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < 2; ++u) {
               uint32_t ro[16];
               const bool need_occ = MODE == 0 || pass == 0;
@@ -512,22 +543,31 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
                 tmem_ld16(tmem + lane_addr + (uint32_t)(bo * 256 + h * 128 + 32 * cc + 16 * u), ro);
                 tmem_wait_ld();
               } else {
-  #pragma unroll
+#pragma unroll
                 for (int i = 0; i < 16; ++i) ro[i] = 0u;
               }
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < 8; ++j) {
                 const float gor = __uint_as_float(ro[2 * j]) * ao, goi = __uint_as_float(ro[2 * j + 1]) * ao;
                 const float gur = tot[32 * cc + 16 * u + 2 * j] * au, gui = tot[32 * cc + 16 * u + 2 * j + 1] * au;
                 float2 v;
-                if (MODE == 0) v = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
-                else v = pass == 0 ? make_float2(gor, goi) : make_float2(gur, gui);
+                if (MODE == 0) {
+                  v = make_float2(-2.0f * (gor * gur + goi * gui), -2.0f * (goi * gur - gor * gui));
+                  if (diag_tile) {
+                    const long rr = grow0 + q * 32 + lane, cn = nc0 + u * 8 + j;
+                    const float f = cn < rr ? 1.f : (cn == rr ? 0.5f : 0.f);
+                    v.x *= f;
+                    v.y *= f;
+                  }
+                } else {
+                  v = pass == 0 ? make_float2(gor, goi) : make_float2(gur, gui);
+                }
                 stg[lane * EPI_COLS + ((u * 8 + j + lane) & (EPI_COLS - 1))] = v;
               }
             }
             __syncwarp();
             float2* outp = (MODE == 0 || pass == 0) ? p.out0 : p.out1;
-  #pragma unroll
+#pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int idx = i * 32 + lane;
               const int rr = idx >> 3, pc = (idx & 7) * 2;
@@ -779,7 +819,7 @@ static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, b
 static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
                      int r0, int n_rows, gw_prec prec, int mode, void* out0, void* out1, void* scratch, bool prep_b,
                      cudaStream_t st, const float* sk_dev = nullptr, int* status_dev = nullptr,
-                     const TcSigma* sig = nullptr) {
+                     const TcSigma* sig = nullptr, bool lower = false) {
   const uint32_t fmt = prec == GW_BF16X3 ? 1u : 0u;
   const Layout L = layout(n_b, n_occ);
   gw_status rc;
@@ -884,6 +924,7 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
   P.coef = 0.0;
   P.acc_u = P.acc_o = nullptr;
   P.acc_stride = 0;
+  P.lower = (mode != 1 && lower) ? 1 : 0;
   if (mode == 2) {
     P.wrr = sig->wrr;
     P.ldw = sig->ldw;
@@ -894,12 +935,25 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
     P.acc_o = sig->acc_o;
     P.acc_stride = sig->acc_stride;
   }
-  const dim3 grid((g.nr + BNC - 1) / BNC, (n_rows + BM - 1) / BM);
+  // lower-triangle self-energy: the column tiles past the block's last row hold no R' <= r
+  const int col_end = (mode == 2 && P.lower) ? std::min(g.nr, r0 + n_rows) : g.nr;
+  const dim3 grid((col_end + BNC - 1) / BNC, (n_rows + BM - 1) / BM);
+  // multiply-adds the launch performs: full tiles, or those meeting R' <= r
+  double tiles = (double)grid.x * grid.y;
+  if (P.lower) {
+    tiles = 0;
+    for (unsigned by = 0; by < grid.y; ++by) {
+      const long last_row = (long)r0 + by * BM + BM - 1;
+      tiles += std::min<double>(grid.x, (double)(last_row / BNC + 1));
+    }
+  }
+  const double tile_frac = tiles / ((double)((g.nr + BNC - 1) / BNC) * grid.y);
   auto go = [&](auto kernel) -> gw_status {
     gw_status r = cuda_check(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                              "cudaFuncSetAttribute");
     if (r) return r;
-    const double work = 8.0 * n_rows * (double)g.nr * n_b + (mode == 2 ? 16.0 * n_rows * (double)g.nr * P.n_n : 0.0);
+    const double work =
+        tile_frac * (8.0 * n_rows * (double)g.nr * n_b + (mode == 2 ? 16.0 * n_rows * (double)g.nr * P.n_n : 0.0));
     KTimer kt(ctx, KF_GREEN_TC, work, st);
     kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mah, mal, mbh, mbl, mph, mpl, P);
     return launch_check(ctx, "green_tc_kernel");
@@ -932,7 +986,7 @@ gw_status tc_sigma_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, cons
                         cudaStream_t st) {
   if (sig.n_n < 1 || sig.n_n > 32) return fail(ctx, GW_ERR_SHAPE, "fused self-energy contraction takes 1..32 bands");
   return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 2, nullptr, nullptr, scratch, prep_b, st, sig.sk,
-                 nullptr, &sig);
+                 nullptr, &sig, true);
 }
 
 gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
@@ -943,9 +997,9 @@ gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, cons
 
 gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
                       int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st,
-                      const float* sk_dev, int* status_dev) {
+                      const float* sk_dev, int* status_dev, bool lower) {
   return tc::run(ctx, g, n_b, n_occ, psi, gs, r0, n_rows, prec, 0, chi, nullptr, scratch, prep_b, st, sk_dev,
-                 status_dev);
+                 status_dev, nullptr, lower);
 }
 
 gw_status tc_check_status(gw_ctx* ctx, const int* status_dev, cudaStream_t st) {

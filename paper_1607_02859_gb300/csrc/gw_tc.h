@@ -19,12 +19,16 @@ gw_status tc_green_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, cons
 // chi rows = -2 G_occ o conj(G_unocc) with both tiles accumulated in tensor memory.
 // sk_dev: the per-band factors gs.s already on the device as FP32 (then the
 // call copies nothing from the host).
+// lower: only R' <= r (grid rows r0 ..): the diagonal halved and zeros above it, whose
+// transform X gives chi(G,G') = X + X^H (chi is Hermitian in (r, R')).
 gw_status tc_chi_rows(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const void* psi, const GreenScales& gs,
                       int r0, int n_rows, gw_prec prec, void* chi, void* scratch, bool prep_b, cudaStream_t st,
-                      const float* sk_dev = nullptr, int* status_dev = nullptr);
+                      const float* sk_dev = nullptr, int* status_dev = nullptr, bool lower = false);
 // The self-energy contraction fused into the G formation of rows r0 .. r0+n_rows-1
-// (first term of Eq. Sigma_occ_reduce): for every 128 x 128 tile, H = G o W~ on
-// CUDA cores, V_n = H psi_n on tcgen05, and
+// (first term of Eq. Sigma_occ_reduce): for every 128 x 128 tile with R' <= r
+// (G o W~ is Hermitian in (r, R'), so the real quadratic form is twice its
+// strictly lower part plus its diagonal), H = w G o W~ on CUDA cores (w = 2, 1),
+// V_n = H psi_n on tcgen05, and
 //   acc_u[n * acc_stride] += coef sum_r Re(conj(psi_n(r)) V_n^unocc(r)),  acc_o likewise with -coef.
 // G never leaves the chip.  wrr: W~(r,R') rows of the block [n_rows][ldw] (FP32
 // complex); bands: device [n_n], 1 <= n_n <= 32.  The scratch must come from

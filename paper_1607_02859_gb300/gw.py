@@ -29,7 +29,7 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh", "gw_sigma_diag_kmesh",
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
            "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau", "gw_mp2_grids",
-           "gw_zgemm_sliced"]
+           "gw_zgemm_sliced", "gw_batch_plan", "gw_batch_launch", "gw_batch_wait", "gw_batch_destroy"]
 
 
 class GwError(RuntimeError):
@@ -41,6 +41,16 @@ class GwError(RuntimeError):
 
 class Grid(ct.Structure):
     _fields_ = [("n", ct.c_int * 3), ("lattice", ct.c_double * 9)]
+
+
+class BatchSystem(ct.Structure):
+    _fields_ = [("grid", Grid), ("n_b", ct.c_int), ("n_occ", ct.c_int), ("eps_h", ct.POINTER(ct.c_double)),
+                ("mu", ct.c_double), ("n", ct.c_int), ("tau_h", ct.POINTER(ct.c_double)),
+                ("omega_h", ct.POINTER(ct.c_double)), ("C_h", ct.POINTER(ct.c_double)),
+                ("S_h", ct.POINTER(ct.c_double)), ("Cinv_h", ct.POINTER(ct.c_double)), ("n_chi", ct.c_int),
+                ("gvec_h", ct.POINTER(ct.c_int32)), ("fft_index_h", ct.POINTER(ct.c_int32)), ("n_n", ct.c_int),
+                ("bands_h", ct.POINTER(ct.c_int32)), ("r_block", ct.c_int), ("refine_iters", ct.c_int),
+                ("psi", ct.c_void_p), ("chi_w", ct.c_void_p), ("w_tau", ct.c_void_p)]
 
 
 _P = ct.c_void_p
@@ -89,6 +99,10 @@ _SIGS = {
     "gw_invert_transform": (_I, [_I, _DP, _DP]),
     "gw_mp2_grids": (_I, [_I, _D, _D, _DP, _DP, _DP, _DP, _DP]),
     "gw_zgemm_sliced": (_I, [_P, _I, _I, _I, _P, ct.c_long, _P, ct.c_long, _P, ct.c_long, _I, _P]),
+    "gw_batch_plan": (_I, [_P, _I, ct.POINTER(BatchSystem), _I, ct.POINTER(_P)]),
+    "gw_batch_launch": (_I, [_P, _P]),
+    "gw_batch_wait": (_I, [_P, _I, _DP, ct.POINTER(ct.c_int)]),
+    "gw_batch_destroy": (_I, [_P]),
     "gw_sigma_to_tau": (_I, [_P, _I, _I, _I, _DP, _DP, _DP, _DP, _P]),
 }
 
@@ -531,3 +545,69 @@ def sigma_diag_kmesh(ctx, grid, nk, psi_k, eps_k, n_occ, mu, bands_k, tau, omega
     if n_real:
         out["sigma_real"] = s_re
     return out
+
+
+class Batch:
+    """Many systems through the whole hot path in one CUDA-graph launch
+    (gw_batch_plan / gw_batch_launch / gw_batch_wait).  Each system is a dict
+    with grid, psi (device), eps, n_occ, mu, tau, omega, C, S, Cinv, gvec,
+    fft_index, bands, chi_w and w_tau (device work arrays) and optionally
+    r_block and refine.  The host arrays are kept alive by the object."""
+
+    def __init__(self, ctx, systems, prec):
+        self.ctx = ctx
+        self.prec = prec_of(prec)
+        self._keep = []
+        arr = (BatchSystem * len(systems))()
+        self.shapes = []
+        for i, s in enumerate(systems):
+            eps, tau, om = _f64(s["eps"]), _f64(s["tau"]), _f64(s["omega"])
+            C, S, Ci = _f64(s["C"]), _f64(s["S"]), _f64(s["Cinv"])
+            gv, fi, bands = _i32(s["gvec"]), _i32(s["fft_index"]), _i32(s["bands"])
+            self._keep += [eps, tau, om, C, S, Ci, gv, fi, bands]
+            b = arr[i]
+            b.grid = s["grid"]
+            b.n_b = s["psi"].shape[0]
+            b.n_occ = int(s["n_occ"])
+            b.eps_h, b.mu, b.n = _dp(eps), float(s["mu"]), len(tau)
+            b.tau_h, b.omega_h, b.C_h, b.S_h, b.Cinv_h = _dp(tau), _dp(om), _dp(C), _dp(S), _dp(Ci)
+            b.n_chi, b.gvec_h, b.fft_index_h = len(fi), _ip(gv), _ip(fi)
+            b.n_n, b.bands_h = len(bands), _ip(bands)
+            b.r_block, b.refine_iters = int(s.get("r_block", 0)), int(s.get("refine", 0))
+            b.psi = _dev(s["psi"], "psi", self.prec)
+            b.chi_w = _dev(s["chi_w"], "chi_w", self.prec)
+            b.w_tau = _dev(s["w_tau"], "w_tau", self.prec)
+            self.shapes.append((len(bands), len(tau)))
+        self._arr = arr
+        h = ct.c_void_p()
+        _check(lib().gw_batch_plan(ctx.handle, len(systems), arr, self.prec, ct.byref(h)), ctx)
+        self.handle = h
+
+    def launch(self):
+        _check(lib().gw_batch_launch(self.handle, _stream()), self.ctx)
+
+    def wait(self, timeout_ms=-1):
+        """(list of Sigma_nn(i omega) arrays [n_n][n], list of per-system status)."""
+        tot = sum(a * b for a, b in self.shapes)
+        buf = np.zeros(2 * tot)
+        st = (ct.c_int * len(self.shapes))()
+        rc = lib().gw_batch_wait(self.handle, int(timeout_ms), _dp(buf), st)
+        if rc not in (0, 5):           # numeric failures are reported per system
+            _check(rc, self.ctx)
+        z = buf[0::2] + 1j * buf[1::2]
+        out, o = [], 0
+        for a, b in self.shapes:
+            out.append(z[o:o + a * b].reshape(a, b))
+            o += a * b
+        return out, list(st)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().gw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -70,6 +70,8 @@ def test_batch_mix_and_flops():
     for p in ps:
         assert p.n[0] in (12, 16, 20, 24) and 128 <= p.n_b <= 1024 and p.n_b % 8 == 0
         assert p.n_occ == p.n_b // 8 and 8 <= len(p.tau) <= 16 and p.n_chi <= 2048
-    # G formation dominates: 8 N_r^2 N_b per tau
-    f = batch.chi0_flops(1728, 128, 8, 1728)
-    assert f > 8 * 8.0 * 1728 ** 2 * 128
+    # G formation dominates: 8 N_r^2 N_b per tau, once for chi0 and once for Sigma; agrees with the bench's model
+    import bench
+    f = batch.chain_flops(1728, 128, 8, 1728, 4)
+    assert f > 2 * 8 * 8.0 * 1728 ** 2 * 128
+    assert abs(f - bench.flop_model(1728, 128, 8, 1728, 4)["total"]) < 1e-9 * f
