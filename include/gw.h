@@ -94,7 +94,7 @@ gw_status gw_ctx_reserve(gw_ctx* ctx, size_t bytes);
  * the minimal HBM traffic for the transforms).  Enabling or disabling clears
  * the totals.  Families: "green_tc", "cgemm_tc", "cgemm_simt", "row_fft",
  * "col_fft", "col_line_ct", "sigma_contract", "ct" (the standalone transform
- * over tau/omega).  gw_ctx_kernel_stats synchronises on the recorded events;
+ * over tau/omega), "cgemm_exact" (the refinement's sliced product).  gw_ctx_kernel_stats synchronises on the recorded events;
  * any output pointer may be NULL. */
 gw_status gw_ctx_set_timing(gw_ctx* ctx, int enabled);
 gw_status gw_ctx_kernel_stats(gw_ctx* ctx, const char* family, unsigned long long* launches,
@@ -263,7 +263,7 @@ gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t
  * inverse of eps~; the same solve of Eq. W_correlated).  GW_FP64 and GW_FP32:
  * two N^3 FP64 complex GEMMs per step and frequency on CUDA cores, 64 n_chi^2
  * bytes more scratch.  GW_F16X3 / GW_BF16X3: the product chi~ X on tcgen05 as
- * exact fp16 slice products summed in FP64 (gw_zgemm_sliced, 5 levels: 36 bits
+ * exact fp16 slice products summed in FP64 (gw_zgemm_sliced, 4 levels: 30 bits
  * of the row and column maxima) and X R as split fp16 products (R is small),
  * about 160 n_chi^2 bytes more scratch.  The result is then limited by the
  * working precision of w_w.  refine_iters = 0 is gw_screen_W. */

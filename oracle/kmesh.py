@@ -49,15 +49,16 @@ def green_stripe(psi_k, eps_k, n_occ, mu, tau, n, nk):
     pos = supercell_index(n, nk)
     nr = int(np.prod(n))
     n_k = len(ks)
+    # ph[l][k] = exp(-i k.L_l) / N_k; G_L = sum_k ph[l][k] G_k for every lattice vector L at once
+    ph = np.exp(-2j * np.pi * (ks / np.asarray(nk)) @ ks.T).T / n_k
     go = np.zeros((nr, n_k * nr), dtype=np.complex128)
     gu = np.zeros((nr, n_k * nr), dtype=np.complex128)
-    for ki, kv in enumerate(ks):
-        gok = _gr.green_occ(psi_k[ki], eps_k[ki], n_occ, mu, tau)
-        guk = _gr.green_unocc(psi_k[ki], eps_k[ki], n_occ, mu, tau)
-        for li, l in enumerate(k_list(nk)):
-            ph = np.exp(-2j * np.pi * np.sum(kv * l / np.asarray(nk))) / n_k
-            go[:, pos[li]] += ph * gok
-            gu[:, pos[li]] += ph * guk
+    for which, out in (("occ", go), ("unocc", gu)):
+        gk = np.stack([(_gr.green_occ if which == "occ" else _gr.green_unocc)(psi_k[ki], eps_k[ki], n_occ, mu, tau)
+                       for ki in range(n_k)])                                   # [N_k][N_r][N_r]
+        gl = (ph @ gk.reshape(n_k, -1)).reshape(n_k, nr, nr)                   # [N_L][N_r][N_r]
+        for li in range(n_k):
+            out[:, pos[li]] = gl[li]
     return go, gu
 
 
@@ -76,6 +77,27 @@ def chi_q(chi_s, n, nk, lattice, gvecs):
         p_row = np.exp(-2j * np.pi * (m / ns) @ i_cell.T)               # exp(-i(q+g).r), r in C
         p_col = np.exp(-2j * np.pi * (m / ns) @ i_sup.T)                # exp(-i(q+g').R'), R' in S
         out.append((dv * dv / vol) * (p_row @ chi_s @ p_col.conj().T))
+    return np.array(out)
+
+
+def chi_q_rows(chi_s, n, nk, lattice, gvecs, qs, rows):
+    """chi_q(g_row, g') for the listed q (indices in k_list order) and G-set rows
+    only, every g': the same sums as chi_q, [len(qs)][len(rows)][N_chi]."""
+    n = np.asarray(n)
+    nk = np.asarray(nk)
+    ns = n * nk
+    vol = abs(np.linalg.det(lattice))
+    dv = vol / int(np.prod(n))
+    i_cell = np.stack(np.meshgrid(*[np.arange(d) for d in n], indexing="ij"), -1).reshape(-1, 3)
+    i_sup = np.stack(np.meshgrid(*[np.arange(d) for d in ns], indexing="ij"), -1).reshape(-1, 3)
+    kl = k_list(nk)
+    out = []
+    for qi in qs:
+        q = kl[qi]
+        m = q[None, :] + nk[None, :] * np.asarray(gvecs)
+        p_row = np.exp(-2j * np.pi * (m[rows] / ns) @ i_cell.T)
+        p_col = np.exp(-2j * np.pi * (m / ns) @ i_sup.T)
+        out.append((dv * dv / vol) * ((p_row @ chi_s) @ p_col.conj().T))
     return np.array(out)
 
 

@@ -273,7 +273,7 @@ struct RegFFT {
 // Grids with compiled FFT kernels (each kernel is specialised on its lengths so
 // that the register FFTs are fully unrolled).  Other grids get GW_ERR_UNSUPPORTED.
 #define GW_GRIDS(X) \
-  X(4, 4, 4) X(6, 6, 6) X(6, 4, 6) X(8, 8, 8) X(8, 6, 10) X(12, 12, 12) X(16, 16, 16) X(20, 20, 20) X(24, 24, 24) X(36, 36, 36)
+  X(4, 4, 4) X(6, 6, 6) X(6, 4, 6) X(8, 8, 8) X(8, 6, 10) X(12, 12, 12) X(16, 16, 16) X(20, 20, 20) X(24, 24, 24) X(36, 36, 36) X(48, 48, 48)
 bool grid_supported(int n1, int n2, int n3);
 
 }  // namespace gw

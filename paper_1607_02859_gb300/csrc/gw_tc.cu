@@ -801,12 +801,12 @@ static size_t scratch_bytes(const GridInfo& g, int n_b, int n_occ, int n_rows, b
   probe.take<float>(n_b);
   probe.take<uint16_t>((size_t)2 * g.nr * L.kpad);
   probe.take<uint16_t>((size_t)2 * g.nr * L.kpad);
-  probe.take<uint16_t>((size_t)n_rows * L.kpad);
-  probe.take<uint16_t>((size_t)n_rows * L.kpad);
   if (n_sig > 0) {
     probe.take<uint16_t>((size_t)sig_np(n_sig) * sig_kp(g));
     probe.take<uint16_t>((size_t)sig_np(n_sig) * sig_kp(g));
   }
+  probe.take<uint16_t>((size_t)n_rows * L.kpad);
+  probe.take<uint16_t>((size_t)n_rows * L.kpad);
   if (with_tmp) probe.take<float2>((size_t)n_rows * g.nr);
   return Carver::round(probe.off);
 }
@@ -832,11 +832,13 @@ static gw_status run(gw_ctx* ctx, const GridInfo& g, int n_b, int n_occ, const v
   float* dsk = cv.take<float>(n_b);
   uint16_t* bhi = cv.take<uint16_t>((size_t)2 * g.nr * L.kpad);
   uint16_t* blo = cv.take<uint16_t>((size_t)2 * g.nr * L.kpad);
-  uint16_t* ahi = cv.take<uint16_t>((size_t)n_rows * L.kpad);
-  uint16_t* alo = cv.take<uint16_t>((size_t)n_rows * L.kpad);
+  // the psi_n operand is prepared by the first call and read by later ones: its place must
+  // not depend on this call's number of rows, so it comes before the A operand
   const int np = mode == 2 ? sig_np(sig->n_n) : 0, kps = sig_kp(g);
   uint16_t* phi = mode == 2 ? cv.take<uint16_t>((size_t)np * kps) : nullptr;
   uint16_t* plo = mode == 2 ? cv.take<uint16_t>((size_t)np * kps) : nullptr;
+  uint16_t* ahi = cv.take<uint16_t>((size_t)n_rows * L.kpad);
+  uint16_t* alo = cv.take<uint16_t>((size_t)n_rows * L.kpad);
   float2* tmp = need_tmp ? cv.take<float2>((size_t)n_rows * g.nr) : nullptr;
   if (mode == 1) {
     if (!out0) out0 = tmp;

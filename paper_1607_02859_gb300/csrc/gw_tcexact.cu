@@ -285,18 +285,22 @@ __global__ void col_exp_fix_kernel(int* cexp, int N) {
   if (j < N && cexp[j] < -1100) cexp[j] = 0;     // all-zero column
 }
 
-__device__ __forceinline__ uint16_t ihalf(double s) { return __half_as_ushort(__double2half((double)s)); }
+__device__ __forceinline__ uint16_t ihalf(long long s) { return __half_as_ushort(__int2half_rn((int)s)); }
 
-// The S slices of x * 2^(beta - e): s_0 = rint(v), v <- (v - s_0) 2^beta, ...
+// The S slices of x 2^(beta - e) (|.| < 2^beta): the integer V = rint(x 2^(beta S - e))
+// (one FP64 multiply and conversion; V < 2^(6S) fits 64 bits) written in balanced
+// base 2^beta, V = sum_a s_a 2^(beta (S-1-a)), lower digits s_a in [-32, 32), the top one
+// |s_0| <= 64, all exact in fp16.  Integer digit extraction keeps FP64 work to two operations.
 template <int S>
 __device__ __forceinline__ void cut(double x, int e, uint16_t (&out)[S]) {
-  double v = ldexp(x, BETA - e);
+  long long v = __double2ll_rn(ldexp(x, BETA * S - e));
 #pragma unroll
-  for (int a = 0; a < S; ++a) {
-    const double s = rint(v);
-    out[a] = ihalf(s);
-    v = ldexp(v - s, BETA);
+  for (int a = S - 1; a > 0; --a) {
+    const long long d = ((v + 32) & 63) - 32;
+    out[a] = ihalf(d);
+    v = (v - d) >> BETA;          // exact: v - d is a multiple of 64
   }
+  out[0] = ihalf(v);
 }
 
 // A [M][K] -> As [S][M][kp]: (re, im) slices at real columns 2k, 2k+1; zero padding.

@@ -196,7 +196,8 @@ class Context:
         """Grow the scratch arena to at least nbytes now (synchronises the device when it grows)."""
         _check(lib().gw_ctx_reserve(self.handle, int(nbytes)), self)
 
-    FAMILIES = ("green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft", "col_line_ct", "sigma_contract", "ct")
+    FAMILIES = ("green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft", "col_line_ct", "sigma_contract", "ct",
+                "cgemm_exact")
 
     def set_timing(self, enabled: bool):
         _check(lib().gw_ctx_set_timing(self.handle, 1 if enabled else 0), self)

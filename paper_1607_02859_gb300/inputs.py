@@ -187,6 +187,14 @@ def si64(seed=3):
                         name="si64_36^3_4224b")
 
 
+def k8448(seed=3):
+    """The 36^3 workload's bands (128 + 4096, so K = 8448 real per G element) and
+    energy windows on a 20^3 grid with 4 tau and chi on 2048 G: the G-formation
+    kernels at their full K, on a device footprint that suits a profiler capture."""
+    return make_problem((20, 20, 20), 20.52 * 20 / 36, 128, 4096, (-0.5, 0.0), (0.03, 5.0), 0.015, 4,
+                        seed, n_bands_sigma=32, n_chi=2048, pin_edges=True, name="k8448_20^3_4224b")
+
+
 def tiny(seed=11, n=(6, 6, 6), a=(6.0, 6.5, 7.0), n_occ=4, n_unocc=20, n_tau=6, real=False,
          n_chi=None):
     """Few-second case for the oracle: orthorhombic cell, ragged sizes allowed."""

@@ -68,6 +68,36 @@ def test_chi0_kmesh(ctx, case, prec):
     assert err < TOL[prec] and max(per_q) < 3 * TOL[prec]
 
 
+def test_chi0_kmesh_12cube_k4x4x4(ctx):
+    """A 12^3 cell on a 4 x 4 x 4 mesh (the meshes of the batched configuration):
+    64 k points and a 48^3 supercell, rows of 110 592 points through the
+    two-pass row transform; sampled q and G rows against the stripe oracle."""
+    p = inputs.kmesh_problem(n=(12, 12, 12), a=(10.26, 10.26, 10.26), nk=(4, 4, 4), n_occ=2, n_unocc=10, n_tau=2,
+                             seed=67, n_chi=60)
+    gv = ogv.g_set(p.n, p.n_chi)
+    mats = ogrids.transform_matrices(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
+    qs, rows = [0, 21, 63], [0, 7, 33, 59]
+    ref_t = []
+    for t in p.tau:
+        go, gu = okm.green_stripe(p.psi_k, p.eps_k, p.n_occ, p.mu, t, p.n, p.nk)
+        ref_t.append(okm.chi_q_rows(-2.0 * go * gu.conj(), p.n, p.nk, p.lattice, gv, qs, rows))
+        del go, gu
+    ref_t = np.array(ref_t)                                                    # [tau][q][rows][n_chi]
+    ref = np.einsum("kj,jqrg->qkrg", mats["C"], ref_t)                         # [q][omega][rows][n_chi]
+    grid = gw.make_grid(p.n, p.lattice)
+    for prec in ("fp32", "f16x3"):
+        dt = gw.cdtype(prec)
+        psi = torch.from_numpy(np.ascontiguousarray(p.psi_k)).to("cuda", dtype=dt)
+        out = torch.zeros((p.n_k, len(p.tau), p.n_chi, p.n_chi), dtype=dt, device="cuda")
+        gw.chi0_omega_kmesh(ctx, grid, p.nk, psi, p.eps_k, p.n_occ, p.mu, p.tau, mats["C"], gv, prec, out)
+        got = out[qs][:, :, rows, :].cpu().numpy().astype(np.complex128)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print("12^3 on 4x4x4 (48^3 supercell) %s: sampled rows %.2e" % (prec, err))
+        assert err < TOL[prec], err
+        del psi, out
+        torch.cuda.empty_cache()
+
+
 def test_kmesh_argument_checks(ctx, case):
     name, p, gv, mats, ref = case
     grid = gw.make_grid(p.n, p.lattice)
