@@ -342,7 +342,9 @@ def main():
         return out
 
     for _ in range(args.warmup):
-        step(psi)
+        out = step(psi)
+        if not np.all(np.isfinite(out["sigma_iw"])):
+            raise RuntimeError("Sigma(i omega) of the warm-up step is not finite")
     torch.cuda.synchronize()
 
     fl = flop_model(p.n_r, p.n_b, n_tau, p.n_chi, len(p.bands))

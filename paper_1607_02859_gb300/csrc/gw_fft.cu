@@ -14,6 +14,7 @@
 //    "line" kernel the i1 1-D FFT in registers.  The last i1 pass of the chi
 //    chain also applies the cosine transform over all tau (Eq. CTX) before
 //    anything is written, saving a full read+write of chi(G,G',tau).
+#include <cooperative_groups.h>
 #include <mutex>
 #include <type_traits>
 
@@ -215,6 +216,156 @@ __global__ void __launch_bounds__(256) row_line_bwd_kernel(const typename cpx<T>
 #pragma unroll
     for (int i1 = 0; i1 < N1; ++i1) out[row * ldo + (long)i1 * PL + i23] = x[i1];
   }
+}
+
+// Rows too long for one CTA's shared memory, split over a thread-block cluster
+// of CL CTAs: CTA c holds planes i1 in [c P, (c+1) P) (P = N1 / CL) of the row
+// and the slice [c n_s, (c+1) n_s) of its G-set side (n_s = ceil(n_chi / CL)).
+// The (i2, i3) transforms run on the CTA's own planes; for the i1 transforms
+// each CTA takes N2 N3 / CL of the (i2, i3) columns and reads and writes the
+// other CTAs' planes and G-set slices through distributed shared memory.  Each
+// element crosses HBM once, as for the one-CTA rows.
+template <typename T, int N1, int N2, int N3>
+struct ClusterRow {
+  using C = typename cpx<T>::t;
+  static constexpr int S2 = N3 % 2 == 0 ? N3 + 1 : N3;
+  static constexpr int PL = N2 * N3;
+  static constexpr size_t plane_bytes(int cl) { return (size_t)(N1 / cl) * N2 * S2 * sizeof(C); }
+  static constexpr bool fits(int cl) {
+    return N1 % cl == 0 && PL % cl == 0 && plane_bytes(cl) + 32768 <= 200 * 1024;
+  }
+  // the smallest cluster whose planes leave room for two CTAs per SM, else the smallest that fits
+  static constexpr int pick() {
+    for (int cl : {2, 4, 8})
+      if (fits(cl) && plane_bytes(cl) <= 96 * 1024) return cl;
+    for (int cl : {2, 4, 8})
+      if (fits(cl)) return cl;
+    return 0;
+  }
+  static constexpr int CL = pick();
+  static constexpr int P = CL ? N1 / CL : 1;
+  static constexpr int COLS = CL ? PL / CL : 1;
+  // one thread per pencil of the local planes (P N2 = COLS when N2 = N3), two CTAs per SM
+  static constexpr int THREADS = CL ? ((P * N2 > COLS ? P * N2 : COLS) + 1) / 2 : 32;
+  static size_t smem(int n_chi) { return plane_bytes(CL) + (size_t)((n_chi + CL - 1) / CL) * sizeof(C); }
+};
+
+// MODE 0 / 1 / 2 as for row_fft_kernel; grid (CL, rows), clusters of CL along x.
+template <typename T, int N1, int N2, int N3, int MODE, bool VEC>
+__global__ void __launch_bounds__(ClusterRow<T, N1, N2, N3>::THREADS, 2)
+    row_cluster_kernel(const typename cpx<T>::t* __restrict__ a, const typename cpx<T>::t* __restrict__ b, long lda,
+                       typename cpx<T>::t* __restrict__ out, long ldo, const int* __restrict__ inv, int n_chi,
+                       T scale) {
+  namespace cg = cooperative_groups;
+  using C = typename cpx<T>::t;
+  using R = ClusterRow<T, N1, N2, N3>;
+  constexpr int P = R::P, PL = R::PL, S2 = R::S2, COLS = R::COLS;
+  constexpr int TH = R::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);                         // [P][N2][S2] own planes
+  C* gs = reinterpret_cast<C*>(smem_raw + R::plane_bytes(R::CL));  // [n_s] own G-set slice
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (int)cluster.block_rank();
+  const long row = blockIdx.y;
+  const int n_s = (n_chi + R::CL - 1) / R::CL;
+  const int j0 = c * n_s, j1 = min(n_chi, j0 + n_s);
+  const long pbase = (long)c * P * PL;                           // the CTA's planes within the row
+  auto plane_pos = [](int e) {
+    const int p = e / PL, rem = e - p * PL, i2 = rem / N3;
+    return (p * N2 + i2) * S2 + (rem - i2 * N3);
+  };
+  auto planes_2d = [&](auto dir) {
+    constexpr int D = decltype(dir)::value;
+    pencil_pass<N3, D>(s, P * N2, 1, [](int q) { return q * S2; });
+    __syncthreads();
+    pencil_pass<N2, D>(s, P * N3, S2, [](int q) { return (q / N3) * (N2 * S2) + (q % N3); });
+    __syncthreads();
+  };
+  if (MODE == 2) {
+    // the G-set slice, then i1 transforms of the CTA's columns into every CTA's planes
+    for (int j = j0 + threadIdx.x; j < j1; j += TH) gs[j - j0] = a[row * lda + j];
+    cluster.sync();
+    for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
+      const int i2 = q / N3, i3 = q - i2 * N3;
+      C x[N1];
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        const int j = __ldg(inv + i1 * PL + q);
+        x[i1] = mk(T(0), T(0));
+        if (j >= 0) {
+          const int o = j / n_s;
+          x[i1] = cluster.map_shared_rank(gs, o)[j - o * n_s];
+        }
+      }
+      RegFFT<N1, -1>::run(x);
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) cluster.map_shared_rank(s, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3] = x[i1];
+    }
+    cluster.sync();                                              // no remote access after this point
+    planes_2d(std::integral_constant<int, -1>{});
+    C* dst = out + row * ldo + pbase;
+    if (VEC) {
+      for (int q = threadIdx.x; q < P * PL / 2; q += TH) {
+        const int ps = plane_pos(2 * q);
+        st_pair(dst + 2 * q, cscale(s[ps], scale), cscale(s[ps + 1], scale));
+      }
+    } else {
+      for (int e = threadIdx.x; e < P * PL; e += TH) dst[e] = cscale(s[plane_pos(e)], scale);
+    }
+    return;
+  }
+  // forward: the CTA's planes (with the product of Eq. chi_rr for MODE 0) ...
+  const C* pa = a + row * lda + pbase;
+  const C* pb = b + row * lda + pbase;
+  if (VEC) {
+    constexpr int NP = P * PL / 2;
+    for (int q0 = threadIdx.x; q0 < NP; q0 += 4 * TH) {
+      C v[4][2], w[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * TH;
+        if (q < NP) {
+          ld_pair(pa + 2 * q, v[u][0], v[u][1]);
+          if (MODE == 0) ld_pair(pb + 2 * q, w[u][0], w[u][1]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * TH;
+        if (q >= NP) continue;
+        const int ps = plane_pos(2 * q);
+        s[ps] = MODE == 0 ? cscale(cmulc(v[u][0], w[u][0]), scale) : v[u][0];
+        s[ps + 1] = MODE == 0 ? cscale(cmulc(v[u][1], w[u][1]), scale) : v[u][1];
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < P * PL; e += TH) {
+      C v = pa[e];
+      if (MODE == 0) v = cscale(cmulc(v, pb[e]), scale);
+      s[plane_pos(e)] = v;
+    }
+  }
+  __syncthreads();
+  planes_2d(std::integral_constant<int, +1>{});
+  cluster.sync();
+  // ... i1 transforms of the CTA's columns, each result scattered to the G-set slice that holds it
+  for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
+    const int i2 = q / N3, i3 = q - i2 * N3;
+    C x[N1];
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) x[i1] = cluster.map_shared_rank(s, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3];
+    RegFFT<N1, +1>::run(x);
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int j = __ldg(inv + i1 * PL + q);
+      if (j >= 0) {
+        const int o = j / n_s;
+        cluster.map_shared_rank(gs, o)[j - o * n_s] = x[i1];
+      }
+    }
+  }
+  cluster.sync();                                                // no remote access after this point
+  for (int j = j0 + threadIdx.x; j < j1; j += TH) out[row * ldo + j] = gs[j - j0];
 }
 
 constexpr int kPlaneW = 16;
@@ -537,12 +688,49 @@ struct GridOps {
                        const int* map, int n_chi, int n_rows, double scale, cudaStream_t st, const int* inv,
                        void* tmp) {
     const size_t bytes = RowLayout<N1, N2, N3>::TOT * sizeof(C);
-    if (bytes > kRowSmemMax)
-      return row_two_pass(ctx, mode, a, b, lda, out, ldo, inv, tmp, n_chi, n_rows, scale, st);
     const double rd = mode == 0 ? 2.0 * RowLayout<N1, N2, N3>::NR : (mode == 1 ? RowLayout<N1, N2, N3>::NR : n_chi);
     const double wr = mode == 2 ? RowLayout<N1, N2, N3>::NR : n_chi;
     auto al = [](const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; };
     const bool vec = al(a) && al(b) && al(out) && lda % 2 == 0 && ldo % 2 == 0 && n_chi % 2 == 0 && N3 % 2 == 0;
+    if (bytes > kRowSmemMax) {
+      using CR = ClusterRow<T, N1, N2, N3>;
+      if constexpr (CR::CL > 0 && RowLayout<N1, N2, N3>::TOT * sizeof(C) > kRowSmemMax) {
+        if (inv && CR::smem(n_chi) <= kRowSmemMax) {
+          const size_t cbytes = CR::smem(n_chi);
+          auto go = [&](auto kernel) -> gw_status {
+            gw_status s = set_smem(ctx, kernel, cbytes);
+            if (s) return s;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(CR::CL, (unsigned)n_rows);
+            cfg.blockDim = dim3(CR::THREADS);
+            cfg.dynamicSmemBytes = cbytes;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = CR::CL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (rd + wr) * sizeof(C), st);
+            gw_status r = cuda_check(ctx, cudaLaunchKernelEx(&cfg, kernel, (const C*)a, (const C*)b, lda, (C*)out, ldo,
+                                                             inv, n_chi, (T)scale),
+                                     "cudaLaunchKernelEx(row_cluster_kernel)");
+            if (r) return r;
+            return launch_check(ctx, "row_cluster_kernel");
+          };
+#define GW_ROWC_GO(M)                                                                        \
+          if (mode == M) return vec ? go(row_cluster_kernel<T, N1, N2, N3, M, N3 % 2 == 0>)  \
+                                    : go(row_cluster_kernel<T, N1, N2, N3, M, false>);
+          GW_ROWC_GO(0)
+          GW_ROWC_GO(1)
+          GW_ROWC_GO(2)
+#undef GW_ROWC_GO
+          return fail(ctx, GW_ERR_ARG, "bad row transform mode");
+        }
+      }
+      return row_two_pass(ctx, mode, a, b, lda, out, ldo, inv, tmp, n_chi, n_rows, scale, st);
+    }
     auto go = [&](auto kernel, int threads) -> gw_status {
       gw_status s = set_smem(ctx, kernel, bytes);
       if (s) return s;

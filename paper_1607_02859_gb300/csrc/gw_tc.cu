@@ -431,7 +431,9 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
         // 4h..4h+3: row `row` of a chunk is 64 bytes at (row/8)*512 + (row%8)*64, its
         // 16-byte segment s stored at s ^ ((row/2) % 4) (the 64-byte swizzle of TMA)
         auto store_h = [&](int sh) {
-          const float s = ldexpf(1.0f, sh);
+          // 2^sh in two factors: a row of tiny H (W~ of a large tau decays like exp(-omega tau))
+          // can need sh above 127, where one FP32 power of two would overflow
+          const float s1 = ldexpf(1.0f, sh >> 1), s2 = ldexpf(1.0f, sh - (sh >> 1));
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int base = (4 * h + j) * A_BYTES + (row >> 3) * 512 + (row & 7) * 64;
@@ -442,8 +444,8 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
               for (int t = 0; t < 4; ++t) {
                 const int c = 16 * j + 4 * sg + t;
                 uint16_t h0, l0, h1, l1;
-                split<FMT>(tot[2 * c] * s, h0, l0);
-                split<FMT>(tot[2 * c + 1] * s, h1, l1);
+                split<FMT>(tot[2 * c] * s1 * s2, h0, l0);
+                split<FMT>(tot[2 * c + 1] * s1 * s2, h1, l1);
                 hw[t] = (uint32_t)h0 | ((uint32_t)h1 << 16);
                 lw[t] = (uint32_t)l0 | ((uint32_t)l1 << 16);
               }
@@ -492,15 +494,18 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
               }
             }
           }
-          const int e = *p.dexp;
-          const float fu = ldexpf(1.0f, -(shu + e)), fo = ldexpf(1.0f, -(sho + e));
+          // 2^-(sh + e) in two factors as well, applied one after the other, so that the
+          // tiny rows come back as normal FP32 numbers where they are representable
+          const int e = *p.dexp, ku = shu + e, ko = sho + e;
+          const float fu1 = ldexpf(1.0f, -(ku >> 1)), fu2 = ldexpf(1.0f, -(ku - (ku >> 1)));
+          const float fo1 = ldexpf(1.0f, -(ko >> 1)), fo2 = ldexpf(1.0f, -(ko - (ko >> 1)));
 #pragma unroll
           for (int n = 0; n < 32; ++n) {
             if (n < p.n_n) {
               float2 ps = make_float2(0.f, 0.f);
               if (rvalid) ps = __ldg(p.psi + (long)p.bands[n] * p.ldpsi + grow);
-              float su = (ps.x * tot[2 * n] + ps.y * tot[2 * n + 1]) * fu;          // Re(conj(psi_n) V_n)
-              float so = (ps.x * tot[64 + 2 * n] + ps.y * tot[64 + 2 * n + 1]) * fo;
+              float su = (ps.x * tot[2 * n] + ps.y * tot[2 * n + 1]) * fu1 * fu2;    // Re(conj(psi_n) V_n)
+              float so = (ps.x * tot[64 + 2 * n] + ps.y * tot[64 + 2 * n + 1]) * fo1 * fo2;
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) {
                 su += __shfl_xor_sync(0xffffffffu, su, o);

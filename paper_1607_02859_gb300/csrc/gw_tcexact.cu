@@ -14,8 +14,16 @@
 // rounding of the additions.  For every slice pair (a, b) with a + b <= L
 // (largest terms first) and every K block of 4096 real elements, one tcgen05
 // pass forms that exact block sum, and the epilogue adds it, times
-// 2^(e_i + f_j - (a+b+2) beta), into the FP64 output.  Dropped pairs and the
+// 2^(e_i + f_j - (a+b+2) beta), into the output.  Dropped pairs and the
 // rest are below 2^(-6(L+1)) of the row and column maxima.
+//
+// GB300's FP64 rate is a few operations per clock and SM, too slow for an
+// FP64 update per pass.  A block sum times 2^-(a+b+2) beta is exact in FP32, so
+// the passes add it into an unevaluated pair hi + lo of FP32 numbers (the
+// error-free sum of Knuth, then a renormalisation: ~48 bits) kept in the
+// output's own 16 bytes per complex element; the last pass converts the pair to
+// FP64 and applies 2^(e_i + f_j).  Tiles are taken in groups of kGroupM row
+// tiles so that the CTAs running together share their operand rows in L2.
 //
 // Complex-to-real mapping as in the other tensor-core GEMMs: A is a real
 // [M][2K] operand with (re, im) interleaved along K, B holds two real rows per
@@ -45,10 +53,35 @@ constexpr int A_BYTES = BM * BK * 2;             // 8 KB
 constexpr int B_BYTES = 2 * BNC * BK * 2;        // 16 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_CPX = 16;                      // complex columns per epilogue round
-constexpr int EPI_BYTES = 4 * 32 * EPI_CPX * 8;  // per epilogue warp: 32 rows x 16 complex (FP32)
+constexpr int EPI_WARPS = 8;                     // two per tensor-memory lane quarter, one per column half
+constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_CPX * 8;   // per epilogue warp: 32 rows x 16 complex (FP32)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
-constexpr int THREADS = 192;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int kGroupM = 8;                       // row tiles per group of the tile order
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+
+// tile t of the persistent order -> (row tile, column tile): kGroupM row tiles are
+// walked down each column before moving on, so ~152 consecutive tiles span
+// kGroupM row tiles and ~19 column tiles of operands
+__device__ __forceinline__ void tile_of(long t, int tm, int tn, int& bm, int& bn) {
+  const long per_group = (long)kGroupM * tn;
+  const int g = (int)(t / per_group);
+  const int first = g * kGroupM;
+  const int rows = min(kGroupM, tm - first);
+  const long r = t - (long)g * per_group;
+  bm = first + (int)(r % rows);
+  bn = (int)(r / rows);
+}
+
+// hi + lo += v exactly (Knuth's two-sum), then renormalised
+__device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (v - bb);
+  const float t = lo + e;
+  hi = s + t;
+  lo = t - (hi - s);
+}
 
 struct XParams {
   int M, N;               // complex output size
@@ -69,7 +102,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
                                                                   const __grid_constant__ CUtensorMap mB, XParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float2* epi = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);     // [4 warps][32 rows][16]
+  float2* epi = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);     // [EPI_WARPS][32 rows][16]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + EPI_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
@@ -88,7 +121,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], EPI_WARPS);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -114,7 +147,8 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
     // ---------------------------------------------------------- TMA producer
     long kit = 0;
     for (long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-      const int bm = (int)(t / p.tn), bn = (int)(t - (long)bm * p.tn);
+      int bm, bn;
+      tile_of(t, p.tm, p.tn, bm, bn);
       for (int q = 0; q < passes && !*abort_flag; ++q) {
         const int pr = q / p.n_kb, kb = q - pr * p.n_kb;
         for (int ks = k_first(kb); ks < k_last(kb); ++ks, ++kit) {
@@ -175,13 +209,16 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
     mbar_wait(done, 0);
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
-    const int qw = warp & 3;
+    const int ew = warp - 2;
+    const int qw = warp & 3;                     // tensor-memory lane quarter
+    const int hh = ew >> 2;                      // column half: complex columns hh*64 .. hh*64+63
     const uint32_t lane_addr = (uint32_t)(qw * 32) << 16;
-    float2* stg = epi + qw * 32 * EPI_CPX;
+    float2* stg = epi + ew * 32 * EPI_CPX;
     long pc = 0;
     bool go = true;
     for (long t = blockIdx.x; t < ntiles && go; t += gridDim.x) {
-      const int bm = (int)(t / p.tn), bn = (int)(t - (long)bm * p.tn);
+      int bm, bn;
+      tile_of(t, p.tm, p.tn, bm, bn);
       const int r0 = bm * BM + qw * 32;
       const int n0 = bn * BNC;
       for (int q = 0; q < passes; ++q, ++pc) {
@@ -195,9 +232,10 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
           break;
         }
         const int shift = (p.pa[pr] + p.pb[pr] + 2) * BETA;
-        const bool first = q == 0;
+        const float scl = __int_as_float((127 - shift) << 23);    // 2^-shift, exact
+        const bool first = q == 0, last = q == passes - 1;
 #pragma unroll 1
-        for (int c = 0; c < 2 * BNC; c += 2 * EPI_CPX) {
+        for (int c = hh * BNC; c < (hh + 1) * BNC; c += 2 * EPI_CPX) {
           uint32_t r[2][16];
           tmem_ld16(tmem + lane_addr + (uint32_t)(b * 256 + c), r[0]);
           tmem_ld16(tmem + lane_addr + (uint32_t)(b * 256 + c + 16), r[1]);
@@ -210,22 +248,33 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
                   make_float2(__uint_as_float(r[u][2 * j]), __uint_as_float(r[u][2 * j + 1]));
           __syncwarp();
           const int nc0 = n0 + c / 2;
-          // two rows of 16 complex FP64 (256 B each) per warp instruction
-#pragma unroll 4
+          // two rows of 16 complex (256 B each) per warp instruction; the sixteen loads of the
+          // running sums are all issued before the first is used
+          const int cc = lane & 15, gn = nc0 + cc;
+          float4 acc[16];
+#pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int rr = 2 * i + (lane >> 4), cc = lane & 15;
-            const int gm = r0 + rr, gn = nc0 + cc;
+            const int gm = r0 + 2 * i + (lane >> 4);
+            acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!first && gm < p.M && gn < p.N)
+              acc[i] = *reinterpret_cast<const float4*>(p.C + (long)gm * p.ldc + gn);
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int rr = 2 * i + (lane >> 4);
+            const int gm = r0 + rr;
             if (gm < p.M && gn < p.N) {
               const float2 v = stg[rr * EPI_CPX + ((cc + rr) & (EPI_CPX - 1))];
-              const int sc = max(p.rexp[gm] + p.cexp[gn] - shift, -2000);
               double2* o = p.C + (long)gm * p.ldc + gn;
-              double2 d = make_double2(ldexp((double)v.x, sc), ldexp((double)v.y, sc));
-              if (!first) {
-                const double2 old = *o;
-                d.x += old.x;
-                d.y += old.y;
+              dd_add(acc[i].x, acc[i].y, v.x * scl);           // (re hi, re lo, im hi, im lo) until the last pass
+              dd_add(acc[i].z, acc[i].w, v.y * scl);
+              if (last) {
+                const int sc = max(p.rexp[gm] + p.cexp[gn], -1000);
+                *o = make_double2(ldexp((double)acc[i].x + (double)acc[i].y, sc),
+                                  ldexp((double)acc[i].z + (double)acc[i].w, sc));
+              } else {
+                *reinterpret_cast<float4*>(o) = acc[i];
               }
-              *o = d;
             }
           }
           __syncwarp();

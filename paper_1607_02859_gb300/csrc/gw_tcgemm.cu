@@ -47,7 +47,7 @@ __device__ __forceinline__ int scale_exp(unsigned int bits) {
   int ex = 0;
   if (!(m > 0.f)) return 0;
   frexpf(m, &ex);
-  return 15 - ex;
+  return min(15 - ex, 126);      // 2^e stays a finite FP32 number for the tiniest operands
 }
 
 // Persistent: CTA c takes tiles c, c + gridDim.x, ... (row tiles ascending, so

@@ -6,11 +6,21 @@ import bench
 
 
 def test_measured_traffic_is_tied_to_the_kernel_source(monkeypatch):
-    key = ("si8", "f16x3", "cgemm_tc")
-    assert bench.measured_traffic(*key) == bench.MEASURED_TRAFFIC[key]["bytes_per_launch"]
-    assert bench.measured_traffic("si64", "f16x3", "green_tc") is None
-    changed = copy.deepcopy(bench.MEASURED_TRAFFIC)
-    path = next(iter(changed[key]["sources"]))
+    import hashlib
+    import os
+    root = os.path.dirname(os.path.abspath(bench.__file__))
+    path = "paper_1607_02859_gb300/csrc/gw_tc.cu"
+    with open(os.path.join(root, path), "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    # every recorded entry names a committed profile summary
+    for k, r in bench.MEASURED_TRAFFIC.items():
+        assert os.path.exists(os.path.join(root, r["profile"])), k
+    key = ("w", "f16x3", "green_tc")
+    rec = {key: {"bytes_per_launch": 1.0e9, "sources": {path: sha}, "profile": "profiles/x.md"}}
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", rec)
+    assert bench.measured_traffic(*key) == 1.0e9
+    assert bench.measured_traffic("w", "f16x3", "cgemm_tc") is None
+    changed = copy.deepcopy(rec)
     changed[key]["sources"][path] = "0" * 40
     monkeypatch.setattr(bench, "MEASURED_TRAFFIC", changed)
     assert bench.measured_traffic(*key) is None

@@ -1,8 +1,9 @@
 """The whole hot path of several uneven systems as one CUDA-graph launch
 (gw_batch_plan / gw_batch_launch / gw_batch_wait): every system's
 Sigma_nn(i omega) against the FP64 oracle chain (chi0 -> W~ -> W~(tau) ->
-Sigma), replays reproduce the first launch, and the plan refuses to replay once
-the context's arena has moved."""
+Sigma), replays reproduce the first launch to rounding (the fused self-energy
+sums its r-block partials with atomics, whose order varies), and the plan
+refuses to replay once the context's arena has moved."""
 import numpy as np
 import pytest
 
@@ -63,12 +64,15 @@ def test_batch_matches_oracle(ctx, problems, prec, refine):
         err = float(np.max(np.abs(got - ref["sigma_iw"])))
         print("%s %s: max |dSigma(i omega)| = %.2e Ha" % (p.name, prec, err))
         assert err < tol, (p.name, err)
-    # a replay gives the same results (the graph keeps every pointer and table)
+    # a replay gives the same results (the graph keeps every pointer and table);
+    # the self-energy's r-block partials are summed by atomics in varying order,
+    # so equal up to rounding of the working precision
     b.launch()
     sig2, status2 = b.wait(timeout_ms=60000)
     assert status2 == [0] * len(problems)
+    rel = 1e-12 if prec == "fp64" else 1e-5
     for a, c in zip(sig, sig2):
-        assert np.array_equal(a, c)
+        assert np.max(np.abs(a - c)) <= rel * np.max(np.abs(a)) + 1e-12
     b.close()
 
 

@@ -58,33 +58,41 @@ def test_chi0_tau_rows(ctx, g36, prec):
     assert err < TAU_TOL[prec]
 
 
+@pytest.mark.parametrize("n,n_chi,prec", [(36, 2048, "fp32"), (36, 8192, "fp32"), (36, 2048, "fp64"),
+                                          (48, 4096, "fp32")])
 @pytest.mark.parametrize("direction", [1, -1])
-def test_row_transform_two_pass(ctx, g36, direction):
-    p, gv, idx, mats = g36
-    grid = gw.make_grid(p.n, p.lattice)
-    rng = np.random.default_rng(7 + direction)
+def test_row_transform_large_rows(ctx, n, n_chi, prec, direction):
+    """Rows longer than one CTA's shared memory: 36^3 and 48^3 FP32 rows are
+    split over a thread-block cluster, FP64 36^3 rows take two passes."""
+    shape = (n, n, n)
+    lattice = np.eye(3) * (n * 10.26 / 12)
+    volume = float(np.linalg.det(lattice))
+    idx = ogv.fft_index(ogv.g_set(shape, n_chi), shape)
+    grid = gw.make_grid(shape, lattice)
+    rng = np.random.default_rng(7 + direction + n + n_chi)
     rows = 5
-    nr = int(np.prod(p.n))
+    nr = n ** 3
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
     if direction > 0:
         x = rng.standard_normal((rows, nr)) + 1j * rng.standard_normal((rows, nr))
         # X(r,G') = sum_R' x(r,R') exp(+i G'.R')  (Eq. FFTX1)
-        ref = np.stack([nr * np.fft.ifftn(v.reshape(p.n)).reshape(-1)[idx] for v in x])
-        out = torch.empty((rows, p.n_chi), dtype=torch.complex64, device="cuda")
+        ref = np.stack([nr * np.fft.ifftn(v.reshape(shape)).reshape(-1)[idx] for v in x])
+        out = torch.empty((rows, n_chi), dtype=cdt, device="cuda")
     else:
-        x = rng.standard_normal((rows, p.n_chi)) + 1j * rng.standard_normal((rows, p.n_chi))
+        x = rng.standard_normal((rows, n_chi)) + 1j * rng.standard_normal((rows, n_chi))
         # W(r,R') = (1/Omega) sum_G' W(r,G') exp(-i G'.R')  (second step of Eq. FFTW)
         ref = []
         for v in x:
             y = np.zeros(nr, dtype=np.complex128)
             y[idx] = v
-            ref.append(np.fft.fftn(y.reshape(p.n)).reshape(-1) / p.volume)
+            ref.append(np.fft.fftn(y.reshape(shape)).reshape(-1) / volume)
         ref = np.stack(ref)
-        out = torch.empty((rows, nr), dtype=torch.complex64, device="cuda")
-    inp = torch.from_numpy(x).to("cuda", dtype=torch.complex64)
-    gw.rr_to_GG_fft(ctx, grid, direction, 1, idx, "fp32", 0, rows, inp, out)
+        out = torch.empty((rows, nr), dtype=cdt, device="cuda")
+    inp = torch.from_numpy(x).to("cuda", dtype=cdt)
+    gw.rr_to_GG_fft(ctx, grid, direction, 1, idx, prec, 0, rows, inp, out)
     got = out.cpu().numpy().astype(np.complex128)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err < 1e-6, err
+    assert err < (1e-6 if prec == "fp32" else 1e-13), err
 
 
 def test_sigma_sparse_w(ctx, g36):

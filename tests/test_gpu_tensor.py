@@ -116,6 +116,36 @@ def test_tc_sigma(ctx, case, prec):
         assert err < 1e-4 * np.max(np.abs(sig_ref))
 
 
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_sigma_fast_decaying_w(ctx, prec):
+    """A W~ whose entries all decay as exp(-omega tau) with omega tau_max ~ 82, so
+    that at the largest tau every product G o W~ is ~1e-36: the fused contraction
+    scales such rows up by more than 2^127 before splitting them into 16-bit
+    parts, and must neither overflow nor lose them."""
+    p = PROBLEMS["k_multi"]()
+    s = opipe.setup(p)
+    grid = gw.make_grid(p.n, p.lattice)
+    n = len(p.tau)
+    t_max = float(np.max(p.tau))
+    base = [(1, 1, -0.9, 81.0), (7, 7, -0.5, 82.0), (1, 7, 0.1 + 0.05j, 81.5), (7, 1, 0.1 - 0.05j, 81.5)]
+    entries = [(a, b, p.volume * c * np.exp(-(x / t_max) * p.tau)) for (a, b, c, x) in base]
+    w = torch.zeros((n, p.n_chi, p.n_chi), dtype=torch.complex64, device="cuda")
+    for (a, b, v) in entries:
+        for j in range(n):
+            w[j, a, b] = complex(v[j])
+    su, so = osg.sigma_pair_sparse(p.psi, p.eps, p.n_occ, p.mu, p.tau, entries, p.n, p.lattice, s["fft_index"],
+                                   p.bands)
+    ref = osg.sigma_iw(su, so, s["C"], s["S"])
+    out = gw.sigma_diag(ctx, grid, dev(p.psi), p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, s["C"], s["S"], w,
+                        s["fft_index"], prec)
+    assert np.all(np.isfinite(out["sigma_unocc"])) and np.all(np.isfinite(out["sigma_occ"]))
+    # the largest tau: ~1e-36 values, compared relative to their own size
+    last = np.abs(out["sigma_unocc"][:, -1] - su[:, -1]).max() / np.abs(su[:, -1]).max()
+    assert last < (1e-3 if prec == "f16x3" else 1e-2), last
+    err = np.max(np.abs(out["sigma_iw"] - ref))
+    assert err < MEV and err < 1e-4 * np.max(np.abs(ref)), err
+
+
 WTOL = {"f16x3": 2e-5, "bf16x3": 3e-4}
 
 
