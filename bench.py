@@ -260,12 +260,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     ap.add_argument("--refine", type=int, default=None,
                     help="refinement steps of the screening solve (default: 1 on si64, whose recipe asks for it, else 0)")
+    ap.add_argument("--r-block", type=int, default=None,
+                    help="rows per r-block of the chi0 pass (default: 4096 on si64, as its recipe streams chi0, "
+                         "else the library's default)")
+    ap.add_argument("--g-form", default="rr", choices=["rr", "pw"],
+                    help="G of the chi0 pass: rr = real-space contraction on the tensor cores (N_r^2 N_b per "
+                         "tau); pw = plane-wave form over the orbitals' plane waves, then transforms "
+                         "(gw_chi0_omega_pw)")
     ap.add_argument("--sigma", default="diag", choices=["diag", "matrix"],
                     help="diag: Sigma_nn, continuation and QP energies; matrix: the full Sigma_nm(i omega)")
     args = ap.parse_args()
 
     from paper_1607_02859_gb300 import inputs
     refine = args.refine if args.refine is not None else (1 if args.workload == "si64" else 0)
+    r_block = args.r_block if args.r_block is not None else (4096 if args.workload == "si64" else 0)
     p = getattr(inputs, args.workload)()
     n_tau = len(p.tau)
     grids = "log-spaced tau in [0.05, 40], omega_k = 1/tau_(N-1-k), weight ridge 1e-6 (the workload's given grid)"
@@ -281,6 +289,9 @@ def main():
                 % (args.workload, *p.n, p.n_r, p.n_occ, p.n_b - p.n_occ, "real" if p.real else "complex", n_tau,
                    p.n_chi, p.n_chi, len(p.bands)),
                 "prec": args.prec, "sigma": args.sigma, "grids": grids, "refine_iters": refine,
+                "r_block": r_block if r_block > 0 else "library default (2048)",
+                "g_form": {"rr": "real-space G contraction (tcgen05)",
+                           "pw": "plane-wave G over the orbitals' N_b plane waves, then transforms"}[args.g_form],
                 "l2": "per-step working set > 40 GB >> 129 MB L2; L2 also flushed between steps",
                 "accuracy": ACCURACY.get(args.prec, "")}
     if args.impl == "reference":
@@ -302,6 +313,8 @@ def main():
     ctx = gw.Context(local)
     grid = gw.make_grid(p.n, p.lattice)
     gvec, fidx = gw.g_set(grid, p.n_chi)                                      # product host setup
+    # the synthetic orbitals span the lowest N_b plane waves e^{+i G.r}
+    pw_index = gw.g_set(grid, p.n_b)[1] if args.g_form == "pw" else None
     mats = gw.fit_transform(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
     dt = gw.cdtype(args.prec)
     psi_h = torch.from_numpy(p.psi.astype(np.complex128)).to(dt).pin_memory()
@@ -319,7 +332,12 @@ def main():
             if events is not None:
                 events[i].record(stream)
         mark(0)
-        gw.chi0_omega(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.tau, mats["C"], fidx, args.prec, chi_w)
+        if args.g_form == "pw":
+            gw.chi0_omega_pw(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.tau, mats["C"], fidx, pw_index, args.prec,
+                             chi_w)
+        else:
+            gw.chi0_omega(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.tau, mats["C"], fidx, args.prec, chi_w,
+                          r_block=r_block)
         mark(1)
         gw.screen_W(ctx, grid, gvec, args.prec, chi_w, chi_w, resid=False, refine=refine)
         mark(2)

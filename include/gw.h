@@ -263,9 +263,9 @@ gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t
  * inverse of eps~; the same solve of Eq. W_correlated).  GW_FP64 and GW_FP32:
  * two N^3 FP64 complex GEMMs per step and frequency on CUDA cores, 64 n_chi^2
  * bytes more scratch.  GW_F16X3 / GW_BF16X3: the product chi~ X on tcgen05 as
- * exact fp16 slice products summed in FP64 (gw_zgemm_sliced, 4 levels: 30 bits
- * of the row and column maxima) and X R as split fp16 products (R is small),
- * about 160 n_chi^2 bytes more scratch.  The result is then limited by the
+ * exact fp16 slice products (gw_zgemm_sliced, 4 levels: 30 bits of the row and
+ * column maxima) and X R as split fp16 products (R is small), about 160
+ * n_chi^2 bytes more scratch.  The result is then limited by the
  * working precision of w_w.  refine_iters = 0 is gw_screen_W. */
 gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h,
                              int n_omega, gw_prec prec, int refine_iters, const void* chi_w,
@@ -274,10 +274,12 @@ gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_chi, const 
 /* Complex FP64 matrix product C = A B with FP64-class accuracy on the fp16
  * tensor cores (the product chi~ X of the refinement residual above; the paper
  * has no counterpart).  Each row of A and column of B is scaled by a power of
- * two and cut into 6-bit integer slices (exact in fp16); the product of two
- * slices summed over 4096 real K elements is an integer below 2^24 and so
- * exact in the FP32 accumulator; slice pairs with a + b <= levels (largest
- * first) are scaled back and added in FP64.  The error is below about
+ * two and cut into 6-bit integer slices (exact in fp16); the products of
+ * slice pairs of one level a + b, summed over 4096 real K elements, are
+ * integers whose bounds add up to at most 2^24 in groups of up to four pairs,
+ * and so exact in one FP32 accumulator; the slice pairs with a + b <= levels
+ * (largest first) are scaled back group by group and added up in pairs of
+ * FP32 numbers (~48 bits), converted to FP64 at the end.  The error is below about
  * 2^(-6(levels+1)) * K * max|A_i.| max|B_.j| per element (levels 5: 2^-36).
  * A [M][K] (lda), B [K][N] (ldb), C [M][N] (ldc) complex double, device,
  * 16-byte aligned, row-major; C is overwritten and must not overlap A or B.
@@ -388,6 +390,30 @@ gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
                         const double* tau_h, const double* C_h, int n_chi,
                         const int32_t* fft_index_h, gw_prec prec, int r_block, void* chi_w,
                         void* stream);
+
+/* chi0(G,G',i omega_k) as gw_chi0_omega, with G taken through its plane-wave
+ * form (the paper evaluates G in a plane-wave representation and Fourier
+ * transforms it to real space when needed, Sec. II.B; at one k point Eqs.
+ * FFT_G1, FFT_G2 are two ordinary transforms).  The orbitals must lie in the
+ * span of the n_pw plane waves e^{+i g.r} whose g sit at the FFT positions
+ * pw_index_h[n_pw] (the formula of fft_index_h); each band's coefficients
+ * D_a(g) = sum_r psi_a(r) e^{-i g.r} must hold its whole norm (Parseval,
+ * relative 1e-5; 1e-10 for GW_FP64), else GW_ERR_ARG names the band.  Per tau_j:
+ *   M(g,g') = sum_a f_a D_a(g) conj(D_a(g')) / N_r^2     (occupied, unoccupied)
+ * over the set, a contraction of n_pw^2 N_b instead of N_r^2 N_b (tcgen05 for
+ * GW_F16X3 / GW_BF16X3), its column transform over the grid, and one row pass
+ * that expands both rows over R', forms chi(r,R') = -2 G_occ conj(G_unocc)
+ * (Eq. chi_rr) and transforms it onto the G set (Eq. FFTX1); then Eqs. FFTX2
+ * and CTX as in gw_chi0_omega.  Scratch (context arena): the slabs
+ * (N_r n_chi n elements) plus 2 N_r n_pw + 2 n_pw^2 + N_b n_pw elements (8 or 16
+ * bytes each) and the tensor-core operands.  GW_ERR_UNSUPPORTED where two
+ * expanded rows of the grid do not fit a thread-block cluster's shared memory
+ * (GW_FP64 at 36^3, every precision at 48^3).  Synchronises the stream once
+ * (the norm check). */
+gw_status gw_chi0_omega_pw(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
+                           const double* eps_h, double mu, int n, const double* tau_h, const double* C_h,
+                           int n_chi, const int32_t* fft_index_h, int n_pw, const int32_t* pw_index_h,
+                           gw_prec prec, void* chi_w, void* stream);
 
 /* chi0(q+G, q+G', i omega_k) for every q of a Gamma-centred nk[0] x nk[1] x nk[2]
  * k mesh, through the supercell stripe of Sec. II.A (spatial transform within

@@ -498,10 +498,11 @@ static gw_status refine_one(gw_ctx* ctx, int n, const typename cpx<T>::t* chi, c
 // The same refinement for the tensor-core precisions, with the product chi~ X
 // of the residual on the tensor cores as exact fp16 slice products (slice pairs
 // up to kRefineLevels, i.e. 30 bits of the row and column maxima: the residual
-// then bounds X to ~1e-9, below the FP32 storage of W~) summed in FP64, and the correction X R as three fp16 split products (R is small: the
-// correction needs only the working precision).  Work: X, chi~, R in FP64 and
-// R, X R in FP32 (the last slot of ws); X in FP32 goes to the upper part of
-// xl, which the final store overwrites with the lower triangle.
+// then bounds X to ~1e-9, below the FP32 storage of W~), and the correction
+// X R as three fp16 split products (R is small: the correction needs only the
+// working precision).  Work: X, chi~, R in FP64 and R, X R in FP32 (the last
+// slot of ws); X in FP32 goes to the upper part of xl, which the final store
+// overwrites with the lower triangle.
 constexpr int kRefineLevels = 4;
 
 __global__ void to_f32_kernel(const double2* __restrict__ X, float2* __restrict__ Y, long nn) {

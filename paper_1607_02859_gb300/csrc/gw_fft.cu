@@ -368,6 +368,136 @@ __global__ void __launch_bounds__(ClusterRow<T, N1, N2, N3>::THREADS, 2)
   for (int j = j0 + threadIdx.x; j < j1; j += TH) out[row * ldo + j] = gs[j - j0];
 }
 
+// chi rows from the plane-wave form of G (the paper evaluates G in a plane-wave
+// representation and transforms it to real space when needed, Sec. II.B; at one
+// k point Eqs. FFT_G1, FFT_G2 are two ordinary transforms).  For each row r the
+// rows a = T_unocc(r, .) and b = T_occ(r, .) over the orbitals' plane-wave set
+// (the column-transformed plane-wave G, length n_pw) are expanded over the grid
+// R' (backward transform), multiplied as
+//   x(R') = scale a(R') conj(b(R'))            (Eq. chi_rr)
+// and transformed forward onto the n_chi-long G set of chi (Eq. FFTX1).  Each
+// element of a row crosses HBM once: n_pw + n_pw values in, n_chi out.  The CL
+// CTAs of a cluster share a row as in row_cluster_kernel (CL = 1: one CTA), with
+// two plane buffers; the slices of the input rows and of the output row share
+// one region (the inputs are read before the first cluster barrier, the output
+// written after the third).
+template <typename T, int N1, int N2, int N3>
+struct PwRow {
+  using C = typename cpx<T>::t;
+  static constexpr int S2 = N3 % 2 == 0 ? N3 + 1 : N3;
+  static constexpr int PL = N2 * N3;
+  static constexpr size_t plane_bytes(int cl) { return (size_t)(N1 / cl) * N2 * S2 * sizeof(C); }
+  static constexpr int pick() {
+    for (int cl : {1, 2, 3, 4, 6, 8})
+      if (N1 % cl == 0 && PL % cl == 0 && 2 * plane_bytes(cl) <= 192 * 1024) return cl;
+    return 0;
+  }
+  static constexpr int CL = pick();
+  static constexpr int P = CL ? N1 / CL : 1;
+  static constexpr int COLS = CL ? PL / CL : 1;
+  static constexpr int WORK = P * N2 > COLS ? (P * N2 > P * N3 ? P * N2 : P * N3) : (COLS > P * N3 ? COLS : P * N3);
+  static constexpr int THREADS = CL ? ((WORK + 31) / 32 * 32 > 1024 ? 1024 : (WORK + 31) / 32 * 32) : 32;
+  static size_t slice_elems(int n_pw, int n_chi) {
+    const size_t in = 2 * (size_t)((n_pw + CL - 1) / CL), out = (size_t)((n_chi + CL - 1) / CL);
+    return in > out ? in : out;
+  }
+  static size_t smem(int n_pw, int n_chi) { return 2 * plane_bytes(CL) + slice_elems(n_pw, n_chi) * sizeof(C); }
+};
+
+template <typename T, int N1, int N2, int N3>
+__global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
+    row_pw_chi_kernel(const typename cpx<T>::t* __restrict__ a, const typename cpx<T>::t* __restrict__ b, long lda,
+                      typename cpx<T>::t* __restrict__ out, long ldo, const int* __restrict__ inv_pw, int n_pw,
+                      const int* __restrict__ inv_chi, int n_chi, T scale) {
+  namespace cg = cooperative_groups;
+  using C = typename cpx<T>::t;
+  using R = PwRow<T, N1, N2, N3>;
+  constexpr int P = R::P, PL = R::PL, S2 = R::S2, COLS = R::COLS, CL = R::CL;
+  constexpr int TH = R::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sa = reinterpret_cast<C*>(smem_raw);                              // [P][N2][S2] a, then x
+  C* sb = reinterpret_cast<C*>(smem_raw + R::plane_bytes(CL));         // [P][N2][S2] b
+  C* sl = reinterpret_cast<C*>(smem_raw + 2 * R::plane_bytes(CL));     // slices
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (int)cluster.block_rank();
+  const long row = blockIdx.y;
+  const int n_ps = (n_pw + CL - 1) / CL, n_cs = (n_chi + CL - 1) / CL;
+  C* su = sl;                 // [n_ps] this CTA's part of a's row
+  C* so = sl + n_ps;          // [n_ps] of b's row
+  {
+    const int j0 = c * n_ps, j1 = min(n_pw, j0 + n_ps);
+    for (int j = j0 + threadIdx.x; j < j1; j += TH) {
+      su[j - j0] = a[row * lda + j];
+      so[j - j0] = b[row * lda + j];
+    }
+  }
+  cluster.sync();
+  // backward i1 transforms of the CTA's columns, for both rows, into every CTA's planes
+  for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
+    const int i2 = q / N3, i3 = q - i2 * N3;
+#pragma unroll 1
+    for (int which = 0; which < 2; ++which) {
+      C* src = which ? so : su;
+      C* dst = which ? sb : sa;
+      C x[N1];
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        const int j = __ldg(inv_pw + i1 * PL + q);
+        x[i1] = mk(T(0), T(0));
+        if (j >= 0) {
+          const int o = j / n_ps;
+          x[i1] = cluster.map_shared_rank(src, o)[j - o * n_ps];
+        }
+      }
+      RegFFT<N1, -1>::run(x);
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1)
+        cluster.map_shared_rank(dst, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3] = x[i1];
+    }
+  }
+  cluster.sync();                  // the planes are complete and the input slices free
+  // (i2, i3) backward transforms of the CTA's planes, both rows
+  pencil_pass<N3, -1>(sa, P * N2, 1, [](int q) { return q * S2; });
+  pencil_pass<N3, -1>(sb, P * N2, 1, [](int q) { return q * S2; });
+  __syncthreads();
+  pencil_pass<N2, -1>(sa, P * N3, S2, [](int q) { return (q / N3) * (N2 * S2) + (q % N3); });
+  pencil_pass<N2, -1>(sb, P * N3, S2, [](int q) { return (q / N3) * (N2 * S2) + (q % N3); });
+  __syncthreads();
+  // the product of Eq. chi_rr, then the forward (i2, i3) transforms
+  for (int e = threadIdx.x; e < P * PL; e += TH) {
+    const int p = e / PL, rem = e - p * PL, i2 = rem / N3;
+    const int ps = (p * N2 + i2) * S2 + (rem - i2 * N3);
+    sa[ps] = cscale(cmulc(sa[ps], sb[ps]), scale);
+  }
+  __syncthreads();
+  pencil_pass<N2, +1>(sa, P * N3, S2, [](int q) { return (q / N3) * (N2 * S2) + (q % N3); });
+  __syncthreads();
+  pencil_pass<N3, +1>(sa, P * N2, 1, [](int q) { return q * S2; });
+  cluster.sync();                  // every CTA's x planes are final
+  // forward i1 transforms of the CTA's columns, each result into the slice of chi that holds it
+  C* sx = sl;                      // [n_cs] this CTA's part of the chi row
+  for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
+    const int i2 = q / N3, i3 = q - i2 * N3;
+    C x[N1];
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) x[i1] = cluster.map_shared_rank(sa, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3];
+    RegFFT<N1, +1>::run(x);
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) {
+      const int j = __ldg(inv_chi + i1 * PL + q);
+      if (j >= 0) {
+        const int o = j / n_cs;
+        cluster.map_shared_rank(sx, o)[j - o * n_cs] = x[i1];
+      }
+    }
+  }
+  cluster.sync();                  // no remote access after this point
+  {
+    const int j0 = c * n_cs, j1 = min(n_chi, j0 + n_cs);
+    for (int j = j0 + threadIdx.x; j < j1; j += TH) out[row * ldo + j] = sx[j - j0];
+  }
+}
+
 constexpr int kPlaneW = 16;
 
 // In-place 2-D FFT over (i2, i3) of the rows of plane i1 = blockIdx.y, for 16
@@ -749,6 +879,43 @@ struct GridOps {
 #undef GW_ROW_GO
     return fail(ctx, GW_ERR_ARG, "bad row transform mode");
   }
+  static bool row_pw_ok(int n_pw, int n_chi) {
+    using PR = PwRow<T, N1, N2, N3>;
+    if constexpr (PR::CL > 0) return PR::smem(n_pw, n_chi) <= kRowSmemMax;
+    return false;
+  }
+  static gw_status row_pw(gw_ctx* ctx, const void* a, const void* b, long lda, void* out, long ldo,
+                           const int* inv_pw, int n_pw, const int* inv_chi, int n_chi, int n_rows, double scale,
+                           cudaStream_t st) {
+    using PR = PwRow<T, N1, N2, N3>;
+    if constexpr (PR::CL > 0) {
+      const size_t bytes = PR::smem(n_pw, n_chi);
+      if (bytes > kRowSmemMax) return fail(ctx, GW_ERR_UNSUPPORTED, "plane-wave chi rows: G sets too large for this grid");
+      auto kernel = row_pw_chi_kernel<T, N1, N2, N3>;
+      gw_status s = set_smem(ctx, kernel, bytes);
+      if (s) return s;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(PR::CL, (unsigned)n_rows);
+      cfg.blockDim = dim3(PR::THREADS);
+      cfg.dynamicSmemBytes = bytes;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = PR::CL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (2.0 * n_pw + n_chi) * sizeof(C), st);
+      s = cuda_check(ctx, cudaLaunchKernelEx(&cfg, kernel, (const C*)a, (const C*)b, lda, (C*)out, ldo, inv_pw, n_pw,
+                                             inv_chi, n_chi, (T)scale),
+                     "cudaLaunchKernelEx(row_pw_chi_kernel)");
+      if (s) return s;
+      return launch_check(ctx, "row_pw_chi_kernel");
+    } else {
+      return fail(ctx, GW_ERR_UNSUPPORTED, "plane-wave chi rows: no cluster split fits this grid and precision");
+    }
+  }
   static gw_status plane(gw_ctx* ctx, int dir, void* buf, long ld, int ncols, double scale, cudaStream_t st) {
     const size_t bytes = (size_t)N2 * N3 * kPlaneW * sizeof(C);
     dim3 grid((ncols + kPlaneW - 1) / kPlaneW, N1);
@@ -845,6 +1012,19 @@ gw_status launch_row_fft(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int mode,
                          cudaStream_t st, const int* inv, void* tmp) {
   if (n_rows <= 0) return GW_OK;
   GW_DISPATCH(prec, g, rc = O::row(ctx, mode, a, b, lda, out, ldo, map, n_chi, n_rows, scale, st, inv, tmp))
+}
+
+gw_status launch_row_pw_chi(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* a, const void* b, long lda,
+                            void* out, long ldo, const int* inv_pw, int n_pw, const int* inv_chi, int n_chi,
+                            int n_rows, double scale, cudaStream_t st) {
+  if (n_rows <= 0) return GW_OK;
+  GW_DISPATCH(prec, g, rc = O::row_pw(ctx, a, b, lda, out, ldo, inv_pw, n_pw, inv_chi, n_chi, n_rows, scale, st))
+}
+
+gw_status check_row_pw(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int n_pw, int n_chi) {
+  GW_DISPATCH(prec, g, rc = O::row_pw_ok(n_pw, n_chi) ? GW_OK : fail(ctx, GW_ERR_UNSUPPORTED,
+                                                                     "plane-wave chi rows: this grid, precision and "
+                                                                     "G sets do not fit a thread-block cluster"))
 }
 
 bool row_two_pass(const GridInfo& g, gw_prec prec) {

@@ -14,6 +14,14 @@ gw_status launch_row_fft(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int mode,
                          long lda, void* out, long ldo, const int* map, int n_chi, int n_rows, double scale,
                          cudaStream_t st, const int* inv = nullptr, void* tmp = nullptr);
 bool row_two_pass(const GridInfo& g, gw_prec prec);
+// chi rows from the plane-wave form of G: a = T_unocc, b = T_occ rows [n_rows][lda]
+// over the orbitals' plane-wave set (inv_pw: grid position -> set index or -1),
+// out [n_rows][ldo] = FFT+(scale a conj(b)) on chi's G set (inv_chi).
+gw_status launch_row_pw_chi(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* a, const void* b, long lda,
+                            void* out, long ldo, const int* inv_pw, int n_pw, const int* inv_chi, int n_chi,
+                            int n_rows, double scale, cudaStream_t st);
+// GW_OK if launch_row_pw_chi supports the grid, precision and set sizes.
+gw_status check_row_pw(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int n_pw, int n_chi);
 
 // gw_sigma.cu: the Sigma contraction over rows of G_occ, G_unocc, W~ (length
 // nr, leading dimension ld) against psi_n (rows of length nr; the row's own

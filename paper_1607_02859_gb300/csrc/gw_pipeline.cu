@@ -8,6 +8,7 @@
 //   (i2,i3) column planes of the slab (first part of Eq. FFTX2).
 // i1 column pass of every slab fused with the cosine transform (Eqs. FFTX2,
 // CTX): chi0(G,G',i omega_k) = sum_j (dV^2/Omega) C_kj FFT_i1(slab_j).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -189,6 +190,211 @@ extern "C" gw_status gw_chi0_omega(gw_ctx* ctx, const gw_grid* grid, int n_b, in
   t.cw = dcw;
   void* tcs = nullptr;
   if ((st = chi0_launch(ctx, g, n_b, n_occ, psi, n, scales, n_chi, prec, rb, t, cw32, cv, chi_w, s, &tcs))) return st;
+  return tc ? tc_check(ctx, tcs, s) : GW_OK;
+}
+
+namespace gw {
+
+// ------------------------------------------------------------------ plane-wave form of G
+//
+// The paper keeps G in a plane-wave representation and transforms it to real
+// space when needed (Sec. II.B; at one k point Eqs. FFT_G1, FFT_G2).  With the
+// orbitals in the span of n_pw plane waves e^{+i g.r} (pw_index), their
+// coefficients D_a(g) = sum_r psi_a(r) e^{+i g.r}, nonzero on the negated set,
+// give
+//   G(r,R') = (1/N_r^2) sum_{g,g'} e^{-i g.r} [sum_a f_a D_a(g) conj(D_a(g'))] e^{+i g'.R'},
+// so with Dc = conj(D)/N_r and Mc = Dc F Dc^H (a G formation over n_pw points)
+//   conj(G(r,R')) = sum_{g,g'} e^{+i g.r} Mc(g,g') e^{-i g'.R'}:
+// a column transform T(r,g') = sum_g e^{+i g.r} Mc(g,g') over the grid, then per
+// row a backward transform over g', and Eq. chi_rr becomes
+//   chi(r,R') = -2 G_occ conj(G_unocc) = -2 conj(G'_occ) G'_unocc     (G' = conj G).
+// The contraction shrinks from N_r^2 N_b to n_pw^2 N_b per tau and occupation;
+// the row kernel expands both rows, multiplies and transforms onto chi's G set.
+
+template <typename C, typename R>
+__global__ void conj_scale_kernel(C* __restrict__ x, size_t n, R s) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    x[e] = mk(x[e].x * s, -x[e].y * s);
+}
+
+// out[2b] = sum_r |psi_b(r)|^2, out[2b+1] = sum_g |D_b(g)|^2 (FP64), one CTA per band.
+template <typename C>
+__global__ void __launch_bounds__(256) band_norms_kernel(const C* __restrict__ psi, long nr, const C* __restrict__ d,
+                                                         long npw, double* __restrict__ out) {
+  __shared__ double red[2][8];
+  const long b = blockIdx.x;
+  double s0 = 0, s1 = 0;
+  for (long i = threadIdx.x; i < nr; i += blockDim.x) {
+    const C v = psi[b * nr + i];
+    s0 += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  for (long i = threadIdx.x; i < npw; i += blockDim.x) {
+    const C v = d[b * npw + i];
+    s1 += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s0;
+    red[1][threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      c += red[1][w];
+    }
+    out[2 * b] = a;
+    out[2 * b + 1] = c;
+  }
+}
+
+static GridInfo pw_grid(const GridInfo& g, int n_pw) {
+  GridInfo q = g;                 // the G formation over the plane-wave set: n_pw "points"
+  q.nr = n_pw;
+  return q;
+}
+
+size_t chi0_pw_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_pw, gw_prec prec) {
+  const size_t es = csize(prec);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  Carver probe(nullptr);
+  probe.take<int>(n_chi);
+  probe.take<int>(g.nr);
+  probe.take<int>(n_pw);
+  probe.take<int>(g.nr);
+  probe.take<double>((size_t)n * n_b);
+  probe.take<double>((size_t)n * n);
+  probe.take<double>(2 * (size_t)n_b);
+  probe.take<char>((size_t)g.nr * n_chi * n * es);       // slabs
+  probe.take<char>((size_t)n_b * n_pw * es);             // Dc
+  probe.take<char>((size_t)n_pw * n_pw * es);            // Mc occ
+  probe.take<char>((size_t)n_pw * n_pw * es);            // Mc unocc
+  probe.take<char>((size_t)g.nr * n_pw * es);            // T occ
+  probe.take<char>((size_t)g.nr * n_pw * es);            // T unocc
+  if (row_two_pass(g, prec) && is_fp64(prec)) probe.take<char>((size_t)n_b * g.nr * es);
+  if (tc) probe.take<char>(tc_scratch_bytes(pw_grid(g, n_pw), n_b, n_occ, n_pw, false));
+  return probe.off;
+}
+
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" gw_status gw_chi0_omega_pw(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
+                                      const double* eps_h, double mu, int n, const double* tau_h, const double* C_h,
+                                      int n_chi, const int32_t* fft_index_h, int n_pw, const int32_t* pw_index_h,
+                                      gw_prec prec, void* chi_w, void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  GridInfo g;
+  gw_status st = chi0_check(ctx, grid, &g, n_b, n_occ, eps_h, mu, n, tau_h, C_h, prec);
+  if (st) return st;
+  if (!psi || !chi_w) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  std::vector<int> map, inv, map_pw, inv_pw;
+  if ((st = index_maps(ctx, g, fft_index_h, n_chi, map, inv))) return st;
+  if ((st = index_maps(ctx, g, pw_index_h, n_pw, map_pw, inv_pw))) return st;
+  // psi = sum_g c(g) e^{+i g.r}: the coefficients D(g) = sum_r psi e^{+i g'.r} sit at g' = -g
+  for (int j = 0; j < n_pw; ++j) {
+    const int q = map_pw[j], i1 = q / (g.n2 * g.n3), i2 = (q / g.n3) % g.n2, i3 = q % g.n3;
+    map_pw[j] = (((g.n1 - i1) % g.n1) * g.n2 + (g.n2 - i2) % g.n2) * g.n3 + (g.n3 - i3) % g.n3;
+  }
+  std::fill(inv_pw.begin(), inv_pw.end(), -1);
+  for (int j = 0; j < n_pw; ++j) inv_pw[map_pw[j]] = j;
+  if ((st = check_row_pw(ctx, g, prec, n_pw, n_chi))) return st;
+  cudaStream_t s = as_stream(stream);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  const size_t es = csize(prec);
+  if ((st = reserve(ctx, chi0_pw_scratch(g, n_b, n_occ, n, n_chi, n_pw, prec)))) return st;
+  std::vector<GreenScales> scales;
+  std::vector<double> cw64;
+  std::vector<float> cw32;
+  chi0_tables(g, n_b, n_occ, eps_h, mu, n, tau_h, C_h, prec, scales, cw64, cw32);
+  Carver cv(ctx->arena);
+  int* dmap = cv.take<int>(n_chi);
+  int* dinv = cv.take<int>(g.nr);
+  int* dmap_pw = cv.take<int>(n_pw);
+  int* dinv_pw = cv.take<int>(g.nr);
+  char* dscale = cv.take<char>((size_t)n * n_b * 8);
+  char* dcw = cv.take<char>((size_t)n * n * 8);
+  double* dnorm = cv.take<double>(2 * (size_t)n_b);
+  const size_t slab = (size_t)g.nr * n_chi;
+  char* slabs = cv.take<char>(slab * n * es);
+  char* dc = cv.take<char>((size_t)n_b * n_pw * es);
+  char* mo = cv.take<char>((size_t)n_pw * n_pw * es);
+  char* mu_ = cv.take<char>((size_t)n_pw * n_pw * es);
+  char* to = cv.take<char>((size_t)g.nr * n_pw * es);
+  char* tu = cv.take<char>((size_t)g.nr * n_pw * es);
+  char* tmp = row_two_pass(g, prec) && is_fp64(prec) ? cv.take<char>((size_t)n_b * g.nr * es) : nullptr;
+  const GridInfo gp = pw_grid(g, n_pw);
+  void* tcs = tc ? cv.take<char>(tc_scratch_bytes(gp, n_b, n_occ, n_pw, false)) : nullptr;
+  if ((st = upload(ctx, dmap, map.data(), sizeof(int) * n_chi, s))) return st;
+  if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
+  if ((st = upload(ctx, dmap_pw, map_pw.data(), sizeof(int) * n_pw, s))) return st;
+  if ((st = upload(ctx, dinv_pw, inv_pw.data(), sizeof(int) * g.nr, s))) return st;
+  if (is_fp64(prec)) st = upload(ctx, dcw, cw64.data(), sizeof(double) * n * n, s);
+  else st = upload(ctx, dcw, cw32.data(), sizeof(float) * 2 * n * n, s);
+  if (st) return st;
+  if (!tc)
+    for (int j = 0; j < n; ++j)
+      if ((st = upload_scales(ctx, dscale + (size_t)j * n_b * 8, scales[j], prec, s))) return st;
+  // plane-wave coefficients D_a(g) of every band, and the check that they hold all of psi
+  if ((st = launch_row_fft(ctx, g, prec, 1, psi, nullptr, g.nr, dc, n_pw, dmap_pw, n_pw, n_b, 1.0, s, dinv_pw, tmp)))
+    return st;
+  if (is_fp64(prec))
+    band_norms_kernel<double2><<<n_b, 256, 0, s>>>((const double2*)psi, g.nr, (const double2*)dc, n_pw, dnorm);
+  else
+    band_norms_kernel<float2><<<n_b, 256, 0, s>>>((const float2*)psi, g.nr, (const float2*)dc, n_pw, dnorm);
+  if ((st = launch_check(ctx, "band_norms_kernel"))) return st;
+  {
+    std::vector<double> nh(2 * (size_t)n_b);
+    if ((st = cuda_check(ctx, cudaMemcpyAsync(nh.data(), dnorm, sizeof(double) * 2 * n_b, cudaMemcpyDeviceToHost, s),
+                         "norms")))
+      return st;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
+    // Parseval: sum_g |D(g)|^2 = N_r sum_r |psi(r)|^2 when psi lies in the set's span
+    const double tol = is_fp64(prec) ? 1e-10 : 1e-5;
+    for (int b = 0; b < n_b; ++b) {
+      const double full = nh[2 * b] * g.nr, part = nh[2 * b + 1];
+      if (!(std::fabs(full - part) <= tol * full))
+        return fail(ctx, GW_ERR_ARG, "band " + std::to_string(b) + " is not in the span of the plane waves of pw_index "
+                                     "(fraction " + std::to_string(full > 0 ? part / full : 0.0) + ")");
+    }
+  }
+  {
+    const size_t nel = (size_t)n_b * n_pw;
+    const int blocks = (int)std::min<size_t>((nel + 255) / 256, (size_t)ctx->num_sms * 8);
+    if (is_fp64(prec)) conj_scale_kernel<<<blocks, 256, 0, s>>>((double2*)dc, nel, 1.0 / g.nr);
+    else conj_scale_kernel<<<blocks, 256, 0, s>>>((float2*)dc, nel, (float)(1.0 / g.nr));
+    if ((st = launch_check(ctx, "conj_scale_kernel"))) return st;
+  }
+  bool first = true;
+  for (int j = 0; j < n; ++j) {
+    // Mc_occ, Mc_unocc over the plane-wave set, then their column transforms T(r, g')
+    if (tc) {
+      st = tc_green_rows(ctx, gp, n_b, n_occ, dc, scales[j], 0, n_pw, prec, mo, mu_, tcs, first, s);
+      first = false;
+    } else {
+      st = green_rows(ctx, gp, n_b, n_occ, dc, dscale + (size_t)j * n_b * 8, scales[j], 0, n_pw, prec, mo, mu_, s);
+    }
+    if (st) return st;
+    for (int part = 0; part < 2; ++part) {
+      char* m = part ? mu_ : mo;
+      char* t = part ? tu : to;
+      if ((st = launch_col_line(ctx, g, prec, +1, 1, m, n_pw, t, n_pw, n_pw, dinv_pw, 1.0, s))) return st;
+      if ((st = launch_col_plane(ctx, g, prec, +1, t, n_pw, n_pw, 1.0, s))) return st;
+    }
+    // chi(r, G', tau_j) for every row r: expand, multiply (Eq. chi_rr), transform (Eq. FFTX1)
+    char* slab_j = slabs + (size_t)j * slab * es;
+    if ((st = launch_row_pw_chi(ctx, g, prec, tu, to, n_pw, slab_j, n_chi, dinv_pw, n_pw, dinv, n_chi, g.nr, -2.0, s)))
+      return st;
+    if ((st = launch_col_plane(ctx, g, prec, -1, slab_j, n_chi, n_chi, 1.0, s))) return st;
+  }
+  if ((st = launch_col_line_ct(ctx, g, prec, slabs, (long)slab, n_chi, n, dcw, n, chi_w, (long)n_chi * n_chi, n_chi,
+                               dinv, n_chi, s, cw32.empty() ? nullptr : cw32.data())))
+    return st;
   return tc ? tc_check(ctx, tcs, s) : GW_OK;
 }
 

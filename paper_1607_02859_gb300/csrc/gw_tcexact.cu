@@ -8,15 +8,17 @@
 // largest component and column j of B the power 2^f_j; each element is then
 // cut into S slices of beta = 6 bits,
 //   A_ik = sum_a s_a(i,k) 2^(e_i - (a+1) beta) + rest,   |s_0| <= 64, |s_a>0| <= 32,
-// all small integers, exact in fp16.  A product of two slices is an integer of
-// at most 2^12, so a sum of up to 4096 of them is an integer of at most 2^24:
-// the FP32 accumulator in tensor memory holds it exactly, whatever the order or
-// rounding of the additions.  For every slice pair (a, b) with a + b <= L
-// (largest terms first) and every K block of 4096 real elements, one tcgen05
-// pass forms that exact block sum, and the epilogue adds it, times
-// 2^(e_i + f_j - (a+b+2) beta), into the output.  Dropped pairs and the
-// rest are below 2^(-6(L+1)) of the row and column maxima.
-//
+// all small integers, exact in fp16.  Over a K block of 4096 real elements
+// the sum of slice products of a pair (a, b) is an integer of at most 2^24
+// (a = b = 0), 2^23 (one of them 0) or 2^22 (neither); pairs of the same level
+// a + b carry the same scale 2^(e_i + f_j - (a+b+2) beta), so a group of them
+// whose bounds add up to at most 2^24 is summed in one FP32 accumulator in
+// tensor memory exactly, whatever the order or rounding of the additions.
+// Levels 0..L (largest terms first) are packed into such groups (L = 4: 15
+// pairs in 8 groups), and for every group and K block one tcgen05 pass forms
+// the exact sum, which the epilogue adds, times its scale, into the output.
+// Dropped pairs and the rest are below 2^(-6(L+1)) of the row and column maxima.
+
 // GB300's FP64 rate is a few operations per clock and SM, too slow for an
 // FP64 update per pass.  A block sum times 2^-(a+b+2) beta is exact in FP32, so
 // the passes add it into an unevaluated pair hi + lo of FP32 numbers (the
@@ -49,6 +51,7 @@ constexpr int KB_REAL = 1 << (24 - 2 * BETA);    // real K per exact block: 4096
 constexpr int KB_STEPS = KB_REAL / BK;
 constexpr int MAX_LEVELS = 7;
 constexpr int MAX_PAIRS = (MAX_LEVELS + 1) * (MAX_LEVELS + 2) / 2;
+constexpr int MAX_GROUPS = MAX_PAIRS;
 constexpr int A_BYTES = BM * BK * 2;             // 8 KB
 constexpr int B_BYTES = 2 * BNC * BK * 2;        // 16 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -87,9 +90,11 @@ struct XParams {
   int M, N;               // complex output size
   int k_steps;            // BK stages over the padded real K
   int n_kb;               // K blocks (KB_STEPS stages each, the last one shorter)
-  int n_pairs;
+  int n_groups;           // groups of pairs summed in one accumulator
   int tm, tn;
-  int pa[MAX_PAIRS], pb[MAX_PAIRS];    // slice indices of each pass's pair
+  int gstart[MAX_GROUPS + 1];          // pairs gstart[g] .. gstart[g+1]-1 form group g
+  int glevel[MAX_GROUPS];              // a + b of the group's pairs
+  int pa[MAX_PAIRS], pb[MAX_PAIRS];    // slice indices of each pair
   const int* rexp;        // [M] e_i
   const int* cexp;        // [N] f_j
   double2* C;
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long ntiles = (long)p.tm * p.tn;
-  const int passes = p.n_pairs * p.n_kb;
+  const int passes = p.n_groups * p.n_kb;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -150,18 +155,19 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
       int bm, bn;
       tile_of(t, p.tm, p.tn, bm, bn);
       for (int q = 0; q < passes && !*abort_flag; ++q) {
-        const int pr = q / p.n_kb, kb = q - pr * p.n_kb;
-        for (int ks = k_first(kb); ks < k_last(kb); ++ks, ++kit) {
-          const int s = (int)(kit % STAGES);
-          if (kit >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((kit / STAGES) & 1) ^ 1))) {
-            timed_out(31);
-            break;
+        const int g = q / p.n_kb, kb = q - g * p.n_kb;
+        for (int pr = p.gstart[g]; pr < p.gstart[g + 1] && !*abort_flag; ++pr)
+          for (int ks = k_first(kb); ks < k_last(kb); ++ks, ++kit) {
+            const int s = (int)(kit % STAGES);
+            if (kit >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((kit / STAGES) & 1) ^ 1))) {
+              timed_out(31);
+              break;
+            }
+            uint8_t* st = smem + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_3d(st, &mA, &full[s], ks * BK, bm * BM, p.pa[pr]);
+            tma_load_3d(st + A_BYTES, &mB, &full[s], ks * BK, 2 * bn * BNC, p.pb[pr]);
           }
-          uint8_t* st = smem + s * STAGE_BYTES;
-          mbar_expect_tx(&full[s], STAGE_BYTES);
-          tma_load_3d(st, &mA, &full[s], ks * BK, bm * BM, p.pa[pr]);
-          tma_load_3d(st + A_BYTES, &mB, &full[s], ks * BK, 2 * bn * BNC, p.pb[pr]);
-        }
       }
     }
     if (*abort_flag)
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
     bool ok = true;
     for (long t = blockIdx.x; t < ntiles && ok && !*abort_flag; t += gridDim.x) {
       for (int q = 0; q < passes && ok; ++q, ++pc) {
-        const int kb = q % p.n_kb;
+        const int g = q / p.n_kb, kb = q - g * p.n_kb;
         const int b = (int)(pc & 1);
         if (pc >= 2 && !mbar_wait(&tempty[b], (uint32_t)(((pc >> 1) & 1) ^ 1))) {
           timed_out(32);
@@ -185,23 +191,25 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(b * 256);
         const int f = k_first(kb);
-        for (int ks = f; ks < k_last(kb); ++ks, ++kit) {
-          const int s = (int)(kit % STAGES);
-          if (!mbar_wait(&full[s], (uint32_t)((kit / STAGES) & 1))) {
-            timed_out(33);
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          uint8_t* st = smem + s * STAGE_BYTES;
-          const uint64_t ad = sw64_desc(st), bd = sw64_desc(st + A_BYTES);
+        for (int pr = p.gstart[g]; pr < p.gstart[g + 1] && ok; ++pr)
+          for (int ks = f; ks < k_last(kb); ++ks, ++kit) {
+            const int s = (int)(kit % STAGES);
+            if (!mbar_wait(&full[s], (uint32_t)((kit / STAGES) & 1))) {
+              timed_out(33);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            uint8_t* st = smem + s * STAGE_BYTES;
+            const uint64_t ad = sw64_desc(st), bd = sw64_desc(st + A_BYTES);
+            const bool fresh = pr == p.gstart[g] && ks == f;      // first stage of the group's sum
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint64_t off = (uint64_t)(kk * 32) >> 4;
-            umma(d, ad + off, bd + off, idesc, (ks > f || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t off = (uint64_t)(kk * 32) >> 4;
+              umma(d, ad + off, bd + off, idesc, (fresh && kk == 0) ? 0u : 1u);
+            }
+            umma_commit(&empty[s]);
           }
-          umma_commit(&empty[s]);
-        }
         umma_commit(&tfull[b]);
       }
     }
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
       const int r0 = bm * BM + qw * 32;
       const int n0 = bn * BNC;
       for (int q = 0; q < passes; ++q, ++pc) {
-        const int pr = q / p.n_kb;
+        const int g = q / p.n_kb;
         const int b = (int)(pc & 1);
         const bool ok = mbar_wait(&tfull[b], (uint32_t)((pc >> 1) & 1));
         if (!ok) timed_out(34);
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
           go = false;
           break;
         }
-        const int shift = (p.pa[pr] + p.pb[pr] + 2) * BETA;
+        const int shift = (p.glevel[g] + 2) * BETA;
         const float scl = __int_as_float((127 - shift) << 23);    // 2^-shift, exact
         const bool first = q == 0, last = q == passes - 1;
 #pragma unroll 1
@@ -338,16 +346,19 @@ __device__ __forceinline__ uint16_t ihalf(long long s) { return __half_as_ushort
 
 // The S slices of x 2^(beta - e) (|.| < 2^beta): the integer V = rint(x 2^(beta S - e))
 // (one FP64 multiply and conversion; V < 2^(6S) fits 64 bits) written in balanced
-// base 2^beta, V = sum_a s_a 2^(beta (S-1-a)), lower digits s_a in [-32, 32), the top one
-// |s_0| <= 64, all exact in fp16.  Integer digit extraction keeps FP64 work to two operations.
+// base 2^beta, V = sum_a s_a 2^(beta (S-1-a)), lower digits s_a in [-32, 32), the top
+// one |s_0| <= 64, all exact in fp16.  Integer digit extraction keeps FP64 work to two
+// operations.
 template <int S>
 __device__ __forceinline__ void cut(double x, int e, uint16_t (&out)[S]) {
-  long long v = __double2ll_rn(ldexp(x, BETA * S - e));
+  constexpr int beta = BETA;
+  long long v = __double2ll_rn(ldexp(x, beta * S - e));
+  constexpr long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
 #pragma unroll
   for (int a = S - 1; a > 0; --a) {
-    const long long d = ((v + 32) & 63) - 32;
+    const long long d = ((v + half) & mask) - half;
     out[a] = ihalf(d);
-    v = (v - d) >> BETA;          // exact: v - d is a multiple of 64
+    v = (v - d) >> beta;          // exact: v - d is a multiple of 2^beta
   }
   out[0] = ihalf(v);
 }
@@ -470,13 +481,28 @@ gw_status tc_zgemm_sliced(gw_ctx* ctx, int M, int N, int K, const double2* A, lo
   P.N = N;
   P.k_steps = kp / BK;
   P.n_kb = (P.k_steps + KB_STEPS - 1) / KB_STEPS;
-  P.n_pairs = 0;
-  for (int lv = 0; lv <= levels; ++lv)            // largest terms first
+  // pairs level by level (largest terms first), packed into groups whose block sums are
+  // bounded by 2^24 together: log2 bound 24 for (0,0), 23 with one top slice, 22 without
+  int n_pairs = 0;
+  P.n_groups = 0;
+  for (int lv = 0; lv <= levels; ++lv) {
+    long room = 0;                                 // units of 2^22 left in the open group
     for (int a = 0; a <= lv; ++a) {
-      P.pa[P.n_pairs] = a;
-      P.pb[P.n_pairs] = lv - a;
-      ++P.n_pairs;
+      const int b = lv - a;
+      const long need = (a == 0 && b == 0) ? 4 : (a == 0 || b == 0) ? 2 : 1;
+      if (need > room) {                           // open a new group at this pair
+        P.gstart[P.n_groups] = n_pairs;
+        P.glevel[P.n_groups] = lv;
+        ++P.n_groups;
+        room = 4;
+      }
+      room -= need;
+      P.pa[n_pairs] = a;
+      P.pb[n_pairs] = b;
+      ++n_pairs;
     }
+  }
+  P.gstart[P.n_groups] = n_pairs;
   P.tm = (M + BM - 1) / BM;
   P.tn = (N + BNC - 1) / BNC;
   P.rexp = rexp;

@@ -29,7 +29,8 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_chi0_omega", "gw_rr_to_GG_fft_noalloc", "gw_workspace_size", "gw_screen_W_refine", "gw_chi0_omega_kmesh", "gw_sigma_diag_kmesh",
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
            "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau", "gw_mp2_grids",
-           "gw_zgemm_sliced", "gw_batch_plan", "gw_batch_launch", "gw_batch_wait", "gw_batch_destroy"]
+           "gw_zgemm_sliced", "gw_batch_plan", "gw_batch_launch", "gw_batch_wait", "gw_batch_destroy",
+           "gw_chi0_omega_pw"]
 
 
 class GwError(RuntimeError):
@@ -93,6 +94,7 @@ _SIGS = {
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                            _DP, _DP, _DP, _I, _DP, _P]),
     "gw_chi0_omega": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
+    "gw_chi0_omega_pw": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _IP, _I, _P, _P]),
     "gw_sigma_matrix": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                              _DP, _DP, _P]),
     "gw_qp_energies": (_I, [_P, _I, _I, _DP, _DP, _DP, _D, _DP, _I, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
@@ -469,6 +471,17 @@ def chi0_omega(ctx, grid, psi, eps, n_occ, mu, tau, C, fft_index, prec, chi_w, r
     _check(lib().gw_chi0_omega(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p), _dp(eps),
                                float(mu), len(tau), _dp(tau), _dp(C), len(idx), _ip(idx), p, int(r_block),
                                _dev(chi_w, "chi_w", p), _stream()), ctx)
+
+
+def chi0_omega_pw(ctx, grid, psi, eps, n_occ, mu, tau, C, fft_index, pw_index, prec, chi_w):
+    """chi0(G,G',i omega) with G through its plane-wave form (gw_chi0_omega_pw);
+    pw_index: FFT positions of the plane waves spanning the orbitals."""
+    p = prec_of(prec)
+    idx = _i32(fft_index)
+    pw = _i32(pw_index)
+    _check(lib().gw_chi0_omega_pw(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p),
+                                  _dp(_f64(eps)), float(mu), len(tau), _dp(_f64(tau)), _dp(_f64(C)), len(idx), _ip(idx),
+                                  len(pw), _ip(pw), p, _dev(chi_w, "chi_w", p), _stream()), ctx)
 
 
 def chi0_omega_kmesh(ctx, grid, nk, psi_k, eps_k, n_occ, mu, tau, C, gvec, prec, chi_w, r_block=0):
