@@ -12,6 +12,10 @@ tensor-core rate.
     python -m paper_1607_02859_gb300.microbench sliced --n 2048 --levels 4
         the exact sliced complex product of the refinement residual
         (gw_zgemm_sliced); flops 8 n^3 per product.
+    python -m paper_1607_02859_gb300.microbench pwchi --n 36 --bands 256 --n-chi 2048 --tau 2
+        chi0 through the plane-wave form of G (gw_chi0_omega_pw) on an n^3 cell
+        whose orbitals span the lowest `bands` plane waves: the call's time and
+        the row pass's share (its launches are the row-transform family).
 
 Inputs are seeded Gaussian; --reps timed launches follow one untimed launch."""
 from __future__ import annotations
@@ -91,6 +95,34 @@ def sliced(args, ctx):
              "frac_of_sliced_tensor": tf / sliced_peak if sliced_peak else None}]
 
 
+def pwchi(args, ctx):
+    import torch
+    from . import inputs
+    n = (args.n, args.n, args.n)
+    p = inputs.tiny(seed=47, n=n, a=(args.n * 10.26 / 12,) * 3, n_occ=args.bands // 8,
+                    n_unocc=args.bands - args.bands // 8, n_tau=args.tau, n_chi=args.n_chi)
+    grid = gw.make_grid(p.n, p.lattice)
+    _, fidx = gw.g_set(grid, p.n_chi)
+    _, pw = gw.g_set(grid, p.n_b)
+    mats = gw.fit_transform(p.tau, p.omega, p.x_min, p.x_max, p.n_x, p.ridge)
+    psi = torch.from_numpy(p.psi).to("cuda", dtype=torch.complex64)
+    chi = torch.empty((len(p.tau), p.n_chi, p.n_chi), dtype=torch.complex64, device="cuda")
+    gw.chi0_omega_pw(ctx, grid, psi, p.eps, p.n_occ, p.mu, p.tau, mats["C"], fidx, pw, args.prec, chi)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        gw.chi0_omega_pw(ctx, grid, psi, p.eps, p.n_occ, p.mu, p.tau, mats["C"], fidx, pw, args.prec, chi)
+    e1.record()
+    torch.cuda.synchronize()
+    stats = ctx.kernel_stats()
+    ctx.set_timing(False)
+    rows = {k: {"launches": v[0] // args.reps, "ms": v[1] / args.reps} for k, v in stats.items() if v[0]}
+    return [{"kernel": "chi0_omega_pw", "grid": list(n), "bands": p.n_b, "n_chi": p.n_chi, "tau": len(p.tau),
+             "prec": args.prec, "ms_per_call": e0.elapsed_time(e1) / args.reps, "families": rows}]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     sub = ap.add_subparsers(dest="what", required=True)
@@ -104,9 +136,16 @@ def main(argv=None):
     s.add_argument("--n", type=int, default=2048)
     s.add_argument("--levels", type=int, default=4)
     s.add_argument("--reps", type=int, default=3)
+    c = sub.add_parser("pwchi")
+    c.add_argument("--n", type=int, default=36)
+    c.add_argument("--bands", type=int, default=256)
+    c.add_argument("--n-chi", type=int, default=2048)
+    c.add_argument("--tau", type=int, default=2)
+    c.add_argument("--prec", default="f16x3", choices=["fp32", "f16x3", "bf16x3"])
+    c.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
     ctx = gw.Context(0)
-    for line in (row if args.what == "row" else sliced)(args, ctx):
+    for line in {"row": row, "sliced": sliced, "pwchi": pwchi}[args.what](args, ctx):
         print(json.dumps(line))
     ctx.close()
 
