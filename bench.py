@@ -264,9 +264,9 @@ def main():
                     help="rows per r-block of the chi0 pass (default: 4096 on si64, as its recipe streams chi0, "
                          "else the library's default)")
     ap.add_argument("--g-form", default="rr", choices=["rr", "pw"],
-                    help="G of the chi0 pass: rr = real-space contraction on the tensor cores (N_r^2 N_b per "
-                         "tau); pw = plane-wave form over the orbitals' plane waves, then transforms "
-                         "(gw_chi0_omega_pw)")
+                    help="G of the chi0 and Sigma passes: rr = real-space contraction on the tensor cores "
+                         "(N_r^2 N_b per tau); pw = plane-wave form over the orbitals' plane waves, then "
+                         "transforms (gw_chi0_omega_pw, gw_sigma_diag_pw)")
     ap.add_argument("--sigma", default="diag", choices=["diag", "matrix"],
                     help="diag: Sigma_nn, continuation and QP energies; matrix: the full Sigma_nm(i omega)")
     args = ap.parse_args()
@@ -350,8 +350,12 @@ def main():
             mark(5)
             mark(6)
             return out
-        out = gw.sigma_diag(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"], mats["S"],
-                            w_tau, fidx, args.prec, w_real=w_real)
+        if args.g_form == "pw":
+            out = gw.sigma_diag_pw(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"],
+                                   mats["S"], w_tau, fidx, pw_index, args.prec, w_real=w_real)
+        else:
+            out = gw.sigma_diag(ctx, grid, psi_dev, p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"],
+                                mats["S"], w_tau, fidx, args.prec, w_real=w_real)
         mark(4)
         out["qp"] = gw.qp_energies(ctx, p.omega, out["sigma_iw"], eps_n, p.mu, vstat, w=w_real + p.mu)
         mark(5)

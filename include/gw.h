@@ -415,6 +415,27 @@ gw_status gw_chi0_omega_pw(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ,
                            int n_chi, const int32_t* fft_index_h, int n_pw, const int32_t* pw_index_h,
                            gw_prec prec, void* chi_w, void* stream);
 
+/* gw_sigma_diag with G through its plane-wave form (as gw_chi0_omega_pw; same
+ * pw_index_h convention and span check).  Per tau_j: the plane-wave G
+ * formation and its column transform, W~(r, G') from the column transform of
+ * w_tau (Eq. FFTW, first step), then per row r one pass that expands W~(r,.),
+ * G_unocc(r,.) and G_occ(r,.) over R', forms H = W~ G and transforms it back
+ * onto the plane waves, h(r, g) = sum_R' H(r,R') e^{+i g.R'}; with the Sigma
+ * bands' coefficients c_n (psi_n = sum_g c_n(g) e^{+i g.r})
+ *   sum_R' H(r,R') psi_n(R') = sum_g h(r,g) c_n(g)
+ * (a GEMM), and Sigma_nn(+-tau_j) as in gw_sigma_diag (first term of Eq.
+ * Sigma_occ_reduce), then the same transforms and continuation.  Scratch
+ * (context arena): N_r (n_chi + 4 n_pw + 2 n_n) + 2 n_pw^2 + (N_b + n_n) n_pw
+ * elements (8 or 16 bytes) and the tensor-core operands.  GW_ERR_UNSUPPORTED
+ * where the expanded rows do not fit a thread-block cluster (GW_FP64 at 36^3,
+ * every precision at 48^3).  Synchronous. */
+gw_status gw_sigma_diag_pw(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
+                           const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n,
+                           const double* tau_h, const double* omega_h, const double* C_h, const double* S_h,
+                           const void* w_tau, int n_chi, const int32_t* fft_index_h, int n_pw,
+                           const int32_t* pw_index_h, gw_prec prec, double* sigma_tau_h, double* sigma_iw_h,
+                           const double* w_real_h, int n_real, double* sigma_real_h, void* stream);
+
 /* chi0(q+G, q+G', i omega_k) for every q of a Gamma-centred nk[0] x nk[1] x nk[2]
  * k mesh, through the supercell stripe of Sec. II.A (spatial transform within
  * a supercell, Eqs. FFT_G1, FFT_G2): for every tau_j and block of cell rows r,

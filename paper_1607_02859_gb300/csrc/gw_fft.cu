@@ -402,6 +402,12 @@ struct PwRow {
     return in > out ? in : out;
   }
   static size_t smem(int n_pw, int n_chi) { return 2 * plane_bytes(CL) + slice_elems(n_pw, n_chi) * sizeof(C); }
+  // row_pw_sigma_kernel: [T_occ | T_unocc | W~] slices in, hu and ho out over the last two
+  static size_t sig_smem(int n_pw, int n_chi) {
+    const size_t ps = (size_t)((n_pw + CL - 1) / CL), ws = (size_t)((n_chi + CL - 1) / CL);
+    const size_t e = 2 * ps + ws > 3 * ps ? 2 * ps + ws : 3 * ps;
+    return 2 * plane_bytes(CL) + e * sizeof(C);
+  }
 };
 
 template <typename T, int N1, int N2, int N3>
@@ -495,6 +501,135 @@ __global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
   {
     const int j0 = c * n_cs, j1 = min(n_chi, j0 + n_cs);
     for (int j = j0 + threadIdx.x; j < j1; j += TH) out[row * ldo + j] = sx[j - j0];
+  }
+}
+
+// The self-energy's rows in the same plane-wave form (first term of Eq.
+// Sigma_occ_reduce with Eq. Sigma_rr): for each row r, the W~ row over chi's G
+// set (wg, column-transformed, Eq. FFTW) and the rows T_unocc(r, .), T_occ(r, .)
+// of the column-transformed plane-wave G are expanded over the grid R'; then
+//   H(r,R') = W~(r,R') G(r,R') = W~ conj(G')            (G' the expanded T row)
+// is transformed forward and gathered on the orbitals' plane waves,
+//   hu / ho(r, g) = sum_R' H(r,R') e^{+i g.R'},
+// so that sum_R' H(r,R') psi_n(R') = sum_g hu(r,g) c_n(g) needs only the
+// plane-wave coefficients c_n of the Sigma bands.  Five transforms per row, W~
+// kept expanded in the first plane buffer while the second takes G_unocc, then
+// G_occ.  inv_neg: grid position -> index into the T rows (the negated set),
+// inv_nat: grid position -> plane-wave index of the outputs, inv_chi: the G set.
+template <typename T, int N1, int N2, int N3>
+__global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
+    row_pw_sigma_kernel(const typename cpx<T>::t* __restrict__ tu, const typename cpx<T>::t* __restrict__ to,
+                        long ldt, const typename cpx<T>::t* __restrict__ wg, long ldw,
+                        typename cpx<T>::t* __restrict__ hu, typename cpx<T>::t* __restrict__ ho, long ldh,
+                        const int* __restrict__ inv_neg, const int* __restrict__ inv_nat, int n_pw,
+                        const int* __restrict__ inv_chi, int n_chi) {
+  namespace cg = cooperative_groups;
+  using C = typename cpx<T>::t;
+  using R = PwRow<T, N1, N2, N3>;
+  constexpr int P = R::P, PL = R::PL, S2 = R::S2, COLS = R::COLS, CL = R::CL;
+  constexpr int TH = R::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sa = reinterpret_cast<C*>(smem_raw);                              // W~ planes
+  C* sb = reinterpret_cast<C*>(smem_raw + R::plane_bytes(CL));         // G', then H planes
+  C* sl = reinterpret_cast<C*>(smem_raw + 2 * R::plane_bytes(CL));
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (int)cluster.block_rank();
+  const long row = blockIdx.y;
+  const int n_ps = (n_pw + CL - 1) / CL, n_ws = (n_chi + CL - 1) / CL;
+  // slices: [T_occ | T_unocc | W~]; outputs hu over T_unocc's, ho from 2 n_ps (both read by then)
+  C* so_in = sl;
+  C* su_in = sl + n_ps;
+  C* sw = sl + 2 * n_ps;
+  C* hu_s = sl + n_ps;
+  C* ho_s = sl + 2 * n_ps;
+  {
+    const int j0 = c * n_ps, j1 = min(n_pw, j0 + n_ps);
+    for (int j = j0 + threadIdx.x; j < j1; j += TH) {
+      su_in[j - j0] = tu[row * ldt + j];
+      so_in[j - j0] = to[row * ldt + j];
+    }
+    const int w0 = c * n_ws, w1 = min(n_chi, w0 + n_ws);
+    for (int j = w0 + threadIdx.x; j < w1; j += TH) sw[j - w0] = wg[row * ldw + j];
+  }
+  cluster.sync();
+  // backward i1 transforms of a slice-held row into every CTA's planes
+  auto line_bwd = [&](const C* src, int ns, const int* inv, C* dst) {
+    for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
+      const int i2 = q / N3, i3 = q - i2 * N3;
+      C x[N1];
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        const int j = __ldg(inv + i1 * PL + q);
+        x[i1] = mk(T(0), T(0));
+        if (j >= 0) {
+          const int o = j / ns;
+          x[i1] = cluster.map_shared_rank(src, o)[j - o * ns];
+        }
+      }
+      RegFFT<N1, -1>::run(x);
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1)
+        cluster.map_shared_rank(dst, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3] = x[i1];
+    }
+  };
+  // forward i1 transforms of every CTA's H planes, gathered on the plane-wave set
+  auto line_fwd = [&](C* out) {
+    for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
+      const int i2 = q / N3, i3 = q - i2 * N3;
+      C x[N1];
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) x[i1] = cluster.map_shared_rank(sb, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3];
+      RegFFT<N1, +1>::run(x);
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        const int j = __ldg(inv_nat + i1 * PL + q);
+        if (j >= 0) {
+          const int o = j / n_ps;
+          cluster.map_shared_rank(out, o)[j - o * n_ps] = x[i1];
+        }
+      }
+    }
+  };
+  auto planes_bwd = [&](C* buf) {
+    pencil_pass<N3, -1>(buf, P * N2, 1, [](int q) { return q * S2; });
+    __syncthreads();
+    pencil_pass<N2, -1>(buf, P * N3, S2, [](int q) { return (q / N3) * (N2 * S2) + (q % N3); });
+    __syncthreads();
+  };
+  // H = W~ conj(G') on the CTA's planes, then the forward (i2, i3) transforms
+  auto product_fwd = [&]() {
+    for (int e = threadIdx.x; e < P * PL; e += TH) {
+      const int p = e / PL, rem = e - p * PL, i2 = rem / N3;
+      const int ps = (p * N2 + i2) * S2 + (rem - i2 * N3);
+      sb[ps] = cmulc(sa[ps], sb[ps]);
+    }
+    __syncthreads();
+    pencil_pass<N2, +1>(sb, P * N3, S2, [](int q) { return (q / N3) * (N2 * S2) + (q % N3); });
+    __syncthreads();
+    pencil_pass<N3, +1>(sb, P * N2, 1, [](int q) { return q * S2; });
+  };
+  line_bwd(sw, n_ws, inv_chi, sa);
+  line_bwd(su_in, n_ps, inv_neg, sb);
+  cluster.sync();                  // W~ and G'_unocc planes complete; W~ and T_unocc slices free
+  planes_bwd(sa);
+  planes_bwd(sb);
+  product_fwd();
+  cluster.sync();                  // H_unocc planes final
+  line_fwd(hu_s);
+  cluster.sync();                  // hu complete; the second buffer free
+  line_bwd(so_in, n_ps, inv_neg, sb);
+  cluster.sync();
+  planes_bwd(sb);
+  product_fwd();
+  cluster.sync();
+  line_fwd(ho_s);
+  cluster.sync();                  // no remote access after this point
+  {
+    const int j0 = c * n_ps, j1 = min(n_pw, j0 + n_ps);
+    for (int j = j0 + threadIdx.x; j < j1; j += TH) {
+      hu[row * ldh + j] = hu_s[j - j0];
+      ho[row * ldh + j] = ho_s[j - j0];
+    }
   }
 }
 
@@ -916,6 +1051,43 @@ struct GridOps {
       return fail(ctx, GW_ERR_UNSUPPORTED, "plane-wave chi rows: no cluster split fits this grid and precision");
     }
   }
+  static bool row_pw_sigma_ok(int n_pw, int n_chi) {
+    using PR = PwRow<T, N1, N2, N3>;
+    if constexpr (PR::CL > 0) return PR::sig_smem(n_pw, n_chi) <= kRowSmemMax;
+    return false;
+  }
+  static gw_status row_pw_sigma(gw_ctx* ctx, const void* tu, const void* to, long ldt, const void* wg, long ldw,
+                                void* hu, void* ho, long ldh, const int* inv_neg, const int* inv_nat, int n_pw,
+                                const int* inv_chi, int n_chi, int n_rows, cudaStream_t st) {
+    using PR = PwRow<T, N1, N2, N3>;
+    if constexpr (PR::CL > 0) {
+      const size_t bytes = PR::sig_smem(n_pw, n_chi);
+      if (bytes > kRowSmemMax) return fail(ctx, GW_ERR_UNSUPPORTED, "plane-wave Sigma rows: G sets too large");
+      auto kernel = row_pw_sigma_kernel<T, N1, N2, N3>;
+      gw_status s = set_smem(ctx, kernel, bytes);
+      if (s) return s;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(PR::CL, (unsigned)n_rows);
+      cfg.blockDim = dim3(PR::THREADS);
+      cfg.dynamicSmemBytes = bytes;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = PR::CL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (4.0 * n_pw + n_chi) * sizeof(C), st);
+      s = cuda_check(ctx, cudaLaunchKernelEx(&cfg, kernel, (const C*)tu, (const C*)to, ldt, (const C*)wg, ldw, (C*)hu,
+                                             (C*)ho, ldh, inv_neg, inv_nat, n_pw, inv_chi, n_chi),
+                     "cudaLaunchKernelEx(row_pw_sigma_kernel)");
+      if (s) return s;
+      return launch_check(ctx, "row_pw_sigma_kernel");
+    } else {
+      return fail(ctx, GW_ERR_UNSUPPORTED, "plane-wave Sigma rows: no cluster split fits this grid and precision");
+    }
+  }
   static gw_status plane(gw_ctx* ctx, int dir, void* buf, long ld, int ncols, double scale, cudaStream_t st) {
     const size_t bytes = (size_t)N2 * N3 * kPlaneW * sizeof(C);
     dim3 grid((ncols + kPlaneW - 1) / kPlaneW, N1);
@@ -1025,6 +1197,22 @@ gw_status check_row_pw(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int n_pw, i
   GW_DISPATCH(prec, g, rc = O::row_pw_ok(n_pw, n_chi) ? GW_OK : fail(ctx, GW_ERR_UNSUPPORTED,
                                                                      "plane-wave chi rows: this grid, precision and "
                                                                      "G sets do not fit a thread-block cluster"))
+}
+
+gw_status launch_row_pw_sigma(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* tu, const void* to, long ldt,
+                              const void* wg, long ldw, void* hu, void* ho, long ldh, const int* inv_neg,
+                              const int* inv_nat, int n_pw, const int* inv_chi, int n_chi, int n_rows,
+                              cudaStream_t st) {
+  if (n_rows <= 0) return GW_OK;
+  GW_DISPATCH(prec, g, rc = O::row_pw_sigma(ctx, tu, to, ldt, wg, ldw, hu, ho, ldh, inv_neg, inv_nat, n_pw, inv_chi,
+                                            n_chi, n_rows, st))
+}
+
+gw_status check_row_pw_sigma(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int n_pw, int n_chi) {
+  GW_DISPATCH(prec, g, rc = O::row_pw_sigma_ok(n_pw, n_chi) ? GW_OK : fail(ctx, GW_ERR_UNSUPPORTED,
+                                                                           "plane-wave Sigma rows: this grid, "
+                                                                           "precision and G sets do not fit a "
+                                                                           "thread-block cluster"))
 }
 
 bool row_two_pass(const GridInfo& g, gw_prec prec) {

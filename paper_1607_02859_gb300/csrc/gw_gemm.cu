@@ -144,6 +144,7 @@ static gw_status run_gemm(gw_ctx* ctx, const GemmArgs& a, cudaStream_t st) {
   GW_GEMM_CASE(0, false, 0, false, false, 0)  // triangular-inverse update: C -= L_below X_i
   GW_GEMM_CASE(1, true, 0, false, false, 2)   // L^{-H} L^{-1}, lower triangle
   GW_GEMM_CASE(0, false, 0, false, false, 1)
+  GW_GEMM_CASE(0, false, 1, true, false, 0)   // A B^H (plane-wave self-energy: h c^H)
 #undef GW_GEMM_CASE
   return fail(ctx, GW_ERR_UNSUPPORTED, "GEMM layout combination not compiled");
 }

@@ -22,6 +22,26 @@ gw_status launch_row_pw_chi(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const 
                             int n_rows, double scale, cudaStream_t st);
 // GW_OK if launch_row_pw_chi supports the grid, precision and set sizes.
 gw_status check_row_pw(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int n_pw, int n_chi);
+// Sigma rows in the plane-wave form: tu, to [n_rows][ldt] (T rows over the negated
+// plane-wave set), wg [n_rows][ldw] (W~ over chi's G set) -> hu, ho [n_rows][ldh] =
+// FFT+(W~ conj(G')) gathered on the plane-wave set (inv_nat).
+gw_status launch_row_pw_sigma(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* tu, const void* to, long ldt,
+                              const void* wg, long ldw, void* hu, void* ho, long ldh, const int* inv_neg,
+                              const int* inv_nat, int n_pw, const int* inv_chi, int n_chi, int n_rows,
+                              cudaStream_t st);
+gw_status check_row_pw_sigma(gw_ctx* ctx, const GridInfo& g, gw_prec prec, int n_pw, int n_chi);
+
+// gw_pipeline.cu: the plane-wave form of G.  pw_negate turns the FFT positions
+// of the orbitals' plane waves e^{+i g.r} into those of -g (where the forward
+// coefficients sit) and rebuilds inv; pw_coefficients writes
+// dc [n_b][n_pw] = conj(D)/N_r, D_a = sum_r psi_a(r) e^{+i g'.r} at the negated set,
+// after checking (one synchronisation) that every band lies in the set's span;
+// pw_grid is the GridInfo of the G formation over the set.
+void pw_negate(const GridInfo& g, std::vector<int>& map, std::vector<int>& inv);
+gw_status pw_coefficients(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* psi, int n_b, int n_pw,
+                          const int* dmap_neg, const int* dinv_neg, void* dc, double* dnorm, void* tmp,
+                          cudaStream_t s);
+GridInfo pw_grid(const GridInfo& g, int n_pw);
 
 // gw_sigma.cu: the Sigma contraction over rows of G_occ, G_unocc, W~ (length
 // nr, leading dimension ld) against psi_n (rows of length nr; the row's own

@@ -252,10 +252,51 @@ __global__ void __launch_bounds__(256) band_norms_kernel(const C* __restrict__ p
   }
 }
 
-static GridInfo pw_grid(const GridInfo& g, int n_pw) {
+GridInfo pw_grid(const GridInfo& g, int n_pw) {
   GridInfo q = g;                 // the G formation over the plane-wave set: n_pw "points"
   q.nr = n_pw;
   return q;
+}
+
+void pw_negate(const GridInfo& g, std::vector<int>& map, std::vector<int>& inv) {
+  // psi = sum_g c(g) e^{+i g.r}: D(g') = sum_r psi e^{+i g'.r} is nonzero at g' = -g
+  for (auto& q : map) {
+    const int i1 = q / (g.n2 * g.n3), i2 = (q / g.n3) % g.n2, i3 = q % g.n3;
+    q = (((g.n1 - i1) % g.n1) * g.n2 + (g.n2 - i2) % g.n2) * g.n3 + (g.n3 - i3) % g.n3;
+  }
+  std::fill(inv.begin(), inv.end(), -1);
+  for (size_t j = 0; j < map.size(); ++j) inv[map[j]] = (int)j;
+}
+
+gw_status pw_coefficients(gw_ctx* ctx, const GridInfo& g, gw_prec prec, const void* psi, int n_b, int n_pw,
+                          const int* dmap_neg, const int* dinv_neg, void* dc, double* dnorm, void* tmp,
+                          cudaStream_t s) {
+  gw_status st;
+  if ((st = launch_row_fft(ctx, g, prec, 1, psi, nullptr, g.nr, dc, n_pw, dmap_neg, n_pw, n_b, 1.0, s, dinv_neg, tmp)))
+    return st;
+  if (is_fp64(prec))
+    band_norms_kernel<double2><<<n_b, 256, 0, s>>>((const double2*)psi, g.nr, (const double2*)dc, n_pw, dnorm);
+  else
+    band_norms_kernel<float2><<<n_b, 256, 0, s>>>((const float2*)psi, g.nr, (const float2*)dc, n_pw, dnorm);
+  if ((st = launch_check(ctx, "band_norms_kernel"))) return st;
+  std::vector<double> nh(2 * (size_t)n_b);
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(nh.data(), dnorm, sizeof(double) * 2 * n_b, cudaMemcpyDeviceToHost, s),
+                       "norms")))
+    return st;
+  if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
+  // Parseval: sum_g |D(g)|^2 = N_r sum_r |psi(r)|^2 when psi lies in the set's span
+  const double tol = is_fp64(prec) ? 1e-10 : 1e-5;
+  for (int b = 0; b < n_b; ++b) {
+    const double full = nh[2 * b] * g.nr, part = nh[2 * b + 1];
+    if (!(std::fabs(full - part) <= tol * full))
+      return fail(ctx, GW_ERR_ARG, "band " + std::to_string(b) + " is not in the span of the plane waves of pw_index "
+                                   "(fraction " + std::to_string(full > 0 ? part / full : 0.0) + ")");
+  }
+  const size_t nel = (size_t)n_b * n_pw;
+  const int blocks = (int)std::min<size_t>((nel + 255) / 256, (size_t)ctx->num_sms * 8);
+  if (is_fp64(prec)) conj_scale_kernel<<<blocks, 256, 0, s>>>((double2*)dc, nel, 1.0 / g.nr);
+  else conj_scale_kernel<<<blocks, 256, 0, s>>>((float2*)dc, nel, (float)(1.0 / g.nr));
+  return launch_check(ctx, "conj_scale_kernel");
 }
 
 size_t chi0_pw_scratch(const GridInfo& g, int n_b, int n_occ, int n, int n_chi, int n_pw, gw_prec prec) {
@@ -296,13 +337,7 @@ extern "C" gw_status gw_chi0_omega_pw(gw_ctx* ctx, const gw_grid* grid, int n_b,
   std::vector<int> map, inv, map_pw, inv_pw;
   if ((st = index_maps(ctx, g, fft_index_h, n_chi, map, inv))) return st;
   if ((st = index_maps(ctx, g, pw_index_h, n_pw, map_pw, inv_pw))) return st;
-  // psi = sum_g c(g) e^{+i g.r}: the coefficients D(g) = sum_r psi e^{+i g'.r} sit at g' = -g
-  for (int j = 0; j < n_pw; ++j) {
-    const int q = map_pw[j], i1 = q / (g.n2 * g.n3), i2 = (q / g.n3) % g.n2, i3 = q % g.n3;
-    map_pw[j] = (((g.n1 - i1) % g.n1) * g.n2 + (g.n2 - i2) % g.n2) * g.n3 + (g.n3 - i3) % g.n3;
-  }
-  std::fill(inv_pw.begin(), inv_pw.end(), -1);
-  for (int j = 0; j < n_pw; ++j) inv_pw[map_pw[j]] = j;
+  pw_negate(g, map_pw, inv_pw);
   if ((st = check_row_pw(ctx, g, prec, n_pw, n_chi))) return st;
   cudaStream_t s = as_stream(stream);
   const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
@@ -340,36 +375,7 @@ extern "C" gw_status gw_chi0_omega_pw(gw_ctx* ctx, const gw_grid* grid, int n_b,
   if (!tc)
     for (int j = 0; j < n; ++j)
       if ((st = upload_scales(ctx, dscale + (size_t)j * n_b * 8, scales[j], prec, s))) return st;
-  // plane-wave coefficients D_a(g) of every band, and the check that they hold all of psi
-  if ((st = launch_row_fft(ctx, g, prec, 1, psi, nullptr, g.nr, dc, n_pw, dmap_pw, n_pw, n_b, 1.0, s, dinv_pw, tmp)))
-    return st;
-  if (is_fp64(prec))
-    band_norms_kernel<double2><<<n_b, 256, 0, s>>>((const double2*)psi, g.nr, (const double2*)dc, n_pw, dnorm);
-  else
-    band_norms_kernel<float2><<<n_b, 256, 0, s>>>((const float2*)psi, g.nr, (const float2*)dc, n_pw, dnorm);
-  if ((st = launch_check(ctx, "band_norms_kernel"))) return st;
-  {
-    std::vector<double> nh(2 * (size_t)n_b);
-    if ((st = cuda_check(ctx, cudaMemcpyAsync(nh.data(), dnorm, sizeof(double) * 2 * n_b, cudaMemcpyDeviceToHost, s),
-                         "norms")))
-      return st;
-    if ((st = cuda_check(ctx, cudaStreamSynchronize(s), "sync"))) return st;
-    // Parseval: sum_g |D(g)|^2 = N_r sum_r |psi(r)|^2 when psi lies in the set's span
-    const double tol = is_fp64(prec) ? 1e-10 : 1e-5;
-    for (int b = 0; b < n_b; ++b) {
-      const double full = nh[2 * b] * g.nr, part = nh[2 * b + 1];
-      if (!(std::fabs(full - part) <= tol * full))
-        return fail(ctx, GW_ERR_ARG, "band " + std::to_string(b) + " is not in the span of the plane waves of pw_index "
-                                     "(fraction " + std::to_string(full > 0 ? part / full : 0.0) + ")");
-    }
-  }
-  {
-    const size_t nel = (size_t)n_b * n_pw;
-    const int blocks = (int)std::min<size_t>((nel + 255) / 256, (size_t)ctx->num_sms * 8);
-    if (is_fp64(prec)) conj_scale_kernel<<<blocks, 256, 0, s>>>((double2*)dc, nel, 1.0 / g.nr);
-    else conj_scale_kernel<<<blocks, 256, 0, s>>>((float2*)dc, nel, (float)(1.0 / g.nr));
-    if ((st = launch_check(ctx, "conj_scale_kernel"))) return st;
-  }
+  if ((st = pw_coefficients(ctx, g, prec, psi, n_b, n_pw, dmap_pw, dinv_pw, dc, dnorm, tmp, s))) return st;
   bool first = true;
   for (int j = 0; j < n; ++j) {
     // Mc_occ, Mc_unocc over the plane-wave set, then their column transforms T(r, g')

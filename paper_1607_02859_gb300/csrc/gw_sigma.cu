@@ -777,6 +777,184 @@ extern "C" gw_status gw_sigma_matrix(gw_ctx* ctx, const gw_grid* grid, int n_b, 
                     fft_index_h, prec, true, sigma_tau_h, sigma_iw_h, nullptr, 0, nullptr, as_stream(stream));
 }
 
+// ------------------------------------------------------------------ plane-wave form of G
+//
+// Sigma_nn(tau) with G through its plane-wave form (as gw_chi0_omega_pw): per
+// tau, M = Dc F Dc^H over the orbitals' plane waves and its column transform
+// T(r, g'), W~(r, G') by the column transform of W~(G, G') (Eq. FFTW, first
+// step), then per row the kernel that expands W~, G_unocc and G_occ over R',
+// forms H = W~ G and transforms H back onto the plane waves (hu, ho);
+//   V_n(r) = sum_R' H(r,R') psi_n(R') = sum_g h(r,g) c_n(g)          (c_n = conj(Dc) rows)
+// is a GEMM against the Sigma bands' coefficients, and
+//   Sigma_unocc_nn(tau) += coef sum_r Re(conj(psi_n(r)) V^unocc_n(r)),  Sigma_occ_nn(-tau) -= ... V^occ,
+// as the fused tensor-core pass does (first term of Eq. Sigma_occ_reduce).
+
+namespace gw {
+
+template <typename C>
+__global__ void gather_rows_kernel(const C* __restrict__ src, long ld, const int* __restrict__ rows, int len,
+                                   C* __restrict__ dst) {
+  const long r = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x)
+    dst[r * len + j] = src[(long)rows[r] * ld + j];
+}
+
+// acc[n * stride] += coef sum_r Re(conj(psi_{bands[n]}(r)) V[r][n]); CTAs split the rows, FP64 sums.
+template <typename C>
+__global__ void __launch_bounds__(256) sigma_pw_reduce_kernel(const C* __restrict__ V, int n_n,
+                                                              const C* __restrict__ psi, long nr,
+                                                              const int* __restrict__ bands, double coef,
+                                                              double* __restrict__ acc, int stride) {
+  __shared__ double red[8];
+  const int n = blockIdx.y;
+  const C* pn = psi + (long)bands[n] * nr;
+  double s = 0;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
+    const C p = pn[r], v = V[r * n_n + n];
+    s += (double)p.x * v.x + (double)p.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(acc + (long)n * stride, coef * t);
+  }
+}
+
+}  // namespace gw
+
+extern "C" gw_status gw_sigma_diag_pw(gw_ctx* ctx, const gw_grid* grid, int n_b, int n_occ, const void* psi,
+                                      const double* eps_h, double mu, const int32_t* bands_h, int n_n, int n,
+                                      const double* tau_h, const double* omega_h, const double* C_h, const double* S_h,
+                                      const void* w_tau, int n_chi, const int32_t* fft_index_h, int n_pw,
+                                      const int32_t* pw_index_h, gw_prec prec, double* sigma_tau_h,
+                                      double* sigma_iw_h, const double* w_real_h, int n_real, double* sigma_real_h,
+                                      void* stream) {
+  GridInfo g;
+  std::vector<int> map, inv;
+  std::vector<GreenScales> scales;
+  gw_status st = sigma_check(ctx, grid, &g, n_b, n_occ, psi, eps_h, mu, bands_h, n_n, n, tau_h, omega_h, C_h, S_h,
+                             w_tau, n_chi, fft_index_h, prec, false, w_real_h, n_real, map, inv, scales);
+  if (st) return st;
+  if (!sigma_iw_h || (n_real > 0 && !sigma_real_h)) return fail(ctx, GW_ERR_ARG, "NULL output pointer");
+  std::vector<int> map_nat, inv_nat;
+  if ((st = index_maps(ctx, g, pw_index_h, n_pw, map_nat, inv_nat))) return st;
+  std::vector<int> map_neg = map_nat, inv_neg = inv_nat;
+  pw_negate(g, map_neg, inv_neg);
+  if ((st = check_row_pw_sigma(ctx, g, prec, n_pw, n_chi))) return st;
+  cudaStream_t s = as_stream(stream);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  const size_t es = csize(prec);
+  const GridInfo gp = pw_grid(g, n_pw);
+  SigmaTables t;
+  int *dmap_neg = nullptr, *dinv_neg = nullptr, *dinv_nat = nullptr;
+  double* dnorm = nullptr;
+  char *dc = nullptr, *cn = nullptr, *mo = nullptr, *mu_ = nullptr, *to = nullptr, *tu = nullptr, *wg = nullptr;
+  char *hu = nullptr, *ho = nullptr, *vu = nullptr, *vo = nullptr, *tmp = nullptr;
+  void* tcs = nullptr;
+  auto carve = [&](Carver& cv) {
+    sigma_carve_tables(cv, g, n_b, n, n_chi, n_n, n_real, false, t);
+    dmap_neg = cv.take<int>(n_pw);
+    dinv_neg = cv.take<int>(g.nr);
+    dinv_nat = cv.take<int>(g.nr);
+    dnorm = cv.take<double>(2 * (size_t)n_b);
+    dc = cv.take<char>((size_t)n_b * n_pw * es);
+    cn = cv.take<char>((size_t)n_n * n_pw * es);
+    mo = cv.take<char>((size_t)n_pw * n_pw * es);
+    mu_ = cv.take<char>((size_t)n_pw * n_pw * es);
+    to = cv.take<char>((size_t)g.nr * n_pw * es);
+    tu = cv.take<char>((size_t)g.nr * n_pw * es);
+    wg = cv.take<char>((size_t)g.nr * n_chi * es);
+    hu = cv.take<char>((size_t)g.nr * n_pw * es);
+    ho = cv.take<char>((size_t)g.nr * n_pw * es);
+    vu = cv.take<char>((size_t)g.nr * n_n * es);
+    vo = cv.take<char>((size_t)g.nr * n_n * es);
+    tmp = row_two_pass(g, prec) && is_fp64(prec) ? cv.take<char>((size_t)n_b * g.nr * es) : nullptr;
+    tcs = tc ? cv.take<char>(tc_scratch_bytes(gp, n_b, n_occ, n_pw, false)) : nullptr;
+  };
+  {
+    Carver probe(nullptr);
+    carve(probe);
+    if ((st = reserve(ctx, probe.off))) return st;
+  }
+  Carver cv(ctx->arena);
+  carve(cv);
+  if ((st = sigma_upload_tables(ctx, t, g, n_b, n, n_chi, map, inv, bands_h, n_n, scales, C_h, S_h, omega_h, w_real_h,
+                                n_real, prec, s)))
+    return st;
+  if ((st = upload(ctx, dmap_neg, map_neg.data(), sizeof(int) * n_pw, s))) return st;
+  if ((st = upload(ctx, dinv_neg, inv_neg.data(), sizeof(int) * g.nr, s))) return st;
+  if ((st = upload(ctx, dinv_nat, inv_nat.data(), sizeof(int) * g.nr, s))) return st;
+  if ((st = pw_coefficients(ctx, g, prec, psi, n_b, n_pw, dmap_neg, dinv_neg, dc, dnorm, tmp, s))) return st;
+  {
+    const dim3 gg((n_pw + 255) / 256, n_n);
+    if (is_fp64(prec)) gather_rows_kernel<<<gg, 256, 0, s>>>((const double2*)dc, n_pw, t.bands, n_pw, (double2*)cn);
+    else gather_rows_kernel<<<gg, 256, 0, s>>>((const float2*)dc, n_pw, t.bands, n_pw, (float2*)cn);
+    if ((st = launch_check(ctx, "gather_rows_kernel"))) return st;
+  }
+  const size_t acc_elems = (size_t)n_n * n;
+  if ((st = cuda_check(ctx, cudaMemsetAsync(t.acc2, 0, sizeof(double2) * acc_elems, s), "memset"))) return st;
+  double* acc_u = reinterpret_cast<double*>(t.acc2);
+  double* acc_o = acc_u + (size_t)n_n * n;
+  const double coef = g.dv * g.dv / g.volume;   // dV^2 and the 1/Omega of Eq. FFTW
+  bool first = true;
+  for (int j = 0; j < n; ++j) {
+    const char* sj = t.scale + (size_t)j * n_b * 8;
+    if (tc) {
+      st = tc_green_rows(ctx, gp, n_b, n_occ, dc, scales[j], 0, n_pw, prec, mo, mu_, tcs, first, s,
+                         reinterpret_cast<const float*>(sj));
+      first = false;
+    } else {
+      st = green_rows(ctx, gp, n_b, n_occ, dc, sj, scales[j], 0, n_pw, prec, mo, mu_, s);
+    }
+    if (st) return st;
+    for (int part = 0; part < 2; ++part) {
+      char* m = part ? mu_ : mo;
+      char* tt = part ? tu : to;
+      if ((st = launch_col_line(ctx, g, prec, +1, 1, m, n_pw, tt, n_pw, n_pw, dinv_neg, 1.0, s))) return st;
+      if ((st = launch_col_plane(ctx, g, prec, +1, tt, n_pw, n_pw, 1.0, s))) return st;
+    }
+    const char* wj = static_cast<const char*>(w_tau) + (size_t)j * n_chi * n_chi * es;
+    if ((st = launch_col_line(ctx, g, prec, +1, 1, wj, n_chi, wg, n_chi, n_chi, t.inv, 1.0, s))) return st;
+    if ((st = launch_col_plane(ctx, g, prec, +1, wg, n_chi, n_chi, 1.0, s))) return st;
+    if ((st = launch_row_pw_sigma(ctx, g, prec, tu, to, n_pw, wg, n_chi, hu, ho, n_pw, dinv_neg, dinv_nat, n_pw, t.inv,
+                                  n_chi, g.nr, s)))
+      return st;
+    for (int part = 0; part < 2; ++part) {
+      GemmArgs a{};
+      a.M = g.nr;
+      a.N = n_n;
+      a.K = n_pw;
+      a.alpha_re = 1.0;
+      a.A = part ? ho : hu;
+      a.lda = n_pw;
+      a.a_km = 0;
+      a.B = cn;
+      a.ldb = n_pw;
+      a.b_nk = 1;
+      a.b_conj = true;                 // c_n(g) = conj(Dc[band][g])
+      a.C = part ? vo : vu;
+      a.ldc = n_n;
+      if ((st = launch_gemm(ctx, prec, a, s))) return st;
+      const dim3 gr((unsigned)std::min<long>((g.nr + 255) / 256, 64), n_n);
+      double* acc = (part ? acc_o : acc_u) + j;
+      const double cf = part ? -coef : coef;
+      if (is_fp64(prec))
+        sigma_pw_reduce_kernel<<<gr, 256, 0, s>>>((const double2*)a.C, n_n, (const double2*)psi, g.nr, t.bands, cf,
+                                                  acc, n);
+      else
+        sigma_pw_reduce_kernel<<<gr, 256, 0, s>>>((const float2*)a.C, n_n, (const float2*)psi, g.nr, t.bands, cf,
+                                                  acc, n);
+      if ((st = launch_check(ctx, "sigma_pw_reduce_kernel"))) return st;
+    }
+  }
+  if ((st = sigma_finish_launch(ctx, acc_u, n_n, n, t.tab, n_real, t.out, t.stat, s))) return st;
+  if (tc && (st = tc_check(ctx, tcs, s))) return st;
+  return sigma_fetch(ctx, acc_u, n_n, n, n_real, t.out, t.stat, bands_h, sigma_tau_h, sigma_iw_h, sigma_real_h, s);
+}
+
 extern "C" gw_status gw_qp_energies(gw_ctx* ctx, int n_n, int n, const double* omega_h, const double* sigma_iw_h,
                                     const double* eps_h, double mu, const double* vstat_h, int n_w, const double* w_h,
                                     double* e_qp_h, double* z_h, double* sigma_eps_h, double* dsigma_h,

@@ -30,7 +30,7 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
            "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau", "gw_mp2_grids",
            "gw_zgemm_sliced", "gw_batch_plan", "gw_batch_launch", "gw_batch_wait", "gw_batch_destroy",
-           "gw_chi0_omega_pw"]
+           "gw_chi0_omega_pw", "gw_sigma_diag_pw"]
 
 
 class GwError(RuntimeError):
@@ -95,6 +95,8 @@ _SIGS = {
                            _DP, _DP, _DP, _I, _DP, _P]),
     "gw_chi0_omega": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
     "gw_chi0_omega_pw": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _IP, _I, _P, _P]),
+    "gw_sigma_diag_pw": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I, _IP,
+                              _I, _DP, _DP, _DP, _I, _DP, _P]),
     "gw_sigma_matrix": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                              _DP, _DP, _P]),
     "gw_qp_energies": (_I, [_P, _I, _I, _DP, _DP, _DP, _D, _DP, _I, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
@@ -396,6 +398,32 @@ def sigma_diag(ctx, grid, psi, eps, n_occ, mu, bands, tau, omega, C, S, w_tau, f
                              s_iw.ctypes.data_as(_DP), _dp(wr), n_real,
                              s_re.ctypes.data_as(_DP) if n_real else None, _stream())
     _check(st, ctx)
+    out = {"sigma_unocc": s_tau[0], "sigma_occ": s_tau[1], "sigma_iw": s_iw}
+    if n_real:
+        out["sigma_real"] = s_re
+    return out
+
+
+def sigma_diag_pw(ctx, grid, psi, eps, n_occ, mu, bands, tau, omega, C, S, w_tau, fft_index, pw_index, prec,
+                  w_real=None):
+    """gw_sigma_diag with G through its plane-wave form (gw_sigma_diag_pw); same outputs as sigma_diag."""
+    p = prec_of(prec)
+    bands = _i32(bands)
+    tau = _f64(tau)
+    idx = _i32(fft_index)
+    pw = _i32(pw_index)
+    n = len(tau)
+    n_n = len(bands)
+    s_tau = np.zeros((2, n_n, n))
+    s_iw = np.zeros((n_n, n), dtype=np.complex128)
+    wr = None if w_real is None else _f64(w_real)
+    n_real = 0 if wr is None else len(wr)
+    s_re = np.zeros((n_n, max(n_real, 1)), dtype=np.complex128)
+    _check(lib().gw_sigma_diag_pw(ctx.handle, ct.byref(grid), psi.shape[0], int(n_occ), _dev(psi, "psi", p),
+                                  _dp(_f64(eps)), float(mu), _ip(bands), n_n, n, _dp(tau), _dp(_f64(omega)),
+                                  _dp(_f64(C)), _dp(_f64(S)), _dev(w_tau, "w_tau", p), len(idx), _ip(idx), len(pw),
+                                  _ip(pw), p, _dp(s_tau), s_iw.ctypes.data_as(_DP), _dp(wr), n_real,
+                                  s_re.ctypes.data_as(_DP) if n_real else None, _stream()), ctx)
     out = {"sigma_unocc": s_tau[0], "sigma_occ": s_tau[1], "sigma_iw": s_iw}
     if n_real:
         out["sigma_real"] = s_re

@@ -1,11 +1,13 @@
-"""chi0(G,G',i omega) with G through its plane-wave form (gw_chi0_omega_pw):
+"""chi0(G,G',i omega) and Sigma_nn(i omega) with G through its plane-wave form
+(gw_chi0_omega_pw, gw_sigma_diag_pw).  chi0:
 the G formation over the orbitals' plane-wave set, its column transform over
 the grid, and the row pass that expands G_occ and G_unocc over R', multiplies
 them (Eq. chi_rr) and transforms onto chi's G set (Eq. FFTX1).  Checked against
 the FP64 oracle chain on the small cases (every precision), against the
 pair sum on sampled rows at 36^3 (the thread-block-cluster row pass), and
 for its refusals: orbitals outside the plane-wave set, and a grid whose two
-expanded rows do not fit a cluster."""
+expanded rows do not fit a cluster.  Sigma: the oracle chain's W~ on the small
+cases, a sparse W~ at 36^3 against the conventional route."""
 import numpy as np
 import pytest
 
@@ -13,6 +15,7 @@ from oracle import chi as ochi
 from oracle import grids as ogrids
 from oracle import gvec as ogv
 from oracle import pipeline as opipe
+from oracle import sigma as osg
 from paper_1607_02859_gb300 import gw, inputs
 
 pytestmark = pytest.mark.gpu
@@ -138,3 +141,52 @@ def test_pw_chi0_36cube_rows(ctx, g36, prec):
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     print("36^3 plane-wave chi0 %s: chi0(i tau) %.2e, chi0(i omega) %.2e" % (prec, err_tau, err))
     assert err_tau < TOL[prec] and err < TOL[prec], (err_tau, err)
+
+
+MEV = 3.674932e-5
+SIG_TOL = {"fp64": 1e-10, "fp32": MEV, "f16x3": MEV, "bf16x3": MEV}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "f16x3", "bf16x3"])
+def test_pw_sigma_diag_matches_oracle(ctx, case, prec):
+    """Sigma_nn(i omega) through the plane-wave G (gw_sigma_diag_pw) for the
+    oracle chain's W~(tau), against the oracle's Sigma (Eqs. Sigma_occ,
+    Sigma_rr, cos_sin_sigma), and equal to gw_sigma_diag's result."""
+    name, p, s, chi_ref = case
+    grid = gw.make_grid(p.n, p.lattice)
+    pw = support(p)
+    wt, _ = opipe.w_tau(p, s, chi_ref)
+    su, so = opipe.sigma_from_w(p, s, wt)
+    ref = osg.sigma_iw(su, so, s["C"], s["S"])
+    out = gw.sigma_diag_pw(ctx, grid, dev(p.psi, prec), p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, s["C"],
+                           s["S"], dev(wt, prec), s["fft_index"], pw, prec)
+    err = float(np.max(np.abs(out["sigma_iw"] - ref)))
+    print("%s %s: plane-wave Sigma_nn(i omega) max error %.2e Ha" % (name, prec, err))
+    assert err < SIG_TOL[prec], err
+    assert np.max(np.abs(out["sigma_unocc"] - su)) < 1e-4 * np.max(np.abs(su)) + 1e-12
+    assert np.max(np.abs(out["sigma_occ"] - so)) < 1e-4 * np.max(np.abs(so)) + 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_pw_sigma_36cube_sparse_w(ctx, g36, prec):
+    """36^3 (cluster rows with three expanded functions): Sigma_nn for a W~ with a
+    few nonzero (G, G') entries, every band in the sums, against the conventional
+    route of the oracle."""
+    p, idx, mats, rows, ref_tau = g36
+    grid = gw.make_grid(p.n, p.lattice)
+    pw = ogv.fft_index(ogv.g_set(p.n, p.n_b), p.n)
+    n = len(p.tau)
+    base = [(3, 3, -0.9, 0.25), (40, 40, -0.5, 0.6), (3, 40, 0.1 + 0.05j, 0.4), (40, 3, 0.1 - 0.05j, 0.4),
+            (900, 900, -0.3, 1.1)]
+    entries = [(a, b, p.volume * c * np.exp(-om * p.tau)) for (a, b, c, om) in base]
+    w = torch.zeros((n, p.n_chi, p.n_chi), dtype=torch.complex64, device="cuda")
+    for (a, b, v) in entries:
+        for j in range(n):
+            w[j, a, b] = complex(v[j])
+    su, so = osg.sigma_pair_sparse(p.psi, p.eps, p.n_occ, p.mu, p.tau, entries, p.n, p.lattice, idx, p.bands)
+    ref = osg.sigma_iw(su, so, mats["C"], mats["S"])
+    out = gw.sigma_diag_pw(ctx, grid, dev(p.psi, prec), p.eps, p.n_occ, p.mu, p.bands, p.tau, p.omega, mats["C"],
+                           mats["S"], w, idx, pw, prec)
+    err = float(np.max(np.abs(out["sigma_iw"] - ref)))
+    print("36^3 plane-wave Sigma_nn %s (sparse W~): max error %.2e Ha" % (prec, err))
+    assert err < MEV and err < 1e-4 * np.max(np.abs(ref)), err
