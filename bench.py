@@ -127,11 +127,14 @@ class ClockSampler:
 # only for the kernel source it was taken on: the sha1 of those files is checked
 # at run time and a mismatch reports null.
 MEASURED_TRAFFIC = {
-    ("si8", "f16x3", "cgemm_tc"): {
-        "bytes_per_launch": 1.3816e10,
-        "sources": {"paper_1607_02859_gb300/csrc/gw_tcgemm.cu": "c27907371a5f4c4ce666246524600209b3efb43e",
+    # green_tc on the 36^3 workload: ncu DRAM bytes per algorithmic flop of the two modes on the
+    # k8448 case (same kernel and K; 4.64e-6 for the chi pass, 3.08e-6 for the fused Sigma
+    # pass, equal flop shares in the step) times the step's 2.12e12 flops per launch
+    ("si64", "f16x3", "green_tc"): {
+        "bytes_per_launch": 8.19e9,
+        "sources": {"paper_1607_02859_gb300/csrc/gw_tc.cu": "52ca6a28979c58fef07cfe4f4d98bec8fdbf46f5",
                     "paper_1607_02859_gb300/csrc/gw_tcgen05.cuh": "9b50b7a589cc5e99cff2a95e30ffc334ce4d64ad"},
-        "profile": "profiles/cgemm_tc_si8_f16x3_dram.md",
+        "profile": "profiles/green_tc_k8448_f16x3.md",
     },
 }
 
@@ -428,6 +431,8 @@ def main():
                     kernels[fam]["frac_of_split_tensor"] = rate / 1e12 / (tc_peak / 3.0)
                 elif fam == "cgemm_exact":
                     kernels[fam]["frac_of_sliced_tensor"] = rate / 1e12 / (tc_peak / SLICE_PAIRS)
+                elif fam in ("row_pw", "cgemm_simt"):
+                    kernels[fam]["frac_of_fp32_alu"] = rate / 1e12 / sm_peak_fp32(sm_max)
         ctx.set_timing(False)
     roof = None
     if kernels:

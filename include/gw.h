@@ -94,8 +94,11 @@ gw_status gw_ctx_reserve(gw_ctx* ctx, size_t bytes);
  * the minimal HBM traffic for the transforms).  Enabling or disabling clears
  * the totals.  Families: "green_tc", "cgemm_tc", "cgemm_simt", "row_fft",
  * "col_fft", "col_line_ct", "sigma_contract", "ct" (the standalone transform
- * over tau/omega), "cgemm_exact" (the refinement's sliced product).  gw_ctx_kernel_stats synchronises on the recorded events;
- * any output pointer may be NULL. */
+ * over tau/omega), "cgemm_exact" (the refinement's sliced product),
+ * "row_pw" (the plane-wave row passes of gw_chi0_omega_pw and gw_sigma_diag_pw;
+ * work = their transforms' 5 N log2 N flops and the products).
+ * gw_ctx_kernel_stats synchronises on the recorded events; any output pointer
+ * may be NULL. */
 gw_status gw_ctx_set_timing(gw_ctx* ctx, int enabled);
 gw_status gw_ctx_kernel_stats(gw_ctx* ctx, const char* family, unsigned long long* launches,
                               double* ms, double* work, int* work_is_bytes);

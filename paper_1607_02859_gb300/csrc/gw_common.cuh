@@ -11,7 +11,7 @@
 
 // Kernel families whose launches can be timed individually (gw_ctx_set_timing).
 enum gw_kfam { KF_GREEN_TC = 0, KF_CGEMM_TC, KF_CGEMM_SIMT, KF_ROW_FFT, KF_COL_FFT, KF_COL_LINE_CT, KF_SIGMA, KF_CT,
-               KF_CGEMM_EXACT,
+               KF_CGEMM_EXACT, KF_ROW_PW,
                KF_COUNT };
 
 struct gw_krec {

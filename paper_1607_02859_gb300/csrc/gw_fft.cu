@@ -1041,7 +1041,9 @@ struct GridOps {
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (2.0 * n_pw + n_chi) * sizeof(C), st);
+      // FP32/FP64 ALU work: three transforms of N_r points (5 N log2 N each) and the product per row
+      const double nr = (double)N1 * N2 * N3;
+      KTimer kt(ctx, KF_ROW_PW, (double)n_rows * (3.0 * 5.0 * nr * std::log2(nr) + 6.0 * nr), st);
       s = cuda_check(ctx, cudaLaunchKernelEx(&cfg, kernel, (const C*)a, (const C*)b, lda, (C*)out, ldo, inv_pw, n_pw,
                                              inv_chi, n_chi, (T)scale),
                      "cudaLaunchKernelEx(row_pw_chi_kernel)");
@@ -1078,7 +1080,9 @@ struct GridOps {
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      KTimer kt(ctx, KF_ROW_FFT, (double)n_rows * (4.0 * n_pw + n_chi) * sizeof(C), st);
+      // five transforms of N_r points and two products per row
+      const double nr = (double)N1 * N2 * N3;
+      KTimer kt(ctx, KF_ROW_PW, (double)n_rows * (5.0 * 5.0 * nr * std::log2(nr) + 12.0 * nr), st);
       s = cuda_check(ctx, cudaLaunchKernelEx(&cfg, kernel, (const C*)tu, (const C*)to, ldt, (const C*)wg, ldw, (C*)hu,
                                              (C*)ho, ldh, inv_neg, inv_nat, n_pw, inv_chi, n_chi),
                      "cudaLaunchKernelEx(row_pw_sigma_kernel)");

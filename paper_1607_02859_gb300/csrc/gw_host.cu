@@ -138,7 +138,7 @@ static void drain_timers(gw_ctx* ctx) {
 using namespace gw;
 
 static const char* kFamNames[KF_COUNT] = {"green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft",
-                                          "col_line_ct", "sigma_contract", "ct", "cgemm_exact"};
+                                          "col_line_ct", "sigma_contract", "ct", "cgemm_exact", "row_pw"};
 
 extern "C" gw_status gw_ctx_set_timing(gw_ctx* ctx, int enabled) {
   if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
@@ -163,7 +163,8 @@ extern "C" gw_status gw_ctx_kernel_stats(gw_ctx* ctx, const char* family, unsign
   if (launches) *launches = ctx->tot_n[f];
   if (ms) *ms = ctx->tot_ms[f];
   if (work) *work = ctx->tot_work[f];
-  if (work_is_bytes) *work_is_bytes = (f == KF_GREEN_TC || f == KF_CGEMM_TC || f == KF_CGEMM_SIMT || f == KF_CGEMM_EXACT) ? 0 : 1;
+  if (work_is_bytes) *work_is_bytes = (f == KF_GREEN_TC || f == KF_CGEMM_TC || f == KF_CGEMM_SIMT || f == KF_CGEMM_EXACT ||
+                                    f == KF_ROW_PW) ? 0 : 1;
   return GW_OK;
 }
 

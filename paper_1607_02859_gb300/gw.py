@@ -201,7 +201,7 @@ class Context:
         _check(lib().gw_ctx_reserve(self.handle, int(nbytes)), self)
 
     FAMILIES = ("green_tc", "cgemm_tc", "cgemm_simt", "row_fft", "col_fft", "col_line_ct", "sigma_contract", "ct",
-                "cgemm_exact")
+                "cgemm_exact", "row_pw")
 
     def set_timing(self, enabled: bool):
         _check(lib().gw_ctx_set_timing(self.handle, 1 if enabled else 0), self)

@@ -75,7 +75,9 @@ def test_si64_screen_refined(ctx, si64, si64_screen):
     chi, w_ref = si64_screen
     errs, res = screen_check(ctx, gw.make_grid(p.n, p.lattice), gv, chi, w_ref, "f16x3", refine=1)
     print("si64 screening f16x3 + 1 refinement step: W~ relative error %s, residual probe %s" % (errs, res))
-    assert max(errs) < 1e-6, errs
+    # one step squares the solve's ~5e-6 error and the 30-bit residual bounds X to ~1e-9: what is
+    # left is W~'s FP32 storage (~6e-8); 2e-7 separates that from a residual product gone wrong
+    assert max(errs) < 2e-7, errs
 
 
 def test_si64_sigma_sparse_w(ctx, si64):
