@@ -266,10 +266,9 @@ gw_status gw_screen_W(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t
  * inverse of eps~; the same solve of Eq. W_correlated).  GW_FP64 and GW_FP32:
  * two N^3 FP64 complex GEMMs per step and frequency on CUDA cores, 64 n_chi^2
  * bytes more scratch.  GW_F16X3 / GW_BF16X3: the product chi~ X on tcgen05 as
- * exact fp16 slice products (as gw_zgemm_sliced with 4 levels, the top slice
- * narrowed to 5 bits so that one exact block holds 16384 real K: 29 bits of the
- * row and column maxima) and X R as split fp16 products (R is small), about
- * 160 n_chi^2 bytes more scratch.  The result is then limited by the
+ * exact fp16 slice products (gw_zgemm_sliced, 4 levels: 30 bits of the row and
+ * column maxima) and X R as split fp16 products (R is small), about 160
+ * n_chi^2 bytes more scratch.  The result is then limited by the
  * working precision of w_w.  refine_iters = 0 is gw_screen_W. */
 gw_status gw_screen_W_refine(gw_ctx* ctx, const gw_grid* grid, int n_chi, const int32_t* gvec_h,
                              int n_omega, gw_prec prec, int refine_iters, const void* chi_w,

@@ -497,10 +497,8 @@ static gw_status refine_one(gw_ctx* ctx, int n, const typename cpx<T>::t* chi, c
 
 // The same refinement for the tensor-core precisions, with the product chi~ X
 // of the residual on the tensor cores as exact fp16 slice products (slice pairs
-// up to kRefineLevels with a narrow top slice, i.e. 29 bits of the row and
-// column maxima: the residual then bounds X to ~2e-9, below the FP32 storage of
-// W~; the narrow top slice lets one exact block hold 16384 real K, so at
-// N_chi = 8192 every slice pair is one pass over the output), and the correction
+// up to kRefineLevels, i.e. 30 bits of the row and column maxima: the residual
+// then bounds X to ~1e-9, below the FP32 storage of W~), and the correction
 // X R as three fp16 split products (R is small: the correction needs only the
 // working precision).  Work: X, chi~, R in FP64 and R, X R in FP32 (the last
 // slot of ws); X in FP32 goes to the upper part of xl, which the final store
@@ -534,7 +532,7 @@ static gw_status refine_one_tc(gw_ctx* ctx, gw_prec prec, int n, const float2* c
   if ((rc = launch_check(ctx, "refine_expand_kernel"))) return rc;
   for (int it = 0; it < iters; ++it) {
     // R = chi~ X (FP64-class), then R = chi~ - X + R
-    if ((rc = tc_zgemm_sliced(ctx, n, n, n, Ct, n, X, n, R, n, kRefineLevels, tstat, sls, st, true))) return rc;
+    if ((rc = tc_zgemm_sliced(ctx, n, n, n, Ct, n, X, n, R, n, kRefineLevels, tstat, sls, st))) return rc;
     refine_resid_kernel<<<eb, 256, 0, st>>>(Ct, X, R, nn);
     if ((rc = launch_check(ctx, "refine_resid_kernel"))) return rc;
     to_f32_kernel<<<eb, 256, 0, st>>>(X, xl, nn);

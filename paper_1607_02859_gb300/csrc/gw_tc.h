@@ -91,13 +91,9 @@ gw_status tc_gemm(gw_ctx* ctx, gw_prec prec, const TcGemm& g, void* scratch, cud
 // C = A B for complex FP64 A [M][K] (lda), B [K][N] (ldb), C [M][N] (ldc, written)
 // with FP64-class accuracy from exact fp16 slice products on tcgen05 (slice pairs
 // a + b <= levels, 6 bits per slice; error below 2^(-6(levels+1)) of the row and
-// column maxima).  narrow_top: the top slice keeps 5 bits like the others (one
-// more bit of exponent headroom), so every slice product is below 2^10 and one
-// exact K block holds 16384 real elements instead of 4096; the bound doubles.
-// status: device words set on a pipeline time-out.
+// column maxima).  status: device words set on a pipeline time-out.
 size_t tc_zgemm_sliced_scratch(int M, int N, int K, int levels);
 gw_status tc_zgemm_sliced(gw_ctx* ctx, int M, int N, int K, const double2* A, long lda, const double2* B, long ldb,
-                          double2* C, long ldc, int levels, int* status, void* scratch, cudaStream_t st,
-                          bool narrow_top = false);
+                          double2* C, long ldc, int levels, int* status, void* scratch, cudaStream_t st);
 
 }  // namespace gw

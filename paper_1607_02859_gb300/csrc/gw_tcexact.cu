@@ -18,9 +18,6 @@
 // pairs in 8 groups), and for every group and K block one tcgen05 pass forms
 // the exact sum, which the epilogue adds, times its scale, into the output.
 // Dropped pairs and the rest are below 2^(-6(L+1)) of the row and column maxima.
-// With a narrow top slice (one more bit of exponent headroom, |s_0| <= 32) every
-// slice product is below 2^10, so a K block of 16384 real elements stays exact
-// for one pair: fewer epilogue passes for long K at twice the error bound.
 
 // GB300's FP64 rate is a few operations per clock and SM, too slow for an
 // FP64 update per pass.  A block sum times 2^-(a+b+2) beta is exact in FP32, so
@@ -50,7 +47,8 @@ using namespace tcx;
 
 constexpr int BM = 128, BNC = 128, BK = 32, STAGES = 6;
 constexpr int BETA = 6;                          // bits per slice
-constexpr int KB_REAL = 1 << (24 - 2 * BETA);    // real K per exact block: 4096 (16384 with a narrow top slice)
+constexpr int KB_REAL = 1 << (24 - 2 * BETA);    // real K per exact block: 4096
+constexpr int KB_STEPS = KB_REAL / BK;
 constexpr int MAX_LEVELS = 7;
 constexpr int MAX_PAIRS = (MAX_LEVELS + 1) * (MAX_LEVELS + 2) / 2;
 constexpr int MAX_GROUPS = MAX_PAIRS;
@@ -91,8 +89,7 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
 struct XParams {
   int M, N;               // complex output size
   int k_steps;            // BK stages over the padded real K
-  int n_kb;               // K blocks (kb_steps stages each, the last one shorter)
-  int kb_steps;           // BK stages per exact K block
+  int n_kb;               // K blocks (KB_STEPS stages each, the last one shorter)
   int n_groups;           // groups of pairs summed in one accumulator
   int tm, tn;
   int gstart[MAX_GROUPS + 1];          // pairs gstart[g] .. gstart[g+1]-1 form group g
@@ -148,8 +145,8 @@ __global__ void __launch_bounds__(THREADS, 1) cgemm_sliced_kernel(const __grid_c
     *abort_flag = 1;
     if (atomicCAS(p.status, 0, 1) == 0) p.status[1] = where;
   };
-  auto k_first = [&](int kb) { return kb * p.kb_steps; };
-  auto k_last = [&](int kb) { return min((kb + 1) * p.kb_steps, p.k_steps); };
+  auto k_first = [&](int kb) { return kb * KB_STEPS; };
+  auto k_last = [&](int kb) { return min((kb + 1) * KB_STEPS, p.k_steps); };
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- TMA producer
@@ -313,7 +310,7 @@ __device__ __forceinline__ int exp_above(double m) {
 
 // e_i of each row of A [M][K] (one warp per row).
 __global__ void __launch_bounds__(256) row_exp_kernel(const double2* __restrict__ A, long lda, int M, int K,
-                                                      int head, int* __restrict__ rexp) {
+                                                      int* __restrict__ rexp) {
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= M) return;
   double m = 0.0;
@@ -322,7 +319,7 @@ __global__ void __launch_bounds__(256) row_exp_kernel(const double2* __restrict_
     m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) rexp[i] = m > 0.0 ? exp_above(m) + head : 0;
+  if (lane == 0) rexp[i] = m > 0.0 ? exp_above(m) : 0;
 }
 
 // f_j of each column of B [K][N]: threads along j, blocks of rows along y; max
@@ -340,9 +337,9 @@ __global__ void __launch_bounds__(256) col_exp_kernel(const double2* __restrict_
   if (m > 0.0) atomicMax(&cexp[j], exp_above(m));
 }
 
-__global__ void col_exp_fix_kernel(int* cexp, int N, int head) {
+__global__ void col_exp_fix_kernel(int* cexp, int N) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < N) cexp[j] = cexp[j] < -1100 ? 0 : cexp[j] + head;     // 0 for an all-zero column
+  if (j < N && cexp[j] < -1100) cexp[j] = 0;     // all-zero column
 }
 
 __device__ __forceinline__ uint16_t ihalf(long long s) { return __half_as_ushort(__int2half_rn((int)s)); }
@@ -445,8 +442,7 @@ size_t tc_zgemm_sliced_scratch(int M, int N, int K, int levels) {
 }
 
 gw_status tc_zgemm_sliced(gw_ctx* ctx, int M, int N, int K, const double2* A, long lda, const double2* B, long ldb,
-                          double2* C, long ldc, int levels, int* status, void* scratch, cudaStream_t st,
-                          bool narrow_top) {
+                          double2* C, long ldc, int levels, int* status, void* scratch, cudaStream_t st) {
   using namespace tx;
   if (M <= 0 || N <= 0) return GW_OK;
   if (K <= 0) return fail(ctx, GW_ERR_SHAPE, "sliced GEMM needs K >= 1");
@@ -459,15 +455,13 @@ gw_status tc_zgemm_sliced(gw_ctx* ctx, int M, int N, int K, const double2* A, lo
   uint16_t* As = cv.take<uint16_t>((size_t)S * M * kp);
   uint16_t* Bs = cv.take<uint16_t>((size_t)S * 2 * N * kp);
   gw_status rc;
-  // a narrow top slice: one more bit of headroom in the exponents keeps |s_0| <= 32 like the others
-  const int head = narrow_top ? 1 : 0;
-  row_exp_kernel<<<(M + 7) / 8, 256, 0, st>>>(A, lda, M, K, head, rexp);
+  row_exp_kernel<<<(M + 7) / 8, 256, 0, st>>>(A, lda, M, K, rexp);
   if ((rc = launch_check(ctx, "row_exp_kernel"))) return rc;
   if ((rc = cuda_check(ctx, cudaMemsetAsync(cexp, 0x80, sizeof(int) * N, st), "memset exponents"))) return rc;
   const int rows = 256;
   col_exp_kernel<<<dim3((N + 255) / 256, (K + rows - 1) / rows), 256, 0, st>>>(B, ldb, K, N, rows, cexp);
   if ((rc = launch_check(ctx, "col_exp_kernel"))) return rc;
-  col_exp_fix_kernel<<<(N + 255) / 256, 256, 0, st>>>(cexp, N, head);
+  col_exp_fix_kernel<<<(N + 255) / 256, 256, 0, st>>>(cexp, N);
   if ((rc = launch_check(ctx, "col_exp_fix_kernel"))) return rc;
   switch (S) {
     case 2: rc = slice_ops<2>(ctx, M, N, K, kp, A, lda, B, ldb, rexp, cexp, As, Bs, st); break;
@@ -486,27 +480,21 @@ gw_status tc_zgemm_sliced(gw_ctx* ctx, int M, int N, int K, const double2* A, lo
   P.M = M;
   P.N = N;
   P.k_steps = kp / BK;
-  // exact K block: slice products are bounded by 2^6 x 2^6 with a full top slice and by
-  // 2^5 x 2^5 with a narrow one, so 4096 or 16384 real K keep a pair's sum below 2^24
-  const long kb_real = narrow_top ? 16384 : KB_REAL;
-  P.kb_steps = (int)(kb_real / BK);
-  P.n_kb = (P.k_steps + P.kb_steps - 1) / P.kb_steps;
-  // pairs level by level (largest terms first), packed into groups whose block-sum bounds
-  // add up to at most 2^24: kb_real x 2^(bits(a) + bits(b)), bits = 6 for a full top
-  // slice, 5 for the others
-  auto bits = [&](int a) { return a == 0 && !narrow_top ? BETA : BETA - 1; };
+  P.n_kb = (P.k_steps + KB_STEPS - 1) / KB_STEPS;
+  // pairs level by level (largest terms first), packed into groups whose block sums are
+  // bounded by 2^24 together: log2 bound 24 for (0,0), 23 with one top slice, 22 without
   int n_pairs = 0;
   P.n_groups = 0;
   for (int lv = 0; lv <= levels; ++lv) {
-    long room = 0;                                 // bound left in the open group
+    long room = 0;                                 // units of 2^22 left in the open group
     for (int a = 0; a <= lv; ++a) {
       const int b = lv - a;
-      const long need = kb_real << (bits(a) + bits(b));
+      const long need = (a == 0 && b == 0) ? 4 : (a == 0 || b == 0) ? 2 : 1;
       if (need > room) {                           // open a new group at this pair
         P.gstart[P.n_groups] = n_pairs;
         P.glevel[P.n_groups] = lv;
         ++P.n_groups;
-        room = 1L << 24;
+        room = 4;
       }
       room -= need;
       P.pa[n_pairs] = a;
