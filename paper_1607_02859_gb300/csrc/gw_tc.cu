@@ -471,21 +471,10 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
         }
         const int sho = times_w(ao);
         bool fine = wait_or_abort(&hfree[h], 0);     // the unoccupied MMAs have read this half
-        // psi_n(r) of this row for the first kPre bands, loaded while the V MMAs run (the row of
-        // H is in shared memory by then, its registers free); band indices from one load per lane
-        constexpr int kPre = 12;
-        const int bl = lane < p.n_n ? __ldg(p.bands + lane) : 0;
-        float2 pre[kPre];
         if (__all_sync(0xffffffffu, fine)) {
           tc_fence_after();
           store_h(sho);
           if (lane == 0) mbar_arrive(&hready[h]);
-#pragma unroll
-          for (int u = 0; u < kPre; ++u) {
-            const int bn = __shfl_sync(0xffffffffu, bl, u);
-            pre[u] = make_float2(0.f, 0.f);
-            if (rvalid && u < p.n_n) pre[u] = __ldg(p.psi + (long)bn * p.ldpsi + grow);
-          }
           fine = wait_or_abort(&vready[h], 0);
         }
         if (__all_sync(0xffffffffu, fine)) {
@@ -510,20 +499,11 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
           const int e = *p.dexp, ku = shu + e, ko = sho + e;
           const float fu1 = ldexpf(1.0f, -(ku >> 1)), fu2 = ldexpf(1.0f, -(ku - (ku >> 1)));
           const float fo1 = ldexpf(1.0f, -(ko >> 1)), fo2 = ldexpf(1.0f, -(ko - (ko >> 1)));
-          // the remaining bands' psi_n(r) in batches of eight loads in flight
-          float2 nxt[8];
 #pragma unroll
           for (int n = 0; n < 32; ++n) {
-            if (n >= kPre && (n - kPre) % 8 == 0 && n < p.n_n) {
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const int bn = __shfl_sync(0xffffffffu, bl, (n + u) & 31);
-                nxt[u] = make_float2(0.f, 0.f);
-                if (rvalid && n + u < p.n_n) nxt[u] = __ldg(p.psi + (long)bn * p.ldpsi + grow);
-              }
-            }
             if (n < p.n_n) {
-              const float2 ps = n < kPre ? pre[n < kPre ? n : 0] : nxt[(n - kPre) % 8];
+              float2 ps = make_float2(0.f, 0.f);
+              if (rvalid) ps = __ldg(p.psi + (long)p.bands[n] * p.ldpsi + grow);
               float su = (ps.x * tot[2 * n] + ps.y * tot[2 * n + 1]) * fu1 * fu2;    // Re(conj(psi_n) V_n)
               float so = (ps.x * tot[64 + 2 * n] + ps.y * tot[64 + 2 * n + 1]) * fo1 * fo2;
 #pragma unroll
