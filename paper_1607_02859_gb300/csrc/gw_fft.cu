@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(ClusterRow<T, N1, N2, N3>::THREADS, 2)
     for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
       const int i2 = q / N3, i3 = q - i2 * N3;
       C x[N1];
+      bool any = false;
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1) {
         const int j = __ldg(inv + i1 * PL + q);
@@ -295,9 +296,11 @@ __global__ void __launch_bounds__(ClusterRow<T, N1, N2, N3>::THREADS, 2)
         if (j >= 0) {
           const int o = j / n_s;
           x[i1] = cluster.map_shared_rank(gs, o)[j - o * n_s];
+          any = true;
         }
       }
-      RegFFT<N1, -1>::run(x);
+      // columns outside the G set's projection are zero and stay zero
+      if (__any_sync(__activemask(), any)) RegFFT<N1, -1>::run(x);
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1) cluster.map_shared_rank(s, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3] = x[i1];
     }
@@ -351,6 +354,11 @@ __global__ void __launch_bounds__(ClusterRow<T, N1, N2, N3>::THREADS, 2)
   // ... i1 transforms of the CTA's columns, each result scattered to the G-set slice that holds it
   for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
     const int i2 = q / N3, i3 = q - i2 * N3;
+    // a column with no G-set point has nothing to deliver: skip it where the whole warp may
+    bool any = false;
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) any |= __ldg(inv + i1 * PL + q) >= 0;
+    if (!__any_sync(__activemask(), any)) continue;
     C x[N1];
 #pragma unroll
     for (int i1 = 0; i1 < N1; ++i1) x[i1] = cluster.map_shared_rank(s, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3];
@@ -446,6 +454,7 @@ __global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
       C* src = which ? so : su;
       C* dst = which ? sb : sa;
       C x[N1];
+      bool any = false;
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1) {
         const int j = __ldg(inv_pw + i1 * PL + q);
@@ -453,9 +462,10 @@ __global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
         if (j >= 0) {
           const int o = j / n_ps;
           x[i1] = cluster.map_shared_rank(src, o)[j - o * n_ps];
+          any = true;
         }
       }
-      RegFFT<N1, -1>::run(x);
+      if (__any_sync(__activemask(), any)) RegFFT<N1, -1>::run(x);   // empty columns stay zero
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1)
         cluster.map_shared_rank(dst, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3] = x[i1];
@@ -484,6 +494,10 @@ __global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
   C* sx = sl;                      // [n_cs] this CTA's part of the chi row
   for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
     const int i2 = q / N3, i3 = q - i2 * N3;
+    bool any = false;                // columns with no point of chi's G set deliver nothing
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) any |= __ldg(inv_chi + i1 * PL + q) >= 0;
+    if (!__any_sync(__activemask(), any)) continue;
     C x[N1];
 #pragma unroll
     for (int i1 = 0; i1 < N1; ++i1) x[i1] = cluster.map_shared_rank(sa, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3];
@@ -557,6 +571,7 @@ __global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
     for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
       const int i2 = q / N3, i3 = q - i2 * N3;
       C x[N1];
+      bool any = false;
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1) {
         const int j = __ldg(inv + i1 * PL + q);
@@ -564,9 +579,10 @@ __global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
         if (j >= 0) {
           const int o = j / ns;
           x[i1] = cluster.map_shared_rank(src, o)[j - o * ns];
+          any = true;
         }
       }
-      RegFFT<N1, -1>::run(x);
+      if (__any_sync(__activemask(), any)) RegFFT<N1, -1>::run(x);   // empty columns stay zero
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1)
         cluster.map_shared_rank(dst, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3] = x[i1];
@@ -576,6 +592,10 @@ __global__ void __launch_bounds__(PwRow<T, N1, N2, N3>::THREADS)
   auto line_fwd = [&](C* out) {
     for (int q = c * COLS + threadIdx.x; q < (c + 1) * COLS; q += TH) {
       const int i2 = q / N3, i3 = q - i2 * N3;
+      bool any = false;              // columns with no plane wave of the set deliver nothing
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) any |= __ldg(inv_nat + i1 * PL + q) >= 0;
+      if (!__any_sync(__activemask(), any)) continue;
       C x[N1];
 #pragma unroll
       for (int i1 = 0; i1 < N1; ++i1) x[i1] = cluster.map_shared_rank(sb, i1 / P)[((i1 % P) * N2 + i2) * S2 + i3];
