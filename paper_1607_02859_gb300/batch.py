@@ -11,7 +11,10 @@ distinct system shape, cached in a JSON file).
 prints one JSON line: the replay time and effective TFLOP/s of the whole batch
 (the algorithmic flops of every system's chain over the replay time) and, for
 the systems with N_r <= --fp64-max-nr, each system's largest difference in meV
-from the same batch run through the library's FP64 path.  (The comparison with
+from the same batch run through the library's FP64 path.  With --stages the
+same chains run once more call by call with the library's per-kernel timing
+(a graph replay cannot carry it), and the line adds each kernel family's device
+time, work and fraction of the measured peaks (MEASURED_PEAKS.json).  (The comparison with
 the FP64 oracle is in the GPU tests, tests/test_gpu_batch.py.)
 """
 from __future__ import annotations
@@ -37,6 +40,50 @@ def chain_flops(n_r, n_b, n_tau, n_chi, n_n):
             + n_tau * 3 * 6.0 * n_r * n_r)                               # real-space products
 
 
+def family_stages(ctx, systems, prec):
+    """Every system's chain through the direct entry points with per-kernel timing on:
+    {family: launches, ms, work, unit and the fraction of the measured peak that bounds it}."""
+    import os
+    import torch
+    peaks = {}
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    tc = peaks.get("bf16_tflops_sustained")
+    alu = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    for s in systems:
+        gw.chi0_omega(ctx, s["grid"], s["psi"], s["eps"], s["n_occ"], s["mu"], s["tau"], s["C"], s["fft_index"],
+                      prec, s["chi_w"], r_block=s["r_block"])
+        gw.screen_W(ctx, s["grid"], s["gvec"], prec, s["chi_w"], s["chi_w"], resid=False, refine=s["refine"])
+        gw.tau_to_omega(ctx, gw.CT, s["Cinv"], s["chi_w"], s["w_tau"], prec)
+        gw.sigma_diag(ctx, s["grid"], s["psi"], s["eps"], s["n_occ"], s["mu"], s["bands"], s["tau"], s["omega"],
+                      s["C"], s["S"], s["w_tau"], s["fft_index"], prec)
+    torch.cuda.synchronize()
+    out = {}
+    split = 3.0 if prec in ("f16x3", "bf16x3") else None
+    for fam, (n, ms, work, is_bytes) in ctx.kernel_stats().items():
+        if not n:
+            continue
+        rate = work / (ms / 1e3)
+        row = {"launches": n, "ms": ms, "work": work, "unit": "B" if is_bytes else "flop"}
+        if is_bytes and hbm:
+            row["frac_of_hbm"] = rate / 1e9 / hbm
+        elif fam in ("green_tc", "cgemm_tc") and tc and split:
+            row["frac_of_split_tensor"] = rate / 1e12 / (tc / split)
+        elif fam == "cgemm_exact" and tc:
+            row["frac_of_sliced_tensor"] = rate / 1e12 / (tc / 15.0)
+        elif not is_bytes:
+            row["frac_of_fp32_alu"] = rate / 1e12 / alu
+        out[fam] = row
+    ctx.set_timing(False)
+    return out
+
+
 def main(argv=None):
     import torch
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
@@ -48,6 +95,7 @@ def main(argv=None):
     ap.add_argument("--tune-cache", default="", help="JSON file for the r-block autotuner (empty: no cache)")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--fp64-max-nr", type=int, default=4096)
+    ap.add_argument("--stages", action="store_true", help="per-kernel-family times of the chains, call by call")
     args = ap.parse_args(argv)
     ctx = gw.Context(0)
     problems = inputs.batch_mix(args.count, args.seed)
@@ -87,6 +135,7 @@ def main(argv=None):
     sig, status = batch.wait()
     t = e0.elapsed_time(e1) / 1e3 / args.reps
     batch.close()
+    stages = family_stages(ctx, systems, args.prec) if args.stages else None
     # the small systems again through the FP64 path, as one more batch
     small = [i for i, (p, _, _) in enumerate(meta) if p.n_r <= args.fp64_max_nr and args.prec != "fp64"]
     ref = {}
@@ -113,8 +162,11 @@ def main(argv=None):
         if i in ref:
             row["max_dsigma_meV_vs_fp64"] = float(np.max(np.abs(s_iw - ref[i]))) / 3.674932e-5
         rows.append(row)
-    print(json.dumps({"batch": len(systems), "prec": args.prec, "refine": args.refine, "replay_ms": t * 1e3,
-                      "tflops": total / t / 1e12, "gflop_total": total / 1e9, "systems": rows}))
+    line = {"batch": len(systems), "prec": args.prec, "refine": args.refine, "replay_ms": t * 1e3,
+            "tflops": total / t / 1e12, "gflop_total": total / 1e9, "systems": rows}
+    if stages is not None:
+        line["kernels"] = stages
+    print(json.dumps(line))
     ctx.close()
 
 
