@@ -322,10 +322,13 @@ __global__ void __launch_bounds__(ClusterRow<T, N1, N2, N3>::THREADS, 2)
   const C* pb = b + row * lda + pbase;
   if (VEC) {
     constexpr int NP = P * PL / 2;
-    for (int q0 = threadIdx.x; q0 < NP; q0 += 4 * TH) {
-      C v[4][2], w[4][2];
+    // the row's ~93 KB per CTA arrive in few round trips: LB 16-byte loads in flight per thread
+    // (the FFT's registers are free here)
+    constexpr int LB = MODE == 0 ? 6 : 12;
+    for (int q0 = threadIdx.x; q0 < NP; q0 += LB * TH) {
+      C v[LB][2], w[LB][2];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < LB; ++u) {
         const int q = q0 + u * TH;
         if (q < NP) {
           ld_pair(pa + 2 * q, v[u][0], v[u][1]);
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(ClusterRow<T, N1, N2, N3>::THREADS, 2)
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < LB; ++u) {
         const int q = q0 + u * TH;
         if (q >= NP) continue;
         const int ps = plane_pos(2 * q);
