@@ -139,8 +139,18 @@ __global__ void __launch_bounds__(THREADS, 1) green_tc_kernel(const __grid_const
   double* red = reinterpret_cast<double*>(epi);   // [2][32] band sums of the CTA (MODE 2 only)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM;
-  const int n0 = blockIdx.x * BNC;
+  // tiles in groups of kGroupRows row tiles: the CTAs that run together walk a group's rows for
+  // each column tile, so they share B (and A) tiles in L2 instead of each reading its B from DRAM
+  int m0, n0;
+  {
+    constexpr int kGroupRows = 8;
+    const int gx = gridDim.x, gy = gridDim.y;
+    const int id = blockIdx.y * gx + blockIdx.x;
+    const int per = kGroupRows * gx, grp = id / per, first = grp * kGroupRows;
+    const int rows = min(kGroupRows, gy - first), r = id - grp * per;
+    m0 = (first + r % rows) * BM;
+    n0 = (r / rows) * BNC;
+  }
   const long grow0 = (long)p.r0 + m0;                 // grid row of the tile's first row
   if (MODE != 1 && p.lower && n0 >= grow0 + BM) {
     // every R' of the tile is above every r: zeros (chi), or nothing (self-energy)
