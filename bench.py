@@ -128,11 +128,12 @@ class ClockSampler:
 # at run time and a mismatch reports null.
 MEASURED_TRAFFIC = {
     # green_tc on the 36^3 workload: ncu DRAM bytes per algorithmic flop of the two modes on the
-    # k8448 case (same kernel and K; 4.64e-6 for the chi pass, 3.08e-6 for the fused Sigma
-    # pass, equal flop shares in the step) times the step's 2.12e12 flops per launch
+    # k8448 case (same kernel and K; 3.49e-6 for the chi pass, 3.07e-6 for the fused Sigma
+    # pass, equal flop shares in the step) times the step's 2.12e12 flops per launch; the
+    # 36^3 launches, with 2-5x more tiles, reuse more in L2, so this is an upper estimate
     ("si64", "f16x3", "green_tc"): {
-        "bytes_per_launch": 8.19e9,
-        "sources": {"paper_1607_02859_gb300/csrc/gw_tc.cu": "52ca6a28979c58fef07cfe4f4d98bec8fdbf46f5",
+        "bytes_per_launch": 6.96e9,
+        "sources": {"paper_1607_02859_gb300/csrc/gw_tc.cu": "6d1061d1b8c170b6b869627d5056bace4943b6de",
                     "paper_1607_02859_gb300/csrc/gw_tcgen05.cuh": "9b50b7a589cc5e99cff2a95e30ffc334ce4d64ad"},
         "profile": "profiles/green_tc_k8448_f16x3.md",
     },
