@@ -176,3 +176,115 @@ def sigma_k_tau(psi_k, eps_k, n_occ, mu, tau, w_s, n, nk, lattice, bands_nk):
         su[i] = (dv * dv * (row.conj() @ ((gu * w_s) @ col))).real
         so[i] = -(dv * dv * (row.conj() @ ((go * w_s) @ col))).real
     return su, so
+
+
+# ------------------------------------------------------------------ plane-wave form of G_k
+# Sec. II.B keeps G_k in its plane-wave form and transforms it to the stripe
+# only when needed.  With the bra-kets of Eq. notation_bra_ket,
+#     <g|psi_ak>  = sum_{r in C}  exp(-i(k+g).r) psi_ak(r),
+#     <psi_ak|G'> = sum_{R' in S} psi*_ak(R') exp(+i G'.R'),
+# a Bloch orbital gives <psi_ak|G'> = N_k conj(<g'|psi_ak>) for G' = k + g' and
+# zero for every other supercell vector (the sum over the cells L of
+# exp(i(k'-k).L) is N_k delta_kk'), so G_k(g, G') lives on G' = k + g' only and
+# is stored as an [N_r][N_r] block per k, g and g' in the cell's FFT order
+# (exp(i g.r) on the cell grid depends on g modulo the grid).
+
+
+def pw_coefficients_k(psi_k, n, nk):
+    """<g|psi_ak> for every k, band and g of the cell's FFT grid (Eq.
+    notation_bra_ket): the Bloch phase exp(-i k.r) applied, then the cell's
+    discrete Fourier transform.  [N_k][N_b][N_r], g in FFT order."""
+    n = np.asarray(n)
+    nk = np.asarray(nk)
+    i_cell = np.stack(np.meshgrid(*[np.arange(d) for d in n], indexing="ij"), -1).reshape(-1, 3)
+    out = np.empty(psi_k.shape, dtype=np.complex128)
+    for ki, kv in enumerate(k_list(nk)):
+        ph = np.exp(-2j * np.pi * (i_cell @ (kv / (nk * n))))                 # exp(-i k.r), r in C
+        x = (psi_k[ki] * ph[None, :]).reshape(-1, *n)
+        out[ki] = np.fft.fftn(x, axes=(1, 2, 3)).reshape(psi_k.shape[1], -1)
+    return out
+
+
+def green_k_pw(c_k, eps_k, n_occ, mu, tau, nk, which):
+    """G_k(g, k+g') in plane-wave form for every k (Eqs. G1_unocc_k, G1_occ_k),
+    energies from mu and the signs of oracle.green:
+        unocc: sum_{a unocc} <g|psi_ak> <psi_ak|k+g'> exp(-(eps_a - mu) tau)
+        occ:   sum_{i occ}   <g|psi_ik> <psi_ik|k+g'> exp(+(eps_i - mu) tau)
+    with <psi|k+g'> = N_k conj(<g'|psi>).  The unoccupied one is minus the
+    paper's overline-G^(1)_k; the occupied one is the complex conjugate of its
+    underline-G^*(1)_k (the same product in the index order of
+    oracle.green.green_occ).  [N_k][N_r][N_r]."""
+    n_k = int(np.prod(nk))
+    out = np.empty((c_k.shape[0], c_k.shape[2], c_k.shape[2]), dtype=np.complex128)
+    for ki in range(c_k.shape[0]):
+        if which == "occ":
+            s = np.exp((eps_k[ki, :n_occ] - mu) * tau)
+            c = c_k[ki, :n_occ]
+        else:
+            s = np.exp(-(eps_k[ki, n_occ:] - mu) * tau)
+            c = c_k[ki, n_occ:]
+        out[ki] = (c.T * s) @ (n_k * c.conj())
+    return out
+
+
+def fft_g1_g2(gk_pw, n, nk, pw_index=None):
+    """Eqs. FFT_G1 then FFT_G2 summed over k, as written (unnormalised sums):
+        G(r, G')  = sum_g exp(+i(k+g).r) G_k(g, G')        r in C
+        G(r, R')  = sum_{G'} G(r, G') exp(-i G'.R')         R' in S
+    where G' runs over k + g' for the block of k.  pw_index (FFT positions)
+    restricts g and g' to a plane-wave set; None takes the whole cell grid.
+    [N_r][N_k N_r], columns in the supercell order of supercell_index."""
+    n = np.asarray(n)
+    nk = np.asarray(nk)
+    ns = n * nk
+    i_cell = np.stack(np.meshgrid(*[np.arange(d) for d in n], indexing="ij"), -1).reshape(-1, 3)
+    i_sup = np.stack(np.meshgrid(*[np.arange(d) for d in ns], indexing="ij"), -1).reshape(-1, 3)
+    sel = np.arange(int(np.prod(n))) if pw_index is None else np.asarray(pw_index)
+    g = i_cell[sel]                                                            # FFT position = g mod n
+    out = np.zeros((len(i_cell), len(i_sup)), dtype=np.complex128)
+    for ki, kv in enumerate(k_list(nk)):
+        m = kv[None, :] + nk[None, :] * g                                      # k + g as supercell triples
+        to_r = np.exp(2j * np.pi * i_cell @ (m / ns).T)                        # exp(+i(k+g).r)   [N_r][n_pw]
+        to_R = np.exp(-2j * np.pi * (m / ns) @ i_sup.T)                        # exp(-i(k+g').R') [n_pw][N_S]
+        out += to_r @ gk_pw[ki][np.ix_(sel, sel)] @ to_R
+    return out
+
+
+def inv_fft_g1_g2(g_s, n, nk):
+    """Eqs. INV_FFT_G1 then INV_FFT_G2, as written (unnormalised sums):
+        G(r, G')    = sum_{R' in S} G(r, R') exp(+i G'.R')
+        G_k(g, G')  = sum_{r in C} exp(-i(k+g).r) G(r, G')
+    for G' = k + g' with every g, g' of the cell's FFT grid.  [N_k][N_r][N_r]."""
+    n = np.asarray(n)
+    nk = np.asarray(nk)
+    ns = n * nk
+    i_cell = np.stack(np.meshgrid(*[np.arange(d) for d in n], indexing="ij"), -1).reshape(-1, 3)
+    i_sup = np.stack(np.meshgrid(*[np.arange(d) for d in ns], indexing="ij"), -1).reshape(-1, 3)
+    out = []
+    for kv in k_list(nk):
+        m = kv[None, :] + nk[None, :] * i_cell
+        from_R = np.exp(2j * np.pi * i_sup @ (m / ns).T)                       # exp(+i(k+g').R') [N_S][N_r]
+        from_r = np.exp(-2j * np.pi * (m / ns) @ i_cell.T)                     # exp(-i(k+g).r)   [N_r][N_r]
+        out.append(from_r @ (g_s @ from_R))
+    return np.array(out)
+
+
+def green_stripe_pw(psi_k, eps_k, n_occ, mu, tau, n, nk, pw_index=None):
+    """G_occ and G_unocc on the stripe through the plane-wave form (Sec. II.B):
+    coefficients, G_k(g, k+g') per k, then Eqs. FFT_G1, FFT_G2.  Each of the two
+    transforms inverts an unnormalised bra-ket (a factor N_r from the cell
+    transform of the coefficients) and the ket over S carries N_k, so the
+    stripe of green_stripe (cell-normalised orbitals, 1/N_k) is the transformed
+    sum divided by N_r^2 N_k^2.  [N_r][N_k N_r] each."""
+    c_k = pw_coefficients_k(psi_k, n, nk)
+    scale = 1.0 / (float(np.prod(n)) ** 2 * float(np.prod(nk)) ** 2)
+    go = scale * fft_g1_g2(green_k_pw(c_k, eps_k, n_occ, mu, tau, nk, "occ"), n, nk, pw_index)
+    gu = scale * fft_g1_g2(green_k_pw(c_k, eps_k, n_occ, mu, tau, nk, "unocc"), n, nk, pw_index)
+    return go, gu
+
+
+def chi_q_tau_pw(psi_k, eps_k, n_occ, mu, tau, n, nk, lattice, gvecs, pw_index=None):
+    """chi_q(g, g', tau) for every q with G on the stripe taken from its
+    plane-wave form (green_stripe_pw), then the stripe product and chi_q."""
+    go, gu = green_stripe_pw(psi_k, eps_k, n_occ, mu, tau, n, nk, pw_index)
+    return chi_q(-2.0 * go * gu.conj(), n, nk, lattice, gvecs)

@@ -93,3 +93,75 @@ def test_sigma_stripe_equals_supercell_gamma_point():
     # and the stripe of W~ is the supercell's W~ restricted to rows in the cell
     pos0 = okm.supercell_index(p.n, p.nk)[0]
     assert np.linalg.norm(w_s - w_rr[pos0]) < 1e-12 * np.linalg.norm(w_rr)
+
+
+# ---------------------------------------------- plane-wave form of G_k (Sec. II.B)
+
+def _support(c_k):
+    """FFT positions where any band at any k has a plane-wave coefficient."""
+    w = np.sum(np.abs(c_k) ** 2, axis=(0, 1))
+    return np.flatnonzero(w > 1e-20 * w.max())
+
+
+def test_pw_form_gives_the_real_space_stripe():
+    """Coefficients, G_k(g, k+g') (Eqs. G1_unocc_k, G1_occ_k) and Eqs. FFT_G1,
+    FFT_G2 give the stripe that the Bloch extension of the real-space Green's
+    functions gives, for both Green's functions."""
+    p = inputs.kmesh_problem(n=(4, 4, 4), a=(5.0, 5.5, 6.0), nk=(2, 1, 2), n_occ=3, n_unocc=9, n_tau=2, seed=57)
+    for tau in p.tau:
+        go, gu = okm.green_stripe(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk)
+        po, pu = okm.green_stripe_pw(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk)
+        assert np.linalg.norm(po - go) < 1e-12 * np.linalg.norm(go)
+        assert np.linalg.norm(pu - gu) < 1e-12 * np.linalg.norm(gu)
+
+
+def test_inverse_transforms_give_the_pw_form():
+    """Eqs. INV_FFT_G1, INV_FFT_G2 applied to the real-space stripe give
+    G_k(g, k+g') / N_k for every k: the ket over the supercell carries the N_k
+    that the cell-normalised stripe (1/N_k) takes back."""
+    p = inputs.kmesh_problem(n=(4, 4, 2), a=(5.0, 5.5, 3.5), nk=(2, 2, 2), n_occ=3, n_unocc=7, n_tau=2, seed=58)
+    tau = p.tau[1]
+    c_k = okm.pw_coefficients_k(p.psi_k, p.n, p.nk)
+    go, gu = okm.green_stripe(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk)
+    for which, g_s in (("occ", go), ("unocc", gu)):
+        ref = okm.green_k_pw(c_k, p.eps_k, p.n_occ, p.mu, tau, p.nk, which) / p.n_k
+        got = okm.inv_fft_g1_g2(g_s, p.n, p.nk)
+        assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_pw_form_at_gamma_is_the_two_sided_dft():
+    """A 1 x 1 x 1 mesh: G(g, g') is the cell DFT of G(r, r') over r and its
+    inverse-signed DFT over r' (numpy's FFT on each side)."""
+    p = inputs.kmesh_problem(n=(4, 3, 5), a=(5.0, 4.0, 6.0), nk=(1, 1, 1), n_occ=3, n_unocc=9, n_tau=2, seed=59)
+    tau = p.tau[0]
+    c_k = okm.pw_coefficients_k(p.psi_k, p.n, p.nk)
+    for which, f in (("occ", ogr.green_occ), ("unocc", ogr.green_unocc)):
+        g_rr = f(p.psi_k[0], p.eps_k[0], p.n_occ, p.mu, tau).reshape(p.n + p.n)
+        ref = np.fft.ifftn(np.fft.fftn(g_rr, axes=(0, 1, 2)), axes=(3, 4, 5)) * p.n_r
+        got = okm.green_k_pw(c_k, p.eps_k, p.n_occ, p.mu, tau, p.nk, which)[0]
+        assert np.linalg.norm(got - ref.reshape(p.n_r, p.n_r)) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_pw_form_needs_only_the_orbitals_plane_waves():
+    """The memory-lean point of Sec. II.B: G_k(g, g') vanishes outside the
+    orbitals' plane-wave set (here the lowest N_b plane waves, fewer than the
+    grid points), and the transforms over that set alone give the same stripe
+    and the same chi_q."""
+    p = inputs.kmesh_problem(n=(4, 4, 4), a=(5.0, 5.5, 6.0), nk=(2, 2, 1), n_occ=3, n_unocc=9, n_tau=2, seed=60)
+    tau = p.tau[0]
+    c_k = okm.pw_coefficients_k(p.psi_k, p.n, p.nk)
+    pw = _support(c_k)
+    assert len(pw) == p.n_b < p.n_r
+    out = np.setdiff1d(np.arange(p.n_r), pw)
+    for which in ("occ", "unocc"):
+        gk = okm.green_k_pw(c_k, p.eps_k, p.n_occ, p.mu, tau, p.nk, which)
+        assert np.abs(gk[:, out, :]).max() < 1e-12 * np.abs(gk).max()
+        assert np.abs(gk[:, :, out]).max() < 1e-12 * np.abs(gk).max()
+    full = okm.green_stripe_pw(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk)
+    lean = okm.green_stripe_pw(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk, pw_index=pw)
+    for a, b in zip(full, lean):
+        assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(a)
+    gv = ogv.g_set(p.n, 30)
+    ref = okm.chi_q_tau(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk, p.lattice, gv)
+    got = okm.chi_q_tau_pw(p.psi_k, p.eps_k, p.n_occ, p.mu, tau, p.n, p.nk, p.lattice, gv, pw_index=pw)
+    assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
