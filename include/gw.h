@@ -462,6 +462,28 @@ gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const int* nk, i
                               const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
                               gw_prec prec, int r_block, void* chi_w, void* stream);
 
+/* chi_w as gw_chi0_omega_kmesh, with every G_k taken through its plane-wave
+ * form (Sec. II.B, Eqs. G1_unocc_k, G1_occ_k; the stripe by Eqs. FFT_G1,
+ * FFT_G2).  The cell-periodic parts u_nk = exp(-i k.r) psi_nk of every orbital
+ * must lie in the span of the n_pw plane waves e^{+i g.r} at the cell FFT
+ * positions pw_index_h[n_pw] (one set for all k; checked per band and k by
+ * Parseval as in gw_chi0_omega_pw, else GW_ERR_ARG).  Per tau_j and k: the
+ * matrix over the set from the coefficients of u_nk (tcgen05 for GW_F16X3 /
+ * GW_BF16X3) and its column transform T_k(r, g') over the cell grid; the stripe
+ * row r is exp(-i k.r) T_k(r, g') / N_k at the supercell plane waves k + nk g'
+ * of every k, and one row pass over the supercell grid expands both Green's
+ * functions over R', forms -2 G_occ conj(G_unocc) and transforms it onto the
+ * supercell G set {q + g}; the rest as gw_chi0_omega_kmesh.  Scratch (context
+ * arena): the slabs (N_r N_k n_chi n elements) plus 2 N_r N_k n_pw + 2 n_pw^2 +
+ * N_k N_b n_pw + N_b N_r elements and the tensor-core operands.
+ * GW_ERR_UNSUPPORTED where two expanded supercell rows do not fit a
+ * thread-block cluster (supercells beyond 36^3, GW_FP64 at 36^3).  Synchronises
+ * the stream once per k (the norm check). */
+gw_status gw_chi0_omega_kmesh_pw(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_b, int n_occ,
+                                 const void* psi_k, const double* eps_k_h, double mu, int n,
+                                 const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
+                                 int n_pw, const int32_t* pw_index_h, gw_prec prec, void* chi_w, void* stream);
+
 /* Diagonal self-energy of Bloch states on the k mesh of gw_chi0_omega_kmesh:
  * the space-time route of gw_sigma_diag on the supercell stripe.  For every
  * tau_j, W~(r, R') = (1/Omega_S) sum_q sum_{g,g'} exp(i(q+g).r) W~_q(g,g') exp(-i(q+g').R')

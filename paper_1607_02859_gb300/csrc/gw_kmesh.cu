@@ -132,6 +132,26 @@ __global__ void __launch_bounds__(256) bloch_extend_kernel(const typename cpx<T>
   if (l == 0) row[(long)i * nr + rp] = v;
 }
 
+// The orbitals of one k with the Bloch phase taken off: u[b][r] = exp(-i k.r) psi_bk(r),
+// the cell-periodic parts whose plane-wave coefficients the plane-wave form of
+// G_k is built from (k.r / 2 pi = sum_d k_d i_d / (nk_d n_d), reduced mod 1).
+template <typename T>
+__global__ void __launch_bounds__(256) bloch_unphase_kernel(const typename cpx<T>::t* __restrict__ psi, int nr,
+                                                            int n1, int n2, int n3, int k1, int k2, int k3, int nk1,
+                                                            int nk2, int nk3, typename cpx<T>::t* __restrict__ u) {
+  const int rp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rp >= nr) return;
+  const long b = blockIdx.y;
+  const int i1 = rp / (n2 * n3), rem = rp - i1 * n2 * n3, i2 = rem / n3, i3 = rem - i2 * n3;
+  double f = (double)k1 * i1 / (nk1 * n1) + (double)k2 * i2 / (nk2 * n2) + (double)k3 * i3 / (nk3 * n3);
+  f -= floor(f);
+  double sn, cs;
+  sincospi(-2.0 * f, &sn, &cs);
+  const T c = T(cs), s = T(sn);
+  const auto v = psi[b * nr + rp];
+  u[b * nr + rp] = mk(v.x * c - v.y * s, v.x * s + v.y * c);
+}
+
 // The supercell grid of a k mesh, and the index maps of the cell G set (cell
 // grid) and of the supercell G set {q + g} (q outer, g inner) on the supercell grid.
 static gw_status kmesh_grids(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_chi, const int32_t* gvec_h,
@@ -334,6 +354,174 @@ extern "C" gw_status gw_chi0_omega_kmesh(gw_ctx* ctx, const gw_grid* grid, const
                                n_k * n_chi, rows, 1.0, s, dsinv, tmp_s)))
         return st;
     }
+    if ((st = launch_q_phase(ctx, prec, g, nk, slab_j, ld, n_chi, -1.0, s))) return st;
+    if ((st = launch_col_plane(ctx, g, prec, -1, slab_j, ld, (int)ld, 1.0, s))) return st;
+  }
+  for (int q = 0; q < n_k; ++q) {
+    char* out_q = static_cast<char*>(chi_w) + (size_t)q * n * n_chi * n_chi * es;
+    if ((st = launch_col_line_ct(ctx, g, prec, slabs + (size_t)q * n_chi * es, (long)slab, ld, n, dcw, n, out_q,
+                                 (long)n_chi * n_chi, n_chi, dinv, n_chi, s, cw32.empty() ? nullptr : cw32.data())))
+      return st;
+  }
+  return tc ? tc_check(ctx, tcs, s) : GW_OK;
+}
+
+// chi0 on a k mesh with G_k in its plane-wave form (Sec. II.B, Eqs. G1_unocc_k,
+// G1_occ_k, then Eqs. FFT_G1 and FFT_G2 on the stripe).  With u_ak = exp(-i k.r)
+// psi_ak (cell-periodic) and its coefficients over the plane-wave set, the G
+// formation of the Gamma-point plane-wave chain gives per k the matrix over the
+// set and its column transform T_k(r, g') over the cell grid (Eq. FFT_G1 without
+// the Bloch factor).  The stripe row r of the supercell's plane-wave chain is
+// then exp(-i k.r) T_k(r, g') / N_k at the (negated) supercell positions k + nk g'
+// for every k: the same rows the Gamma-point chain would form for the orbitals
+// extended over the supercell, whose plane waves of different k never meet.
+// The plane-wave row pass expands both Green's functions over R' (Eq. FFT_G2),
+// multiplies them and transforms onto the supercell G set {q + g} (the two
+// factors 1/N_k go into its scale); the q phases, column passes and cosine
+// transform are those of gw_chi0_omega_kmesh.
+extern "C" gw_status gw_chi0_omega_kmesh_pw(gw_ctx* ctx, const gw_grid* grid, const int* nk, int n_b, int n_occ,
+                                            const void* psi_k, const double* eps_k_h, double mu, int n,
+                                            const double* tau_h, const double* C_h, int n_chi, const int32_t* gvec_h,
+                                            int n_pw, const int32_t* pw_index_h, gw_prec prec, void* chi_w,
+                                            void* stream) {
+  if (!ctx) return fail(nullptr, GW_ERR_ARG, "ctx is NULL");
+  if (!psi_k || !eps_k_h || !tau_h || !C_h || !chi_w || !pw_index_h) return fail(ctx, GW_ERR_ARG, "NULL pointer");
+  if (!valid_prec(prec)) return fail(ctx, GW_ERR_ARG, "bad precision");
+  GridInfo g, gs;
+  std::vector<int> map, inv, smap, sinv;
+  gw_status st = kmesh_grids(ctx, grid, nk, n_chi, gvec_h, &g, &gs, map, inv, smap, sinv);
+  if (st) return st;
+  const int n_k = nk[0] * nk[1] * nk[2];
+  if (n_b < 2 || n_b > g.nr) return fail(ctx, GW_ERR_SHAPE, "need 2 <= n_b <= N_r");
+  for (int k = 0; k < n_k; ++k)
+    if ((st = check_energies(ctx, eps_k_h + (size_t)k * n_b, n_b, n_occ, mu))) return st;
+  if (n < 1 || n > 32) return fail(ctx, GW_ERR_SHAPE, "need 1 <= n <= 32");
+  for (int j = 0; j < n; ++j)
+    if (!(tau_h[j] > 0)) return fail(ctx, GW_ERR_ARG, "tau must be > 0");
+  std::vector<int> map_pw, inv_pw;
+  if ((st = index_maps(ctx, g, pw_index_h, n_pw, map_pw, inv_pw))) return st;
+  // supercell positions of the plane waves k + nk g' of every k, negated as on the cell grid;
+  // (k, g') -> k + nk g' is one-to-one onto the supercell grid, so no two entries meet
+  const int sn[3] = {gs.n1, gs.n2, gs.n3};
+  std::vector<int> inv_pws(gs.nr, -1);
+  for (int k = 0; k < n_k; ++k) {
+    const int kv[3] = {k / (nk[1] * nk[2]), (k / nk[2]) % nk[1], k % nk[2]};
+    for (int j = 0; j < n_pw; ++j) {
+      const int p = map_pw[j];
+      const int pv[3] = {p / (g.n2 * g.n3), (p / g.n3) % g.n2, p % g.n3};
+      int pos = 0;
+      for (int d = 0; d < 3; ++d) {
+        const int m = (kv[d] + nk[d] * pv[d]) % sn[d];
+        pos = pos * sn[d] + (sn[d] - m) % sn[d];
+      }
+      inv_pws[pos] = k * n_pw + j;
+    }
+  }
+  pw_negate(g, map_pw, inv_pw);
+  const int n_pws = n_k * n_pw, n_chis = n_k * n_chi;
+  if ((st = check_row_pw(ctx, gs, prec, n_pws, n_chis))) return st;
+  cudaStream_t s = as_stream(stream);
+  const size_t es = csize(prec);
+  const bool tc = prec == GW_F16X3 || prec == GW_BF16X3;
+  const long ld = (long)n_chis;                        // slab row: all q blocks
+  const long ldt = (long)n_pws;                        // T row: all k blocks
+  const size_t slab = (size_t)g.nr * ld;
+  const GridInfo gp = pw_grid(g, n_pw);
+  const bool tmp_needed = row_two_pass(g, prec) && is_fp64(prec);
+  Carver probe(nullptr);
+  probe.take<int>(g.nr);
+  probe.take<int>(gs.nr);
+  probe.take<int>(n_pw);
+  probe.take<int>(g.nr);
+  probe.take<int>(gs.nr);
+  probe.take<char>((size_t)n_k * n_b * 8);
+  probe.take<char>((size_t)n * n * 8);
+  probe.take<double>(2 * (size_t)n_b);
+  probe.take<char>(slab * n * es);
+  probe.take<char>((size_t)n_b * g.nr * es);
+  probe.take<char>((size_t)n_k * n_b * n_pw * es);
+  probe.take<char>((size_t)n_pw * n_pw * es);
+  probe.take<char>((size_t)n_pw * n_pw * es);
+  probe.take<char>((size_t)g.nr * ldt * es);
+  probe.take<char>((size_t)g.nr * ldt * es);
+  if (tmp_needed) probe.take<char>((size_t)n_b * g.nr * es);
+  if (tc) probe.take<char>(tc_scratch_bytes(gp, n_b, n_occ, n_pw, false));
+  if ((st = reserve(ctx, probe.off))) return st;
+  Carver cv(ctx->arena);
+  int* dinv = cv.take<int>(g.nr);
+  int* dsinv = cv.take<int>(gs.nr);
+  int* dmap_pw = cv.take<int>(n_pw);
+  int* dinv_pw = cv.take<int>(g.nr);
+  int* dinv_pws = cv.take<int>(gs.nr);
+  char* dscale = cv.take<char>((size_t)n_k * n_b * 8);
+  char* dcw = cv.take<char>((size_t)n * n * 8);
+  double* dnorm = cv.take<double>(2 * (size_t)n_b);
+  char* slabs = cv.take<char>(slab * n * es);
+  char* u = cv.take<char>((size_t)n_b * g.nr * es);
+  char* dc = cv.take<char>((size_t)n_k * n_b * n_pw * es);
+  char* mo = cv.take<char>((size_t)n_pw * n_pw * es);
+  char* mu_ = cv.take<char>((size_t)n_pw * n_pw * es);
+  char* to = cv.take<char>((size_t)g.nr * ldt * es);
+  char* tu = cv.take<char>((size_t)g.nr * ldt * es);
+  char* tmp = tmp_needed ? cv.take<char>((size_t)n_b * g.nr * es) : nullptr;
+  void* tcs = tc ? cv.take<char>(tc_scratch_bytes(gp, n_b, n_occ, n_pw, false)) : nullptr;
+  if ((st = upload(ctx, dinv, inv.data(), sizeof(int) * g.nr, s))) return st;
+  if ((st = upload(ctx, dsinv, sinv.data(), sizeof(int) * gs.nr, s))) return st;
+  if ((st = upload(ctx, dmap_pw, map_pw.data(), sizeof(int) * n_pw, s))) return st;
+  if ((st = upload(ctx, dinv_pw, inv_pw.data(), sizeof(int) * g.nr, s))) return st;
+  if ((st = upload(ctx, dinv_pws, inv_pws.data(), sizeof(int) * gs.nr, s))) return st;
+  const double fac = g.dv * g.dv / g.volume;   // Eq. FFTX2 normalisation
+  std::vector<float> cw32;
+  if (is_fp64(prec)) {
+    std::vector<double> cw(C_h, C_h + n * n);
+    for (auto& v : cw) v *= fac;
+    if ((st = upload(ctx, dcw, cw.data(), sizeof(double) * n * n, s))) return st;
+  } else {
+    cw32 = split_weights(C_h, n * n, fac);
+    if ((st = upload(ctx, dcw, cw32.data(), sizeof(float) * 2 * n * n, s))) return st;
+  }
+  // the coefficients of u_ak over the set for every k (checked to span every band)
+  for (int k = 0; k < n_k; ++k) {
+    const int kv[3] = {k / (nk[1] * nk[2]), (k / nk[2]) % nk[1], k % nk[2]};
+    const char* pk = static_cast<const char*>(psi_k) + (size_t)k * n_b * g.nr * es;
+    const dim3 grd((g.nr + 255) / 256, n_b);
+    if (is_fp64(prec))
+      bloch_unphase_kernel<double><<<grd, 256, 0, s>>>((const double2*)pk, g.nr, g.n1, g.n2, g.n3, kv[0], kv[1],
+                                                       kv[2], nk[0], nk[1], nk[2], (double2*)u);
+    else
+      bloch_unphase_kernel<float><<<grd, 256, 0, s>>>((const float2*)pk, g.nr, g.n1, g.n2, g.n3, kv[0], kv[1], kv[2],
+                                                      nk[0], nk[1], nk[2], (float2*)u);
+    if ((st = launch_check(ctx, "bloch_unphase_kernel"))) return st;
+    if ((st = pw_coefficients(ctx, g, prec, u, n_b, n_pw, dmap_pw, dinv_pw, dc + (size_t)k * n_b * n_pw * es, dnorm,
+                              tmp, s)))
+      return st;
+  }
+  const double row_scale = -2.0 / ((double)n_k * n_k);
+  for (int j = 0; j < n; ++j) {
+    for (int k = 0; k < n_k; ++k) {
+      const GreenScales sc = green_scales(eps_k_h + (size_t)k * n_b, n_b, n_occ, mu, tau_h[j]);
+      const char* dck = dc + (size_t)k * n_b * n_pw * es;
+      if (tc) {
+        st = tc_green_rows(ctx, gp, n_b, n_occ, dck, sc, 0, n_pw, prec, mo, mu_, tcs, true, s);
+      } else {
+        if ((st = upload_scales(ctx, dscale + (size_t)k * n_b * 8, sc, prec, s))) return st;
+        st = green_rows(ctx, gp, n_b, n_occ, dck, dscale + (size_t)k * n_b * 8, sc, 0, n_pw, prec, mo, mu_, s);
+      }
+      if (st) return st;
+      for (int part = 0; part < 2; ++part) {
+        const char* m = part ? mu_ : mo;
+        char* t = (part ? tu : to) + (size_t)k * n_pw * es;
+        if ((st = launch_col_line(ctx, g, prec, +1, 1, m, n_pw, t, ldt, n_pw, dinv_pw, 1.0, s))) return st;
+        if ((st = launch_col_plane(ctx, g, prec, +1, t, ldt, n_pw, 1.0, s))) return st;
+      }
+    }
+    // exp(-i k.r) on the block of each k, then per row: expand, multiply, transform onto {q + g}
+    if ((st = launch_q_phase(ctx, prec, g, nk, to, ldt, n_pw, -1.0, s))) return st;
+    if ((st = launch_q_phase(ctx, prec, g, nk, tu, ldt, n_pw, -1.0, s))) return st;
+    char* slab_j = slabs + (size_t)j * slab * es;
+    if ((st = launch_row_pw_chi(ctx, gs, prec, tu, to, ldt, slab_j, ld, dinv_pws, n_pws, dsinv, n_chis, g.nr,
+                                row_scale, s)))
+      return st;
     if ((st = launch_q_phase(ctx, prec, g, nk, slab_j, ld, n_chi, -1.0, s))) return st;
     if ((st = launch_col_plane(ctx, g, prec, -1, slab_j, ld, (int)ld, 1.0, s))) return st;
   }

@@ -30,7 +30,7 @@ EXPORTS = ["gw_ctx_create", "gw_ctx_destroy", "gw_last_error", "gw_ctx_launches"
            "gw_chi0_plan_create", "gw_chi0_plan_launch", "gw_chi0_plan_status", "gw_chi0_plan_destroy",
            "gw_sigma_matrix", "gw_qp_energies", "gw_invert_transform", "gw_sigma_to_tau", "gw_mp2_grids",
            "gw_zgemm_sliced", "gw_batch_plan", "gw_batch_launch", "gw_batch_wait", "gw_batch_destroy",
-           "gw_chi0_omega_pw", "gw_sigma_diag_pw"]
+           "gw_chi0_omega_pw", "gw_sigma_diag_pw", "gw_chi0_omega_kmesh_pw"]
 
 
 class GwError(RuntimeError):
@@ -91,6 +91,8 @@ _SIGS = {
     "gw_sigma_diag_kmesh": (_I, [_P, _G, _IP, _I, _I, _P, _DP, ct.c_double, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I,
                                  _IP, _I, _DP, _P, _DP, _I, _P, _P]),
     "gw_chi0_omega_kmesh": (_I, [_P, _G, _IP, _I, _I, _P, _DP, ct.c_double, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
+    "gw_chi0_omega_kmesh_pw": (_I, [_P, _G, _IP, _I, _I, _P, _DP, ct.c_double, _I, _DP, _DP, _I, _IP, _I, _IP, _I,
+                                    _P, _P]),
     "gw_sigma_diag": (_I, [_P, _G, _I, _I, _P, _DP, _D, _IP, _I, _I, _DP, _DP, _DP, _DP, _P, _I, _IP, _I,
                            _DP, _DP, _DP, _I, _DP, _P]),
     "gw_chi0_omega": (_I, [_P, _G, _I, _I, _P, _DP, _D, _I, _DP, _DP, _I, _IP, _I, _I, _P, _P]),
@@ -524,6 +526,23 @@ def chi0_omega_kmesh(ctx, grid, nk, psi_k, eps_k, n_occ, mu, tau, C, gvec, prec,
     _check(lib().gw_chi0_omega_kmesh(ctx.handle, ct.byref(grid), _ip(nkv), psi_k.shape[1], int(n_occ),
                                      _dev(psi_k, "psi_k", p), _dp(eps_k), float(mu), len(tau), _dp(tau), _dp(C),
                                      len(gv), _ip(gv), p, int(r_block), _dev(chi_w, "chi_w", p), _stream()), ctx)
+
+
+def chi0_omega_kmesh_pw(ctx, grid, nk, psi_k, eps_k, n_occ, mu, tau, C, gvec, pw_index, prec, chi_w):
+    """chi0_q(G,G',i omega) on a Gamma-centred k mesh with G_k through its plane-wave
+    form (gw_chi0_omega_kmesh_pw).  psi_k: device [N_k][N_b][N_r]; pw_index: cell
+    FFT positions of the plane waves spanning every exp(-i k.r) psi_nk; the rest as
+    chi0_omega_kmesh."""
+    p = prec_of(prec)
+    nkv = _i32(nk)
+    eps_k = _f64(eps_k)
+    tau = _f64(tau)
+    C = _f64(C)
+    gv = _i32(gvec)
+    pw = _i32(pw_index)
+    _check(lib().gw_chi0_omega_kmesh_pw(ctx.handle, ct.byref(grid), _ip(nkv), psi_k.shape[1], int(n_occ),
+                                        _dev(psi_k, "psi_k", p), _dp(eps_k), float(mu), len(tau), _dp(tau), _dp(C),
+                                        len(gv), _ip(gv), len(pw), _ip(pw), p, _dev(chi_w, "chi_w", p), _stream()), ctx)
 
 
 class Chi0Plan:
