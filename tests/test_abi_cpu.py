@@ -99,6 +99,10 @@ def test_device_calls_reject_null_context(L):
     st = L.gw_chi0_rtau(None, 4, 4, 1, None, None, None, None)
     assert st == 1
     assert b"ctx" in L.gw_last_error(None)
+    st = L.gw_chi0_omega_kmesh_pw(None, None, None, 0, 0, None, None, 0.0, 0, None, None, 0, None, 0, None, 0, None,
+                                  None)
+    assert st == 1
+    assert b"ctx" in L.gw_last_error(None)
 
 
 def test_ctx_create_without_gpu_fails_cleanly(L):
